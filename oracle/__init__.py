@@ -1,0 +1,283 @@
+"""Plain FP64 CPU oracle of the multiple Arnoldi (mArnoldi) method.
+
+TEST INFRASTRUCTURE ONLY: imported by ``tests/``, by ``__graft_entry__.smoke()``
+and by the CPU-baseline leg of ``bench.py``.  The product library never imports,
+links or runs anything here, and nothing here imports the product.
+
+The arithmetic lives in ``marnoldi_oracle.c`` (plain loops, OpenMP over columns
+only); this module compiles it with gcc, calls it through ctypes and arranges
+its per-column outputs into BSR density values.  The steps follow
+Hoshi, Yamazaki, Akiyama, arXiv:1307.3218, Section 2 (Eq. 1, Eq. 2 and the
+paragraph after Eq. 2); the readings of points the paper leaves open are listed
+at the top of ``marnoldi_oracle.c``.
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+import os
+import platform
+import subprocess
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "marnoldi_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB = None
+
+TAU_FP64 = 1e-10      # relative breakdown threshold
+BISECT_RTOL = 1e-12   # |N - Ne| <= rtol * Ne
+BISECT_MAXIT = 200
+
+
+def lib_path() -> str:
+    return os.path.join(_BUILD, f"libmarnoldi_oracle_{platform.machine()}.so")
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (-O2, OpenMP).  Returns the library path."""
+    out = lib_path()
+    if force or not os.path.exists(out) or os.path.getmtime(out) < os.path.getmtime(_SRC):
+        os.makedirs(_BUILD, exist_ok=True)
+        tmp = out + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=c11",
+                               "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, out)
+    return out
+
+
+def _lib():
+    global _LIB
+    if _LIB is None:
+        L = C.CDLL(build())
+        P = C.c_void_p
+        i64, i32, d = C.c_int64, C.c_int, C.c_double
+        L.oracle_column.restype = i32
+        L.oracle_column.argtypes = [i64, P, P, P, P, i64, i32, d, i64, P, P, P, P, P, P, P]
+        L.oracle_columns.restype = i32
+        L.oracle_columns.argtypes = [i64, P, P, P, P, i64, P, i32, d, P, P, P, P, P, P, P, i32]
+        L.oracle_jacobi_eigh.restype = i32
+        L.oracle_jacobi_eigh.argtypes = [i32, P, P, P]
+        L.oracle_fermi.restype = d
+        L.oracle_fermi.argtypes = [d]
+        L.oracle_count.restype = None
+        L.oracle_count.argtypes = [i64, P, P, d, d, P, P]
+        L.oracle_bisect.restype = i32
+        L.oracle_bisect.argtypes = [i64, P, P, d, d, d, i32, P, P, P]
+        L.oracle_density.restype = None
+        L.oracle_density.argtypes = [i64, i32, P, P, P, P, d, d, P, P]
+        L.oracle_threads.restype = i32
+        L.oracle_threads.argtypes = []
+        _LIB = L
+    return _LIB
+
+
+class use_library:
+    """Context manager: run the oracle functions against another build of the oracle source.
+
+    Only the mutation tests use it, to check that planted mistakes fail the pins.
+    """
+
+    def __init__(self, path: str):
+        self.path = path
+
+    def __enter__(self):
+        global _LIB
+        self.saved = _LIB
+        _LIB = None
+        real_build = globals()["build"]
+        globals()["build"] = lambda force=False: self.path
+        try:
+            _lib()
+        finally:
+            globals()["build"] = real_build
+        return self
+
+    def __exit__(self, *exc):
+        global _LIB
+        _LIB = self.saved
+        return False
+
+
+def _p(a: np.ndarray):
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def threads() -> int:
+    return int(_lib().oracle_threads())
+
+
+def fermi(x: float) -> float:
+    return float(_lib().oracle_fermi(float(x)))
+
+
+def jacobi_eigh(A: np.ndarray) -> tuple[np.ndarray, np.ndarray]:
+    A = np.ascontiguousarray(A, dtype=np.float64).copy()
+    n = A.shape[0]
+    e = np.zeros(n)
+    V = np.zeros((n, n))
+    if _lib().oracle_jacobi_eigh(n, _p(A), _p(e), _p(V)) < 0:
+        raise RuntimeError("Jacobi did not converge")
+    return e, V
+
+
+def pattern_rows(sysm, j: int) -> np.ndarray:
+    """Orbital rows of column j's pattern: the 4 rows of every block in block-row j//4, in block order."""
+    J = j // 4
+    blocks = sysm.col_idx[sysm.row_ptr[J]:sysm.row_ptr[J + 1]].astype(np.int64)
+    return (4 * blocks[:, None] + np.arange(4)[None, :]).reshape(-1)
+
+
+def _csr_args(sysm):
+    rp = np.ascontiguousarray(sysm.row_ptr, dtype=np.int64)
+    ci = np.ascontiguousarray(sysm.col_idx, dtype=np.int32)
+    Hv = np.ascontiguousarray(sysm.H, dtype=np.float64)
+    Sv = np.ascontiguousarray(sysm.S, dtype=np.float64)
+    return rp, ci, Hv, Sv
+
+
+@dataclass
+class Columns:
+    cols: np.ndarray        # (nc,) int64 orbital columns
+    nu: int
+    nu_eff: np.ndarray      # (nc,) int32
+    eps: np.ndarray         # (nc, nu)
+    w: np.ndarray           # (nc, nu)
+    t: np.ndarray           # (nc, nu)
+    row_off: np.ndarray     # (nc+1,) offsets into rows / Y
+    rows: np.ndarray        # concatenated orbital rows per column
+    Y: np.ndarray           # (row_off[-1], nu): rows of K V
+
+
+def column(sysm, j: int, nu: int, tau: float = TAU_FP64, rows: np.ndarray | None = None):
+    """One column with its subspace matrix and basis (small systems; for the pins)."""
+    rp, ci, Hv, Sv = _csr_args(sysm)
+    M = sysm.M
+    rows = np.arange(M, dtype=np.int64) if rows is None else np.ascontiguousarray(rows, np.int64)
+    eps = np.zeros(nu); w = np.zeros(nu); t = np.zeros(nu)
+    Y = np.zeros((rows.size, nu)); Hsub = np.zeros((nu, nu)); K = np.zeros((nu, M))
+    r = _lib().oracle_column(sysm.n_block_rows, _p(rp), _p(ci), _p(Hv), _p(Sv), int(j), int(nu),
+                             float(tau), rows.size, _p(rows), _p(eps), _p(w), _p(t), _p(Y),
+                             _p(Hsub), _p(K))
+    if r < 0:
+        raise RuntimeError(f"oracle column failed: {r}")
+    return dict(nu_eff=r, eps=eps, w=w, t=t, Y=Y, Hsub=Hsub, K=K, rows=rows)
+
+
+def columns(sysm, cols, nu: int, tau: float = TAU_FP64, full_rows: bool = False,
+            nthreads: int = 0) -> Columns:
+    rp, ci, Hv, Sv = _csr_args(sysm)
+    cols = np.ascontiguousarray(cols, dtype=np.int64)
+    nc = cols.size
+    if full_rows:
+        rows_l = [np.arange(sysm.M, dtype=np.int64)] * nc
+    else:
+        rows_l = [pattern_rows(sysm, int(j)) for j in cols]
+    row_off = np.zeros(nc + 1, np.int64)
+    row_off[1:] = np.cumsum([r.size for r in rows_l])
+    rows = np.ascontiguousarray(np.concatenate(rows_l) if nc else np.zeros(0, np.int64))
+    nu_eff = np.zeros(nc, np.int32)
+    eps = np.zeros((nc, nu)); w = np.zeros((nc, nu)); t = np.zeros((nc, nu))
+    Y = np.zeros((int(row_off[-1]), nu))
+    r = _lib().oracle_columns(sysm.n_block_rows, _p(rp), _p(ci), _p(Hv), _p(Sv), nc, _p(cols),
+                              int(nu), float(tau), _p(row_off), _p(rows), _p(nu_eff), _p(eps),
+                              _p(w), _p(t), _p(Y), int(nthreads))
+    if r < 0:
+        raise RuntimeError(f"oracle columns failed: {r}")
+    return Columns(cols, nu, nu_eff, eps, w, t, row_off, rows, Y)
+
+
+def valid_levels(c: Columns) -> tuple[np.ndarray, np.ndarray]:
+    """(eps, w) of the nu_eff valid levels of every column, concatenated."""
+    mask = np.arange(c.nu)[None, :] < c.nu_eff[:, None]
+    return np.ascontiguousarray(c.eps[mask]), np.ascontiguousarray(c.w[mask])
+
+
+def count(eps, w, mu: float, kT: float) -> tuple[float, float]:
+    eps = np.ascontiguousarray(eps, np.float64); w = np.ascontiguousarray(w, np.float64)
+    N = C.c_double(); E = C.c_double()
+    _lib().oracle_count(eps.size, _p(eps), _p(w), float(mu), float(kT), C.byref(N), C.byref(E))
+    return N.value, E.value
+
+
+def bisect(eps, w, Ne: float, kT: float, rtol: float = BISECT_RTOL,
+           maxit: int = BISECT_MAXIT) -> tuple[float, float, float, int]:
+    eps = np.ascontiguousarray(eps, np.float64); w = np.ascontiguousarray(w, np.float64)
+    mu = C.c_double(); N = C.c_double(); E = C.c_double()
+    it = _lib().oracle_bisect(eps.size, _p(eps), _p(w), float(Ne), float(kT), float(rtol),
+                              int(maxit), C.byref(mu), C.byref(N), C.byref(E))
+    if it < 0:
+        raise RuntimeError("electron count outside the bisection bracket")
+    return mu.value, N.value, E.value, it
+
+
+def density_rows(c: Columns, mu: float, kT: float) -> tuple[np.ndarray, np.ndarray]:
+    rho = np.zeros(c.Y.shape[0]); rhoE = np.zeros(c.Y.shape[0])
+    _lib().oracle_density(c.cols.size, c.nu, _p(c.row_off), _p(np.ascontiguousarray(c.eps)),
+                          _p(np.ascontiguousarray(c.t)), _p(c.Y), float(mu), float(kT),
+                          _p(rho), _p(rhoE))
+    return rho, rhoE
+
+
+def green_rows(c: Columns, z: complex) -> np.ndarray:
+    """G(z) e_j on each column's rows: (K V) diag(1/(z - eps)) t (valid levels only)."""
+    out = np.zeros(c.Y.shape[0], np.complex128)
+    for ci_ in range(c.cols.size):
+        ne = int(c.nu_eff[ci_])
+        y = c.t[ci_, :ne] / (z - c.eps[ci_, :ne])
+        sl = slice(c.row_off[ci_], c.row_off[ci_ + 1])
+        out[sl] = c.Y[sl, :ne] @ y
+    return out
+
+
+def block_index(sysm) -> dict:
+    """(I, J) -> BSR block index."""
+    rows = np.repeat(np.arange(sysm.n_block_rows), np.diff(sysm.row_ptr))
+    return {(int(I), int(J)): k for k, (I, J) in enumerate(zip(rows, sysm.col_idx))}
+
+
+def scatter_pattern(sysm, c: Columns, vals_rows: np.ndarray) -> np.ndarray:
+    """Put pattern-row values of columns j into BSR values [nnzb, 4, 4] (entry [I,J][a][b] = col 4J+b, row 4I+a).
+
+    Blocks whose column was not computed stay NaN.
+    """
+    out = np.full((sysm.nnzb, 4, 4), np.nan, dtype=vals_rows.dtype)
+    bidx = block_index(sysm)
+    for ci_, j in enumerate(c.cols):
+        J, b = int(j) // 4, int(j) % 4
+        seg = vals_rows[c.row_off[ci_]:c.row_off[ci_ + 1]]
+        for r, row in enumerate(c.rows[c.row_off[ci_]:c.row_off[ci_ + 1]]):
+            I, a = int(row) // 4, int(row) % 4
+            out[bidx[(I, J)], a, b] = seg[r]
+    return out
+
+
+@dataclass
+class Solution:
+    mu: float
+    N: float
+    E_band: float
+    rho: np.ndarray       # [nnzb, 4, 4]
+    rhoE: np.ndarray      # [nnzb, 4, 4]
+    cols: Columns
+    iters: int
+
+
+def solve(sysm, nu: int, kT: float, Ne: float | None = None, mu_fixed: float | None = None,
+          cols=None, tau: float = TAU_FP64, nthreads: int = 0) -> Solution:
+    """The whole path: every column's subspace, the Fermi level, rho and rho^E on H's pattern, E_band."""
+    if cols is None:
+        cols = sysm.real_columns()
+    c = columns(sysm, cols, nu, tau=tau, nthreads=nthreads)
+    e, w = valid_levels(c)
+    if mu_fixed is None:
+        Ne = sysm.n_electrons if Ne is None else Ne
+        mu, N, E, it = bisect(e, w, Ne, kT)
+    else:
+        mu = float(mu_fixed)
+        N, E = count(e, w, mu, kT)
+        it = 0
+    rr, rre = density_rows(c, mu, kT)
+    return Solution(mu, N, E, scatter_pattern(sysm, c, rr), scatter_pattern(sysm, c, rre), c, it)
