@@ -1,0 +1,189 @@
+/*
+ * marnoldi.h -- C ABI of libmarnoldi, the GB300 (sm_103a) multiple Arnoldi solver.
+ *
+ * The library implements the data-parallel hot path of the multiple Arnoldi
+ * (mArnoldi) method of Hoshi, Yamazaki and Akiyama (arXiv:1307.3218, Section 2):
+ * for every requested basis index j of a sparse real-symmetric LCAO pair (H, S),
+ * S positive definite, it
+ *   1. builds the nu-dimensional Krylov subspace L_nu^(j) that contains e_j
+ *      (span{e_j, H e_j, ..., H^(nu-1) e_j}) with an S-orthonormal basis K,
+ *      using two-pass modified Gram-Schmidt in the S inner product;
+ *   2. solves the nu x nu standard subspace eigenproblem H_sub = K^T H K
+ *      (levels eps_a, vectors v_a);
+ *   3. turns the subspace eigenpairs into the columns of the Green's function
+ *      (z S - H)^-1 e_j (Eq. 1), of the density matrix and of the
+ *      energy-density matrix, and into the band energy, at a Fermi level mu
+ *      found by bisection on the electron count (or given).
+ *
+ * Conventions
+ *   - Matrices are BSR with 4x4 blocks: row_ptr[n_block_rows + 1] (int64,
+ *     row_ptr[0] = 0), col_idx[nnzb] (int32, strictly ascending inside a block
+ *     row, the diagonal block present), vals[nnzb][4][4] row-major doubles.
+ *     Orbital index of (atom I, orbital a) is 4 I + a; M = 4 n_block_rows.
+ *     H and S share one pattern, which must be symmetric.
+ *   - Outputs on H's pattern use the same BSR layout: entry [k][a][b] of block
+ *     k = (I, J) is row 4 I + a, column 4 J + b.  Column 4 J + b of rho,
+ *     rho^E and G(z) is produced by the subspace of j = 4 J + b; the columns
+ *     are not symmetrised.
+ *   - Energies in the units of H (eV for the bundled models); kT in the same
+ *     units; f(x) = 1 / (1 + e^x), spin factor 2.
+ *   - Every function returns a marnoldi_status; nothing throws or exits
+ *     across the ABI.  On failure marnoldi_last_error(ctx) describes it.
+ *   - Host pointers unless a name ends in _device.  The caller owns every
+ *     array it passes; the library copies what it keeps.
+ *   - One context per structure.  A context's calls are issued on its CUDA
+ *     stream and are not thread-safe; different contexts are independent.
+ */
+#ifndef MARNOLDI_H
+#define MARNOLDI_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct marnoldi_ctx marnoldi_ctx;
+
+typedef enum {
+    MARNOLDI_OK = 0,
+    MARNOLDI_EINVAL = -1,    /* bad argument or malformed matrices */
+    MARNOLDI_ENOTSPD = -2,   /* S shown not positive definite */
+    MARNOLDI_ENOMEM = -3,    /* device or host allocation failed */
+    MARNOLDI_ECUDA = -4,     /* a CUDA call failed */
+    MARNOLDI_ETIMEOUT = -5,  /* a bounded device loop ran out of iterations */
+    MARNOLDI_ESTATE = -6,    /* call out of order (e.g. density before solve) */
+    MARNOLDI_ENOCONV = -7    /* the subspace eigensolver or the bisection did not converge */
+} marnoldi_status;
+
+typedef enum {
+    MARNOLDI_FP64 = 0,   /* every step in FP64 */
+    MARNOLDI_MIXED = 1   /* FP32 SpMM and Krylov-vector storage; FP64 inner products,
+                            Gram-Schmidt coefficients, eigensolve and accumulation */
+} marnoldi_precision;
+
+/* Device allocator hook: alloc(bytes, stream, user) returns device memory usable
+ * in the order of `stream`; free(ptr, bytes, stream, user) releases it.  Passing
+ * NULL for both restores the default (cudaMallocAsync / cudaFreeAsync).
+ * Process-wide; set it before creating contexts.  Returns MARNOLDI_OK. */
+typedef void *(*marnoldi_alloc_fn)(size_t bytes, void *stream, void *user);
+typedef void (*marnoldi_free_fn)(void *ptr, size_t bytes, void *stream, void *user);
+int marnoldi_set_allocator(marnoldi_alloc_fn alloc, marnoldi_free_fn free_fn, void *user);
+
+/*
+ * Validate and upload one structure (H, S) to the device (arXiv:1307.3218,
+ * Section 2: sparse real-symmetric M x M LCAO matrices, S positive definite).
+ *
+ *   out           receives a new context (NULL on failure).
+ *   n_block_rows  number of atoms (>= 1).
+ *   row_ptr, col_idx, H_vals, S_vals   the BSR pair described above (host).
+ *   orbital_mask  n_block_rows*4 bytes, 1 = real orbital, 0 = padding orbital
+ *                 (e.g. the three dummy orbitals of a hydrogen atom); NULL = all
+ *                 real.  Padding orbitals must not couple to real ones.
+ *   positions     n_block_rows*3 doubles (atom positions) and
+ *   box           3 doubles (periodic box lengths); both NULL unless a
+ *                 regional solve will be requested.
+ *   precision     marnoldi_precision.
+ *   cuda_stream   cudaStream_t to issue all work on (NULL = legacy default stream).
+ *
+ * Checks (MARNOLDI_EINVAL): pattern shape, ascending columns, diagonal blocks,
+ * pattern symmetry, |H - H^T| and |S - S^T| <= 1e-12 max|.|, finite values.
+ * MARNOLDI_ENOTSPD: S_jj <= 0 for a real orbital, or a Lanczos Ritz value of S
+ * <= 0 (which proves S indefinite).  All checks run on the host before any
+ * device work.
+ */
+int marnoldi_setup(marnoldi_ctx **out, int64_t n_block_rows, const int64_t *row_ptr,
+                   const int32_t *col_idx, const double *H_vals, const double *S_vals,
+                   const uint8_t *orbital_mask, const double *positions, const double *box,
+                   int precision, void *cuda_stream);
+
+/*
+ * Run the hot path for a set of columns (arXiv:1307.3218, Section 2: the
+ * subspaces L_nu^(j) containing e_j, their nu x nu standard eigenproblems, and
+ * the Green's function built from the subspace levels and vectors).
+ *
+ *   columns, ncols  orbital indices to solve (host int64); columns == NULL and
+ *                   ncols < 0 select every real orbital.  Duplicates and
+ *                   padding orbitals are rejected (MARNOLDI_EINVAL).
+ *   nu              subspace dimension, 1 <= nu <= min(M_real, 110).
+ *   region_atoms    0 = global mode (Krylov vectors over all M orbitals, M <= 16384).
+ *                   > 0 = regional mode (not available in this build: MARNOLDI_EINVAL).
+ *   electron_count  target N_e of the bisection (ignored when mu_fixed != NULL).
+ *   kT              > 0.
+ *   mu_fixed        NULL = find mu by bisection on N(mu) = sum_j sum_a 2 f w_a over
+ *                   the solved columns, bracket [min eps - 40 kT, max eps + 40 kT],
+ *                   stop at |N - N_e| <= 1e-12 N_e or after 200 halvings;
+ *                   else use *mu_fixed.
+ *
+ * Per-column Krylov breakdown (||w||_S <= 1e-10 ||H k_n||_S in FP64, 1e-5 in
+ * MIXED) is not an error: the column keeps nu_eff < nu levels (see
+ * marnoldi_column_stats).  Replaces the previous solve's results.
+ */
+int marnoldi_solve(marnoldi_ctx *ctx, const int64_t *columns, int64_t ncols, int nu,
+                   int region_atoms, double electron_count, double kT, const double *mu_fixed);
+
+/*
+ * Density and energy-density values on H's pattern after marnoldi_solve:
+ * rho e_j = K V diag(2 f) V^T q and rho^E e_j = K V diag(2 f eps) V^T q with
+ * q = K^T e_j (arXiv:1307.3218, Section 2: the Green's function determined by
+ * the subspace levels and vectors).  Each output holds nnzb*16 doubles in the
+ * BSR layout above; entries of columns that were not solved are set to 0.
+ * marnoldi_density writes host arrays, marnoldi_density_device device arrays
+ * (written in the context's stream order).
+ */
+int marnoldi_density(marnoldi_ctx *ctx, double *rho_vals, double *rhoE_vals);
+int marnoldi_density_device(marnoldi_ctx *ctx, double *rho_vals_device, double *rhoE_vals_device);
+
+/*
+ * Band energy E = sum_j sum_a 2 f eps_a w_a, the Fermi level mu and the
+ * electron count N(mu) of the last solve (any pointer may be NULL).
+ */
+int marnoldi_energy(marnoldi_ctx *ctx, double *band_energy, double *mu, double *electron_count_out);
+
+/*
+ * Green's-function values G(z) e_j = K V diag(1 / (z - eps)) V^T q on H's
+ * pattern (the solution x of (z S - H) x = e_j inside L_nu^(j); Eq. 1 of
+ * arXiv:1307.3218) for nz complex shifts z = z_re_im[2i] + i z_re_im[2i+1].
+ * G_re_im (host) receives nz * nnzb * 16 complex values, interleaved (re, im),
+ * shift-major.  Entries of unsolved columns are 0.
+ */
+int marnoldi_green(marnoldi_ctx *ctx, const double *z_re_im, int nz, double *G_re_im);
+
+/*
+ * Per-column results of the last solve, in the order of the solved columns
+ * (host arrays; any may be NULL): nu_eff[ncols], eps[ncols*nu] (ascending
+ * subspace levels, zero past nu_eff), w[ncols*nu] (weights
+ * w_a = sqrt(S_jj) v_a[0] (V^T q)_a, zero past nu_eff).
+ */
+int marnoldi_column_stats(marnoldi_ctx *ctx, int32_t *nu_eff, double *eps, double *w);
+
+/* Number of solved columns and nu of the last solve (either pointer may be NULL). */
+int marnoldi_solved_shape(marnoldi_ctx *ctx, int64_t *ncols, int *nu);
+
+/*
+ * Tuning and instrumentation.
+ *   marnoldi_set_batch: columns per device batch (0 = choose from free memory).
+ *   marnoldi_set_profiling: 1 = time every kernel launch with CUDA events on the
+ *     context's stream (adds event records; off by default).
+ *   marnoldi_kernel_stats: for kind = 0 .. marnoldi_kernel_kinds()-1, the kernel
+ *     name, the number of launches and the summed event time (ms, profiling
+ *     only) since the last reset; reset != 0 clears them after reading.
+ */
+int marnoldi_set_batch(marnoldi_ctx *ctx, int64_t batch_columns);
+int marnoldi_set_profiling(marnoldi_ctx *ctx, int enable);
+int marnoldi_kernel_kinds(void);
+int marnoldi_kernel_stats(marnoldi_ctx *ctx, int kind, const char **name, int64_t *launches,
+                          double *ms, int reset);
+
+/* Message of the last failure on ctx (or of the last failed setup when ctx is NULL). */
+const char *marnoldi_last_error(const marnoldi_ctx *ctx);
+
+/* Release the context and its device memory (NULL is ignored). */
+void marnoldi_destroy(marnoldi_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MARNOLDI_H */

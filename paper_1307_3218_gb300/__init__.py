@@ -1,0 +1,24 @@
+"""GB300-native multiple Arnoldi (mArnoldi) solver.
+
+The hot path of the mArnoldi method (Hoshi, Yamazaki, Akiyama, arXiv:1307.3218,
+Section 2) runs in libmarnoldi, hand-written CUDA for sm_103a behind the C ABI
+declared in ``include/marnoldi.h``.  This package holds the CUDA sources
+(``csrc/``), their build (``build.py``) and the ctypes binding
+(``marnoldi.py``), whose functions carry the C names.
+"""
+
+from .marnoldi import (MARNOLDI_FP64, MARNOLDI_MIXED, Context, MarnoldiError, load,
+                       marnoldi_column_stats, marnoldi_density, marnoldi_density_device,
+                       marnoldi_destroy, marnoldi_energy, marnoldi_green, marnoldi_kernel_kinds,
+                       marnoldi_kernel_stats, marnoldi_last_error, marnoldi_set_allocator,
+                       marnoldi_set_batch, marnoldi_set_profiling, marnoldi_setup,
+                       marnoldi_solve, marnoldi_solved_shape, setup_system, use_torch_allocator)
+
+__all__ = [
+    "MARNOLDI_FP64", "MARNOLDI_MIXED", "Context", "MarnoldiError", "load",
+    "marnoldi_column_stats", "marnoldi_density", "marnoldi_density_device", "marnoldi_destroy",
+    "marnoldi_energy", "marnoldi_green", "marnoldi_kernel_kinds", "marnoldi_kernel_stats",
+    "marnoldi_last_error", "marnoldi_set_allocator", "marnoldi_set_batch",
+    "marnoldi_set_profiling", "marnoldi_setup", "marnoldi_solve", "marnoldi_solved_shape",
+    "setup_system", "use_torch_allocator",
+]

@@ -1,0 +1,808 @@
+// Host side of libmarnoldi: the exported C ABI (include/marnoldi.h), input
+// validation, device memory, the batch loop over columns, and the Fermi-level
+// bisection (one device reduction and one 16-byte read-back per step).
+#include "marnoldi.h"
+#include "internal.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <utility>
+#include <vector>
+
+using namespace marnoldi;
+
+namespace {
+
+marnoldi_alloc_fn g_alloc = nullptr;
+marnoldi_free_fn g_free = nullptr;
+void *g_user = nullptr;
+thread_local std::string g_setup_err;
+
+constexpr double kTauFp64 = 1e-10;
+constexpr double kTauMixed = 1e-5;
+constexpr double kBisectRtol = 1e-12;
+constexpr int kBisectMaxit = 200;
+
+}  // namespace
+
+struct marnoldi_ctx {
+    cudaStream_t stream = nullptr;
+    int prec = 0;
+    int64_t nbr = 0, nnzb = 0, m = 0;
+    std::vector<int64_t> rp;
+    std::vector<int32_t> ci;
+    std::vector<uint8_t> mask;
+    std::vector<double> pos, box;
+    marnoldi_alloc_fn alloc = nullptr;
+    marnoldi_free_fn free_fn = nullptr;
+    void *user = nullptr;
+
+    // device copies of the structure
+    DeviceMatrix A{};
+    std::vector<std::pair<void *, size_t>> owned;  // structure + scratch allocations
+
+    // reduction scratch and pinned read-back
+    double *d_partial = nullptr;
+    unsigned *d_ticket = nullptr;
+    double *d_out = nullptr;
+    double *h_out = nullptr;
+
+    // solved state
+    bool solved = false;
+    int64_t ncols = 0;
+    int nu = 0;
+    double mu = 0.0, N = 0.0, E = 0.0, kT = 0.0;
+    std::vector<int64_t> cols;
+    void *state = nullptr;
+    size_t state_bytes = 0;
+    ColumnState st{};
+    int64_t *d_cols = nullptr;
+
+    // batch workspace
+    void *ws = nullptr;
+    size_t ws_bytes = 0;
+    int64_t batch_override = 0;
+    int64_t last_batch = 0;
+
+    // instrumentation
+    int64_t launches[KK_NKINDS] = {};
+    double ms[KK_NKINDS] = {};
+    int profile = 0;
+    std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> pending;
+    std::vector<cudaEvent_t> events;
+
+    std::string err;
+};
+
+namespace {
+
+int fail(marnoldi_ctx *c, int code, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (c) c->err = buf; else g_setup_err = buf;
+    return code;
+}
+
+int fail_cuda(marnoldi_ctx *c, cudaError_t e, const char *what)
+{
+    return fail(c, MARNOLDI_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+void *dalloc(marnoldi_ctx *c, size_t bytes)
+{
+    if (bytes == 0) bytes = 16;
+    void *p = nullptr;
+    if (c->alloc) {
+        p = c->alloc(bytes, (void *)c->stream, c->user);
+    } else if (cudaMallocAsync(&p, bytes, c->stream) != cudaSuccess) {
+        cudaGetLastError();
+        p = nullptr;
+    }
+    return p;
+}
+
+void dfree(marnoldi_ctx *c, void *p, size_t bytes)
+{
+    if (!p) return;
+    if (c->free_fn) c->free_fn(p, bytes, (void *)c->stream, c->user);
+    else cudaFreeAsync(p, c->stream);
+}
+
+template <typename T>
+int dupload(marnoldi_ctx *c, T **dst, const T *src, size_t n, const char *what)
+{
+    const size_t bytes = n * sizeof(T);
+    void *p = dalloc(c, bytes);
+    if (!p) return fail(c, MARNOLDI_ENOMEM, "device allocation of %zu bytes for %s failed", bytes, what);
+    c->owned.push_back({p, bytes});
+    *dst = (T *)p;
+    if (n) {
+        cudaError_t e = cudaMemcpyAsync(p, src, bytes, cudaMemcpyHostToDevice, c->stream);
+        if (e != cudaSuccess) return fail_cuda(c, e, what);
+    }
+    return MARNOLDI_OK;
+}
+
+cudaEvent_t get_event(marnoldi_ctx *c)
+{
+    if (!c->events.empty()) {
+        cudaEvent_t e = c->events.back();
+        c->events.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+void collect_profile(marnoldi_ctx *c)
+{
+    for (auto &p : c->pending) {
+        float t = 0.f;
+        if (cudaEventElapsedTime(&t, p.second.first, p.second.second) == cudaSuccess)
+            c->ms[p.first] += t;
+        c->events.push_back(p.second.first);
+        c->events.push_back(p.second.second);
+    }
+    c->pending.clear();
+    cudaGetLastError();
+}
+
+template <typename F>
+int launch(marnoldi_ctx *c, int kind, F &&f)
+{
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (c->profile) {
+        e0 = get_event(c);
+        e1 = get_event(c);
+        cudaEventRecord(e0, c->stream);
+    }
+    cudaError_t e = f();
+    if (e != cudaSuccess) return fail_cuda(c, e, kernel_name(kind));
+    if (c->profile) {
+        cudaEventRecord(e1, c->stream);
+        c->pending.push_back({kind, {e0, e1}});
+    }
+    c->launches[kind]++;
+    return MARNOLDI_OK;
+}
+
+int sync(marnoldi_ctx *c, const char *what)
+{
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return fail_cuda(c, e, what);
+    if (c->profile) collect_profile(c);
+    return MARNOLDI_OK;
+}
+
+// Smallest eigenvalue of a symmetric tridiagonal matrix (diag a, off b) by
+// Sturm-sequence bisection.
+double tridiag_min_eig(const std::vector<double> &a, const std::vector<double> &b)
+{
+    const int n = (int)a.size();
+    double lo = 1e300, hi = -1e300;
+    for (int i = 0; i < n; ++i) {
+        const double r = (i > 0 ? std::fabs(b[i - 1]) : 0.0) + (i + 1 < n ? std::fabs(b[i]) : 0.0);
+        lo = std::min(lo, a[i] - r);
+        hi = std::max(hi, a[i] + r);
+    }
+    for (int it = 0; it < 200; ++it) {
+        const double x = 0.5 * (lo + hi);
+        int neg = 0;
+        double q = 1.0;
+        for (int i = 0; i < n; ++i) {
+            q = a[i] - x - (i > 0 ? b[i - 1] * b[i - 1] / q : 0.0);
+            if (q == 0.0) q = -1e-300;
+            if (q < 0.0) ++neg;
+        }
+        if (neg >= 1) hi = x; else lo = x;
+        if (hi - lo <= 1e-14 * std::max(1.0, std::fabs(hi))) break;
+    }
+    return lo;
+}
+
+// Lowest Ritz value of S after `steps` plain Lanczos steps from a fixed
+// pseudo-random start on the real orbitals.  Ritz values lie inside S's
+// spectrum, so a value <= 0 proves S is not positive definite.
+double lanczos_min_ritz(const marnoldi_ctx *c, const double *Sv, int steps)
+{
+    const int64_t M = c->m;
+    std::vector<double> v(M, 0.0), vp(M, 0.0), wv(M, 0.0);
+    uint64_t st = 0x9E3779B97F4A7C15ull;
+    double nrm = 0.0;
+    for (int64_t r = 0; r < M; ++r) {
+        st ^= st << 13; st ^= st >> 7; st ^= st << 17;
+        const double x = c->mask.empty() || c->mask[r] ? ((double)(st >> 11) / 9007199254740992.0 - 0.5) : 0.0;
+        v[r] = x;
+        nrm += x * x;
+    }
+    nrm = std::sqrt(nrm);
+    for (auto &x : v) x /= nrm;
+    std::vector<double> a, b;
+    double beta = 0.0;
+    for (int s = 0; s < steps; ++s) {
+        for (int64_t I = 0; I < c->nbr; ++I) {
+            double acc[4] = {0, 0, 0, 0};
+            for (int64_t k = c->rp[I]; k < c->rp[I + 1]; ++k) {
+                const double *B = Sv + 16 * k;
+                const double *x = v.data() + 4 * (int64_t)c->ci[k];
+                for (int p = 0; p < 4; ++p)
+                    for (int q = 0; q < 4; ++q) acc[p] += B[4 * p + q] * x[q];
+            }
+            for (int p = 0; p < 4; ++p) wv[4 * I + p] = acc[p];
+        }
+        double alpha = 0.0;
+        for (int64_t r = 0; r < M; ++r) alpha += wv[r] * v[r];
+        for (int64_t r = 0; r < M; ++r) wv[r] -= alpha * v[r] + beta * vp[r];
+        a.push_back(alpha);
+        double nb = 0.0;
+        for (int64_t r = 0; r < M; ++r) nb += wv[r] * wv[r];
+        nb = std::sqrt(nb);
+        if (!(nb > 1e-12) || s + 1 == steps) break;
+        b.push_back(nb);
+        beta = nb;
+        vp.swap(v);
+        for (int64_t r = 0; r < M; ++r) v[r] = wv[r] / nb;
+    }
+    b.resize(a.size() > 0 ? a.size() - 1 : 0);
+    return tridiag_min_eig(a, b);
+}
+
+int validate_structure(marnoldi_ctx *c, const double *H, const double *S)
+{
+    const int64_t nbr = c->nbr;
+    const auto &rp = c->rp;
+    const auto &ci = c->ci;
+    if (rp[0] != 0) return fail(nullptr, MARNOLDI_EINVAL, "row_ptr[0] must be 0");
+    for (int64_t I = 0; I < nbr; ++I) {
+        if (rp[I + 1] < rp[I]) return fail(nullptr, MARNOLDI_EINVAL, "row_ptr decreases at %lld", (long long)I);
+        bool diag = false;
+        for (int64_t k = rp[I]; k < rp[I + 1]; ++k) {
+            if (ci[k] < 0 || ci[k] >= nbr)
+                return fail(nullptr, MARNOLDI_EINVAL, "col_idx[%lld] = %d out of range", (long long)k, ci[k]);
+            if (k > rp[I] && ci[k] <= ci[k - 1])
+                return fail(nullptr, MARNOLDI_EINVAL, "col_idx not strictly ascending in block row %lld", (long long)I);
+            if (ci[k] == I) diag = true;
+        }
+        if (!diag) return fail(nullptr, MARNOLDI_EINVAL, "block row %lld has no diagonal block", (long long)I);
+    }
+    // symmetry of pattern and values
+    double hmax = 0.0, smax = 0.0;
+    for (int64_t k = 0; k < 16 * c->nnzb; ++k) {
+        if (!std::isfinite(H[k]) || !std::isfinite(S[k]))
+            return fail(nullptr, MARNOLDI_EINVAL, "non-finite matrix value in block %lld", (long long)(k / 16));
+        hmax = std::max(hmax, std::fabs(H[k]));
+        smax = std::max(smax, std::fabs(S[k]));
+    }
+    for (int64_t I = 0; I < nbr; ++I) {
+        for (int64_t k = rp[I]; k < rp[I + 1]; ++k) {
+            const int64_t J = ci[k];
+            const int32_t *b0 = ci.data() + rp[J], *b1 = ci.data() + rp[J + 1];
+            const int32_t *f = std::lower_bound(b0, b1, (int32_t)I);
+            if (f == b1 || *f != (int32_t)I)
+                return fail(nullptr, MARNOLDI_EINVAL, "pattern not symmetric: block (%lld,%lld) has no mirror",
+                            (long long)I, (long long)J);
+            const int64_t kt = rp[J] + (f - b0);
+            for (int a = 0; a < 4; ++a)
+                for (int bb = 0; bb < 4; ++bb) {
+                    if (std::fabs(H[16 * k + 4 * a + bb] - H[16 * kt + 4 * bb + a]) > 1e-12 * hmax)
+                        return fail(nullptr, MARNOLDI_EINVAL, "H not symmetric in block (%lld,%lld)", (long long)I, (long long)J);
+                    if (std::fabs(S[16 * k + 4 * a + bb] - S[16 * kt + 4 * bb + a]) > 1e-12 * smax)
+                        return fail(nullptr, MARNOLDI_EINVAL, "S not symmetric in block (%lld,%lld)", (long long)I, (long long)J);
+                    if (!c->mask.empty() && c->mask[4 * I + a] != c->mask[4 * J + bb] &&
+                        (H[16 * k + 4 * a + bb] != 0.0 || S[16 * k + 4 * a + bb] != 0.0))
+                        return fail(nullptr, MARNOLDI_EINVAL, "padding orbital couples to a real orbital in block (%lld,%lld)",
+                                    (long long)I, (long long)J);
+                }
+        }
+    }
+    // S_jj > 0 for real orbitals; Lanczos lower Ritz value
+    for (int64_t I = 0; I < nbr; ++I)
+        for (int64_t k = rp[I]; k < rp[I + 1]; ++k)
+            if (ci[k] == I)
+                for (int a = 0; a < 4; ++a)
+                    if ((c->mask.empty() || c->mask[4 * I + a]) && !(S[16 * k + 5 * a] > 0.0))
+                        return fail(nullptr, MARNOLDI_ENOTSPD, "S_jj <= 0 at orbital %lld", (long long)(4 * I + a));
+    const double ritz = lanczos_min_ritz(c, S, 40);
+    if (!(ritz > 0.0))
+        return fail(nullptr, MARNOLDI_ENOTSPD, "S is not positive definite (Lanczos Ritz value %.3e)", ritz);
+    return MARNOLDI_OK;
+}
+
+void free_state(marnoldi_ctx *c)
+{
+    if (c->state) dfree(c, c->state, c->state_bytes);
+    c->state = nullptr;
+    c->state_bytes = 0;
+    c->solved = false;
+}
+
+}  // namespace
+
+// ===================================================================== C ABI
+
+extern "C" {
+
+int marnoldi_set_allocator(marnoldi_alloc_fn alloc, marnoldi_free_fn free_fn, void *user)
+{
+    if ((alloc == nullptr) != (free_fn == nullptr)) return MARNOLDI_EINVAL;
+    g_alloc = alloc;
+    g_free = free_fn;
+    g_user = user;
+    return MARNOLDI_OK;
+}
+
+int marnoldi_kernel_kinds(void) { return KK_NKINDS; }
+
+const char *marnoldi_last_error(const marnoldi_ctx *ctx)
+{
+    return ctx ? ctx->err.c_str() : g_setup_err.c_str();
+}
+
+void marnoldi_destroy(marnoldi_ctx *c)
+{
+    if (!c) return;
+    cudaStreamSynchronize(c->stream);
+    free_state(c);
+    if (c->ws) dfree(c, c->ws, c->ws_bytes);
+    for (auto &p : c->owned) dfree(c, p.first, p.second);
+    if (c->h_out) cudaFreeHost(c->h_out);
+    for (auto &p : c->pending) {
+        c->events.push_back(p.second.first);
+        c->events.push_back(p.second.second);
+    }
+    for (auto e : c->events) cudaEventDestroy(e);
+    cudaStreamSynchronize(c->stream);
+    cudaGetLastError();
+    delete c;
+}
+
+int marnoldi_setup(marnoldi_ctx **out, int64_t n_block_rows, const int64_t *row_ptr,
+                   const int32_t *col_idx, const double *H_vals, const double *S_vals,
+                   const uint8_t *orbital_mask, const double *positions, const double *box,
+                   int precision, void *cuda_stream)
+{
+    g_setup_err.clear();
+    if (!out) return fail(nullptr, MARNOLDI_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (n_block_rows < 1) return fail(nullptr, MARNOLDI_EINVAL, "n_block_rows must be >= 1");
+    if (!row_ptr || !col_idx || !H_vals || !S_vals) return fail(nullptr, MARNOLDI_EINVAL, "NULL matrix array");
+    if (precision != MARNOLDI_FP64 && precision != MARNOLDI_MIXED)
+        return fail(nullptr, MARNOLDI_EINVAL, "unknown precision %d", precision);
+    if ((positions == nullptr) != (box == nullptr))
+        return fail(nullptr, MARNOLDI_EINVAL, "positions and box must be given together");
+    if (n_block_rows > (int64_t)1 << 30) return fail(nullptr, MARNOLDI_EINVAL, "too many block rows");
+    const int64_t nnzb = row_ptr[n_block_rows];
+    if (nnzb < n_block_rows || nnzb > ((int64_t)1 << 31) - 1)
+        return fail(nullptr, MARNOLDI_EINVAL, "row_ptr[n_block_rows] = %lld is not a valid block count", (long long)nnzb);
+
+    marnoldi_ctx *c = new marnoldi_ctx();
+    c->prec = precision;
+    c->nbr = n_block_rows;
+    c->nnzb = nnzb;
+    c->m = 4 * n_block_rows;
+    c->stream = (cudaStream_t)cuda_stream;
+    c->alloc = g_alloc;
+    c->free_fn = g_free;
+    c->user = g_user;
+    c->rp.assign(row_ptr, row_ptr + n_block_rows + 1);
+    c->ci.assign(col_idx, col_idx + nnzb);
+    if (orbital_mask) {
+        c->mask.assign(orbital_mask, orbital_mask + c->m);
+        for (auto v : c->mask)
+            if (v > 1) { delete c; return fail(nullptr, MARNOLDI_EINVAL, "orbital_mask values must be 0 or 1"); }
+    }
+    int rc = validate_structure(c, H_vals, S_vals);
+    if (rc != MARNOLDI_OK) { delete c; return rc; }
+    // transpose map: block (I, J) at k -> index of block (J, I)
+    std::vector<int64_t> tmap(nnzb);
+    for (int64_t I = 0; I < n_block_rows; ++I)
+        for (int64_t k = c->rp[I]; k < c->rp[I + 1]; ++k) {
+            const int64_t J = c->ci[k];
+            const int32_t *b0 = c->ci.data() + c->rp[J], *b1 = c->ci.data() + c->rp[J + 1];
+            tmap[k] = c->rp[J] + (std::lower_bound(b0, b1, (int32_t)I) - b0);
+        }
+    if (positions) {
+        c->pos.assign(positions, positions + 3 * n_block_rows);
+        c->box.assign(box, box + 3);
+    }
+    std::vector<double> sdiag(c->m, 1.0);
+    for (int64_t I = 0; I < n_block_rows; ++I)
+        for (int64_t k = c->rp[I]; k < c->rp[I + 1]; ++k)
+            if (c->ci[k] == I)
+                for (int a = 0; a < 4; ++a) sdiag[4 * I + a] = S_vals[16 * k + 5 * a];
+
+    // ---- device upload
+    int64_t *drp = nullptr, *dtm = nullptr;
+    int32_t *dci = nullptr;
+    double *dH = nullptr, *dS = nullptr, *dsd = nullptr;
+    if ((rc = dupload(c, &drp, c->rp.data(), c->rp.size(), "row_ptr")) ||
+        (rc = dupload(c, &dci, c->ci.data(), c->ci.size(), "col_idx")) ||
+        (rc = dupload(c, &dH, H_vals, (size_t)16 * nnzb, "H")) ||
+        (rc = dupload(c, &dS, S_vals, (size_t)16 * nnzb, "S")) ||
+        (rc = dupload(c, &dsd, sdiag.data(), sdiag.size(), "diag S")) ||
+        (rc = dupload(c, &dtm, tmap.data(), tmap.size(), "transpose map"))) {
+        g_setup_err = c->err;
+        marnoldi_destroy(c);
+        return rc;
+    }
+    c->A.nbr = n_block_rows;
+    c->A.nnzb = nnzb;
+    c->A.rp = drp;
+    c->A.ci = dci;
+    c->A.Hd = dH;
+    c->A.Sd = dS;
+    c->A.sdiag = dsd;
+    c->A.tmap = dtm;
+    if (precision == MARNOLDI_MIXED) {
+        std::vector<float> hf(16 * nnzb), sf(16 * nnzb);
+        for (int64_t k = 0; k < 16 * nnzb; ++k) {
+            hf[k] = (float)H_vals[k];
+            sf[k] = (float)S_vals[k];
+        }
+        float *dHf = nullptr, *dSf = nullptr;
+        if ((rc = dupload(c, &dHf, hf.data(), hf.size(), "H fp32")) ||
+            (rc = dupload(c, &dSf, sf.data(), sf.size(), "S fp32"))) {
+            g_setup_err = c->err;
+            marnoldi_destroy(c);
+            return rc;
+        }
+        c->A.Hf = dHf;
+        c->A.Sf = dSf;
+    }
+    // reduction scratch
+    void *p = dalloc(c, (2 * kReduceBlocks + 2) * sizeof(double) + 16);
+    if (!p) { g_setup_err = "device allocation failed"; marnoldi_destroy(c); return MARNOLDI_ENOMEM; }
+    c->owned.push_back({p, (2 * kReduceBlocks + 2) * sizeof(double) + 16});
+    c->d_partial = (double *)p;
+    c->d_out = c->d_partial + 2 * kReduceBlocks;
+    c->d_ticket = (unsigned *)(c->d_out + 2);
+    cudaError_t e = cudaMemsetAsync(p, 0, (2 * kReduceBlocks + 2) * sizeof(double) + 16, c->stream);
+    if (e == cudaSuccess) e = cudaMallocHost(&c->h_out, 4 * sizeof(double));
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+        fail_cuda(c, e, "setup");
+        g_setup_err = c->err;
+        marnoldi_destroy(c);
+        return MARNOLDI_ECUDA;
+    }
+    *out = c;
+    return MARNOLDI_OK;
+}
+
+int marnoldi_set_batch(marnoldi_ctx *c, int64_t batch_columns)
+{
+    if (!c || batch_columns < 0) return MARNOLDI_EINVAL;
+    c->batch_override = batch_columns;
+    return MARNOLDI_OK;
+}
+
+int marnoldi_set_profiling(marnoldi_ctx *c, int enable)
+{
+    if (!c) return MARNOLDI_EINVAL;
+    c->profile = enable ? 1 : 0;
+    return MARNOLDI_OK;
+}
+
+int marnoldi_kernel_stats(marnoldi_ctx *c, int kind, const char **name, int64_t *launches,
+                          double *ms, int reset)
+{
+    if (!c || kind < 0 || kind >= KK_NKINDS) return MARNOLDI_EINVAL;
+    if (name) *name = kernel_name(kind);
+    if (launches) *launches = c->launches[kind];
+    if (ms) *ms = c->ms[kind];
+    if (reset) {
+        c->launches[kind] = 0;
+        c->ms[kind] = 0.0;
+    }
+    return MARNOLDI_OK;
+}
+
+int marnoldi_solved_shape(marnoldi_ctx *c, int64_t *ncols, int *nu)
+{
+    if (!c) return MARNOLDI_EINVAL;
+    if (!c->solved) return fail(c, MARNOLDI_ESTATE, "no solve yet");
+    if (ncols) *ncols = c->ncols;
+    if (nu) *nu = c->nu;
+    return MARNOLDI_OK;
+}
+
+static int count_at(marnoldi_ctx *c, double mu, double kT, double *N, double *E)
+{
+    int rc = launch(c, KK_COUNT, [&] {
+        return launch_count(c->st, mu, kT, c->d_partial, c->d_ticket, c->d_out, c->stream);
+    });
+    if (rc) return rc;
+    cudaError_t e = cudaMemcpyAsync(c->h_out, c->d_out, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+    if (e != cudaSuccess) return fail_cuda(c, e, "count read-back");
+    if ((rc = sync(c, "count"))) return rc;
+    *N = c->h_out[0];
+    *E = c->h_out[1];
+    return MARNOLDI_OK;
+}
+
+int marnoldi_solve(marnoldi_ctx *c, const int64_t *columns, int64_t ncols, int nu,
+                   int region_atoms, double electron_count, double kT, const double *mu_fixed)
+{
+    if (!c) return MARNOLDI_EINVAL;
+    c->err.clear();
+    c->solved = false;   // a failed solve leaves no stale results
+    if (region_atoms != 0)
+        return fail(c, MARNOLDI_EINVAL, "regional mode (region_atoms > 0) is not available in this build");
+    if (c->m > kMaxGlobalM)
+        return fail(c, MARNOLDI_EINVAL, "global mode supports M <= %lld (got %lld)", (long long)kMaxGlobalM, (long long)c->m);
+    if (!(kT > 0.0) || !std::isfinite(kT)) return fail(c, MARNOLDI_EINVAL, "kT must be positive and finite");
+    if (mu_fixed && !std::isfinite(*mu_fixed)) return fail(c, MARNOLDI_EINVAL, "mu_fixed must be finite");
+    if (!mu_fixed && !(electron_count > 0.0 && std::isfinite(electron_count)))
+        return fail(c, MARNOLDI_EINVAL, "electron_count must be positive and finite");
+    // column list
+    std::vector<int64_t> cols;
+    if (!columns) {
+        if (ncols >= 0) return fail(c, MARNOLDI_EINVAL, "columns is NULL but ncols >= 0");
+        for (int64_t j = 0; j < c->m; ++j)
+            if (c->mask.empty() || c->mask[j]) cols.push_back(j);
+    } else {
+        if (ncols < 1) return fail(c, MARNOLDI_EINVAL, "ncols must be >= 1");
+        cols.assign(columns, columns + ncols);
+        std::vector<int64_t> sorted = cols;
+        std::sort(sorted.begin(), sorted.end());
+        for (size_t q = 0; q < sorted.size(); ++q) {
+            if (sorted[q] < 0 || sorted[q] >= c->m)
+                return fail(c, MARNOLDI_EINVAL, "column %lld out of range", (long long)sorted[q]);
+            if (q && sorted[q] == sorted[q - 1])
+                return fail(c, MARNOLDI_EINVAL, "column %lld requested twice", (long long)sorted[q]);
+            if (!c->mask.empty() && !c->mask[sorted[q]])
+                return fail(c, MARNOLDI_EINVAL, "column %lld is a padding orbital", (long long)sorted[q]);
+        }
+    }
+    if (cols.empty()) return fail(c, MARNOLDI_EINVAL, "no columns to solve");
+    int64_t m_real = c->mask.empty() ? c->m : 0;
+    if (!c->mask.empty())
+        for (auto v : c->mask) m_real += v;
+    if (nu < 1 || nu > kMaxNu || nu > m_real)
+        return fail(c, MARNOLDI_EINVAL, "nu = %d outside [1, min(M_real = %lld, %d)]", nu, (long long)m_real, kMaxNu);
+
+    free_state(c);
+    const int64_t nc = (int64_t)cols.size();
+    // per-column state: cols | p_off | nu_eff | eig_status | eps w t | P
+    std::vector<int64_t> p_off(nc);
+    int64_t prow = 0;
+    for (int64_t q = 0; q < nc; ++q) {
+        p_off[q] = prow * nu;
+        const int64_t J = cols[q] >> 2;
+        prow += 4 * (c->rp[J + 1] - c->rp[J]);
+    }
+    auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    const size_t o_cols = 0, o_poff = o_cols + al(nc * 8), o_nue = o_poff + al(nc * 8),
+                 o_est = o_nue + al(nc * 4), o_eps = o_est + al(nc * 4),
+                 o_w = o_eps + al((size_t)nc * nu * 8), o_t = o_w + al((size_t)nc * nu * 8),
+                 o_P = o_t + al((size_t)nc * nu * 8), total = o_P + al((size_t)prow * nu * 8);
+    c->state = dalloc(c, total);
+    if (!c->state) return fail(c, MARNOLDI_ENOMEM, "device allocation of %zu bytes for column state failed", total);
+    c->state_bytes = total;
+    char *sb = (char *)c->state;
+    c->d_cols = (int64_t *)(sb + o_cols);
+    c->st.ncols = nc;
+    c->st.nu = nu;
+    c->st.cols = c->d_cols;
+    c->st.p_off = (const int64_t *)(sb + o_poff);
+    c->st.nu_eff = (int *)(sb + o_nue);
+    c->st.eig_status = (int *)(sb + o_est);
+    c->st.eps = (double *)(sb + o_eps);
+    c->st.w = (double *)(sb + o_w);
+    c->st.t = (double *)(sb + o_t);
+    c->st.P = (double *)(sb + o_P);
+    cudaError_t e = cudaMemcpyAsync(c->d_cols, cols.data(), nc * 8, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync((void *)c->st.p_off, p_off.data(), nc * 8, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->st.eig_status, 0, nc * 4, c->stream);
+    if (e != cudaSuccess) return fail_cuda(c, e, "column state upload");
+
+    // batch workspace
+    const ColumnShape shape = column_shape(c->m);
+    const size_t vs = c->prec == 0 ? 8 : 4;
+    const size_t per_col = al((size_t)2 * nu * shape.m_pad * vs) + (size_t)3 * shape.m_pad * vs +
+                           (size_t)nu * nu * 8 + 64;
+    int64_t B = c->batch_override;
+    if (B <= 0) {
+        size_t freeb = 0, totb = 0;
+        if (cudaMemGetInfo(&freeb, &totb) != cudaSuccess) { cudaGetLastError(); freeb = (size_t)8 << 30; }
+        const size_t budget = std::min<size_t>(freeb / 2, (size_t)48 << 30);
+        B = std::max<int64_t>(1, (int64_t)(budget / per_col));
+    }
+    B = std::min<int64_t>(B, nc);
+    B = std::min<int64_t>(B, 65535 * 32);
+    c->last_batch = B;
+    const size_t oK = 0, oSK = oK + al((size_t)B * nu * shape.m_pad * vs),
+                 oU = oSK + al((size_t)B * nu * shape.m_pad * vs), oW = oU + al((size_t)B * shape.m_pad * vs),
+                 oSW = oW + al((size_t)B * shape.m_pad * vs), oH = oSW + al((size_t)B * shape.m_pad * vs),
+                 oC = oH + al((size_t)B * nu * nu * 8), oS = oC + al((size_t)B * 8),
+                 oN = oS + al((size_t)B * 4), wtot = oN + al((size_t)B * 4);
+    if (c->ws_bytes < wtot) {
+        if (c->ws) dfree(c, c->ws, c->ws_bytes);
+        c->ws = dalloc(c, wtot);
+        c->ws_bytes = c->ws ? wtot : 0;
+        if (!c->ws) return fail(c, MARNOLDI_ENOMEM, "device allocation of %zu bytes for the batch workspace failed", wtot);
+    }
+    // zero once: padding rows of the vectors must stay zero
+    e = cudaMemsetAsync(c->ws, 0, wtot, c->stream);
+    if (e != cudaSuccess) return fail_cuda(c, e, "workspace clear");
+    char *wb = (char *)c->ws;
+    KrylovBatch kb{};
+    kb.prec = c->prec;
+    kb.nu = nu;
+    kb.m = c->m;
+    kb.shape = shape;
+    kb.K = wb + oK;
+    kb.SK = wb + oSK;
+    kb.U = wb + oU;
+    kb.W = wb + oW;
+    kb.SW = wb + oSW;
+    kb.Hsub = (double *)(wb + oH);
+    kb.cn2 = (double *)(wb + oC);
+    kb.status = (int *)(wb + oS);
+    kb.nu_eff = (int *)(wb + oN);
+    const double tau = c->prec == 0 ? kTauFp64 : kTauMixed;
+    const int64_t mp = shape.m_pad;
+    int rc = MARNOLDI_OK;
+    for (int64_t start = 0; start < nc; start += B) {
+        kb.nb = (int)std::min<int64_t>(B, nc - start);
+        kb.cols = c->d_cols + start;
+        if ((rc = launch(c, KK_INIT, [&] { return launch_init(c->A, kb, c->stream); }))) return rc;
+        for (int n = 0; n < nu; ++n) {
+            const char *Kn = (const char *)kb.K + (size_t)n * mp * vs;
+            if ((rc = launch(c, KK_SPMM_H, [&] {
+                     return launch_spmm(c->A, 0, kb, Kn, (int64_t)nu * mp, kb.U, mp, c->stream);
+                 })))
+                return rc;
+            const int need_w = n + 1 < nu;
+            if ((rc = launch(c, KK_MGS, [&] { return launch_mgs(kb, n, need_w, c->stream); }))) return rc;
+            if (!need_w) break;
+            if ((rc = launch(c, KK_SPMM_S, [&] {
+                     return launch_spmm(c->A, 1, kb, kb.W, mp, kb.SW, mp, c->stream);
+                 })))
+                return rc;
+            if ((rc = launch(c, KK_NORMALIZE, [&] { return launch_normalize(kb, n, tau, c->stream); })))
+                return rc;
+        }
+        if ((rc = launch(c, KK_EIG, [&] { return launch_eig(c->A, kb, c->st, start, c->stream); }))) return rc;
+    }
+    // ---- Fermi level
+    double mu = 0.0, N = 0.0, E = 0.0;
+    if (mu_fixed) {
+        mu = *mu_fixed;
+        if ((rc = count_at(c, mu, kT, &N, &E))) return rc;
+    } else {
+        if ((rc = launch(c, KK_MINMAX, [&] {
+                 return launch_minmax(c->st, c->d_partial, c->d_ticket, c->d_out, c->stream);
+             })))
+            return rc;
+        e = cudaMemcpyAsync(c->h_out, c->d_out, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+        if (e != cudaSuccess) return fail_cuda(c, e, "minmax read-back");
+        if ((rc = sync(c, "minmax"))) return rc;
+        double lo = c->h_out[0] - 40.0 * kT, hi = c->h_out[1] + 40.0 * kT;
+        double Nlo, Nhi;
+        if ((rc = count_at(c, lo, kT, &Nlo, &E)) || (rc = count_at(c, hi, kT, &Nhi, &E))) return rc;
+        if (!(Nlo <= electron_count && electron_count <= Nhi))
+            return fail(c, MARNOLDI_ENOCONV, "electron count %.6g outside [N(lo) = %.6g, N(hi) = %.6g]",
+                        electron_count, Nlo, Nhi);
+        for (int it = 1; it <= kBisectMaxit; ++it) {
+            mu = 0.5 * (lo + hi);
+            if ((rc = count_at(c, mu, kT, &N, &E))) return rc;
+            if (std::fabs(N - electron_count) <= kBisectRtol * electron_count) break;
+            if (N < electron_count) lo = mu; else hi = mu;
+        }
+    }
+    if ((rc = sync(c, "solve"))) return rc;
+    std::vector<int> est(nc);
+    e = cudaMemcpy(est.data(), c->st.eig_status, nc * 4, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return fail_cuda(c, e, "status read-back");
+    c->ncols = nc;
+    c->nu = nu;
+    c->cols = std::move(cols);
+    c->mu = mu;
+    c->N = N;
+    c->E = E;
+    c->kT = kT;
+    c->solved = true;
+    for (int64_t q = 0; q < nc; ++q) {
+        if (est[q] & 2)
+            return fail(c, MARNOLDI_ENOTSPD, "column %lld: a Krylov vector has non-positive S norm", (long long)c->cols[q]);
+        if (est[q] & 1)
+            return fail(c, MARNOLDI_ENOCONV, "column %lld: QL iteration did not converge", (long long)c->cols[q]);
+    }
+    return MARNOLDI_OK;
+}
+
+int marnoldi_density_device(marnoldi_ctx *c, double *rho, double *rhoE)
+{
+    if (!c || !rho || !rhoE) return MARNOLDI_EINVAL;
+    if (!c->solved) return fail(c, MARNOLDI_ESTATE, "density requested before a successful solve");
+    const size_t bytes = (size_t)c->nnzb * 16 * sizeof(double);
+    cudaError_t e = cudaMemsetAsync(rho, 0, bytes, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(rhoE, 0, bytes, c->stream);
+    if (e != cudaSuccess) return fail_cuda(c, e, "density clear");
+    return launch(c, KK_DENSITY, [&] {
+        return launch_density(c->A, c->st, c->mu, c->kT, rho, rhoE, c->stream);
+    });
+}
+
+int marnoldi_density(marnoldi_ctx *c, double *rho, double *rhoE)
+{
+    if (!c || !rho || !rhoE) return MARNOLDI_EINVAL;
+    if (!c->solved) return fail(c, MARNOLDI_ESTATE, "density requested before a successful solve");
+    const size_t bytes = (size_t)c->nnzb * 16 * sizeof(double);
+    double *d = (double *)dalloc(c, 2 * bytes);
+    if (!d) return fail(c, MARNOLDI_ENOMEM, "device allocation for density output failed");
+    int rc = marnoldi_density_device(c, d, d + c->nnzb * 16);
+    cudaError_t e = cudaSuccess;
+    if (!rc) {
+        e = cudaMemcpyAsync(rho, d, bytes, cudaMemcpyDeviceToHost, c->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(rhoE, d + c->nnzb * 16, bytes, cudaMemcpyDeviceToHost, c->stream);
+    }
+    dfree(c, d, 2 * bytes);
+    if (!rc && e != cudaSuccess) rc = fail_cuda(c, e, "density read-back");
+    int rs = sync(c, "density");
+    return rc ? rc : rs;
+}
+
+int marnoldi_energy(marnoldi_ctx *c, double *band_energy, double *mu, double *electron_count_out)
+{
+    if (!c) return MARNOLDI_EINVAL;
+    if (!c->solved) return fail(c, MARNOLDI_ESTATE, "energy requested before a successful solve");
+    if (band_energy) *band_energy = c->E;
+    if (mu) *mu = c->mu;
+    if (electron_count_out) *electron_count_out = c->N;
+    return MARNOLDI_OK;
+}
+
+int marnoldi_green(marnoldi_ctx *c, const double *z, int nz, double *G)
+{
+    if (!c || (nz > 0 && (!z || !G)) || nz < 0) return MARNOLDI_EINVAL;
+    if (!c->solved) return fail(c, MARNOLDI_ESTATE, "green requested before a successful solve");
+    const size_t per = (size_t)c->nnzb * 16 * 2;
+    double *d = (double *)dalloc(c, per * sizeof(double));
+    if (!d) return fail(c, MARNOLDI_ENOMEM, "device allocation for green output failed");
+    int rc = MARNOLDI_OK;
+    for (int q = 0; q < nz && !rc; ++q) {
+        if (!std::isfinite(z[2 * q]) || !std::isfinite(z[2 * q + 1]) || z[2 * q + 1] == 0.0) {
+            rc = fail(c, MARNOLDI_EINVAL, "shift %d must be finite with a nonzero imaginary part", q);
+            break;
+        }
+        cudaError_t e = cudaMemsetAsync(d, 0, per * sizeof(double), c->stream);
+        if (e != cudaSuccess) { rc = fail_cuda(c, e, "green clear"); break; }
+        rc = launch(c, KK_GREEN, [&] {
+            return launch_green(c->A, c->st, z[2 * q], z[2 * q + 1], d, c->stream);
+        });
+        if (rc) break;
+        e = cudaMemcpyAsync(G + q * per, d, per * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+        if (e != cudaSuccess) rc = fail_cuda(c, e, "green read-back");
+    }
+    dfree(c, d, per * sizeof(double));
+    int rs = sync(c, "green");
+    return rc ? rc : rs;
+}
+
+int marnoldi_column_stats(marnoldi_ctx *c, int32_t *nu_eff, double *eps, double *w)
+{
+    if (!c) return MARNOLDI_EINVAL;
+    if (!c->solved) return fail(c, MARNOLDI_ESTATE, "column stats requested before a successful solve");
+    int rc = sync(c, "column stats");
+    if (rc) return rc;
+    cudaError_t e = cudaSuccess;
+    const size_t n = (size_t)c->ncols * c->nu;
+    if (nu_eff) e = cudaMemcpy(nu_eff, c->st.nu_eff, c->ncols * 4, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && eps) e = cudaMemcpy(eps, c->st.eps, n * 8, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && w) e = cudaMemcpy(w, c->st.w, n * 8, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return fail_cuda(c, e, "column stats read-back");
+    return MARNOLDI_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,107 @@
+// Internal declarations shared by the libmarnoldi translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+
+namespace marnoldi {
+
+// Kernel kinds, for launch counting and optional event timing.
+enum KernelKind {
+    KK_INIT = 0,
+    KK_SPMM_H,
+    KK_MGS,
+    KK_SPMM_S,
+    KK_NORMALIZE,
+    KK_EIG,
+    KK_MINMAX,
+    KK_COUNT,
+    KK_DENSITY,
+    KK_GREEN,
+    KK_NKINDS
+};
+
+const char *kernel_name(int kind);
+
+// Largest subspace dimension of the shared-memory eigensolver.
+constexpr int kMaxNu = 110;
+// Largest Krylov-vector length of global mode (one CTA holds a column's vector).
+constexpr int64_t kMaxGlobalM = 16384;
+
+// Threads per CTA and values per thread for a column-per-CTA kernel on vectors
+// of length m: T * VPT = m_pad >= m, T a multiple of 32, T <= 1024.
+struct ColumnShape {
+    int vpt;
+    int threads;
+    int64_t m_pad;
+};
+ColumnShape column_shape(int64_t m);
+
+// ---------------------------------------------------------------- Krylov build
+// All pointers are device pointers.  Batch layout (c = batch column):
+//   K[c][i][r], SK[c][i][r] at ((c * nu) + i) * m_pad + r  (i < nu)
+//   U[c][r], W[c][r], SW[c][r] at c * m_pad + r
+//   Hsub[c][i][l] at (c * nu + i) * nu + l (double)
+// status[c]: 0 active, 1 stopped (breakdown), 2 non-positive S norm.
+struct KrylovBatch {
+    int prec;             // 0 FP64, 1 mixed (vectors float)
+    int nb;               // columns in this batch
+    int nu;
+    int64_t m;            // vector length
+    ColumnShape shape;
+    void *K, *SK, *U, *W, *SW;
+    double *Hsub;
+    double *cn2;          // per column: sum_i (c1_i + c2_i)^2 of the last MGS
+    int *status;
+    int *nu_eff;
+    const int64_t *cols;  // global orbital column of each batch column
+};
+
+struct DeviceMatrix {
+    int64_t nbr, nnzb;
+    const int64_t *rp;
+    const int32_t *ci;
+    const double *Hd, *Sd;   // FP64 values
+    const float *Hf, *Sf;    // FP32 copies (mixed precision), else null
+    const double *sdiag;     // S_jj, length 4 nbr
+    const int64_t *tmap;     // block (J, I) -> index of block (I, J)
+};
+
+cudaError_t launch_init(const DeviceMatrix &A, const KrylovBatch &b, cudaStream_t s);
+cudaError_t launch_spmm(const DeviceMatrix &A, int which /*0 H, 1 S*/, const KrylovBatch &b,
+                        const void *X, int64_t ldx, void *Y, int64_t ldy, cudaStream_t s);
+cudaError_t launch_mgs(const KrylovBatch &b, int n, int need_w, cudaStream_t s);
+cudaError_t launch_normalize(const KrylovBatch &b, int n, double tau, cudaStream_t s);
+
+// ---------------------------------------------------------------- subspace eigensolve
+// Per solved column c (global index col0 + batch column):
+//   eps/w/t at c * nu (zero past nu_eff); P rows at p_off[c] (n_pat x nu, row-major).
+struct ColumnState {
+    int64_t ncols;
+    int nu;
+    const int64_t *cols;
+    int *nu_eff;
+    double *eps, *w, *t, *P;
+    const int64_t *p_off;
+    int *eig_status;     // 0 ok, 1 QL did not converge
+};
+
+cudaError_t launch_eig(const DeviceMatrix &A, const KrylovBatch &b, const ColumnState &st,
+                       int64_t col0, cudaStream_t s);
+
+// ---------------------------------------------------------------- Fermi level, outputs
+// Deterministic two-level reductions; `partial` holds 2 * kReduceBlocks doubles,
+// `ticket` one zero-initialised unsigned int, `out` two doubles.
+constexpr int kReduceBlocks = 304;
+cudaError_t launch_minmax(const ColumnState &st, double *partial, unsigned *ticket, double *out,
+                          cudaStream_t s);
+cudaError_t launch_count(const ColumnState &st, double mu, double kT, double *partial,
+                         unsigned *ticket, double *out, cudaStream_t s);
+cudaError_t launch_density(const DeviceMatrix &A, const ColumnState &st, double mu, double kT,
+                           double *rho, double *rhoE, cudaStream_t s);
+cudaError_t launch_green(const DeviceMatrix &A, const ColumnState &st, double zr, double zi,
+                         double *G, cudaStream_t s);
+
+}  // namespace marnoldi

@@ -1,0 +1,331 @@
+"""Python binding of libmarnoldi (include/marnoldi.h): argument marshalling only.
+
+Every function keeps the C name and forwards to the library through ctypes;
+the work runs in the library's CUDA kernels.  There is no fallback: if the
+library is not built or cannot be loaded, the first call raises.
+
+PyTorch is used only as plumbing: the CUDA stream the library issues its work
+on (``torch.cuda.current_stream()`` unless one is given) and, through
+``marnoldi_set_allocator``, the caching allocator that backs the library's
+device memory.
+"""
+
+from __future__ import annotations
+
+import atexit
+import ctypes as C
+import os
+import weakref
+
+import numpy as np
+
+from . import build as _build
+
+MARNOLDI_OK = 0
+MARNOLDI_EINVAL = -1
+MARNOLDI_ENOTSPD = -2
+MARNOLDI_ENOMEM = -3
+MARNOLDI_ECUDA = -4
+MARNOLDI_ETIMEOUT = -5
+MARNOLDI_ESTATE = -6
+MARNOLDI_ENOCONV = -7
+MARNOLDI_FP64 = 0
+MARNOLDI_MIXED = 1
+
+STATUS_NAMES = {0: "OK", -1: "EINVAL", -2: "ENOTSPD", -3: "ENOMEM", -4: "ECUDA", -5: "ETIMEOUT",
+                -6: "ESTATE", -7: "ENOCONV"}
+
+_LIB = None
+_ALLOC_CB = None     # keep the ctypes callbacks alive
+_FREE_CB = None
+_KEEP_ALIVE: list = []
+
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+
+
+class MarnoldiError(RuntimeError):
+    def __init__(self, code: int, message: str):
+        super().__init__(f"{STATUS_NAMES.get(code, code)}: {message}")
+        self.code = code
+
+
+def library_path() -> str:
+    return _build.lib_path()
+
+
+def load(path: str | None = None):
+    """Load libmarnoldi (building it first when MARNOLDI_BUILD=1)."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    p = path or library_path()
+    if not os.path.exists(p):
+        if os.environ.get("MARNOLDI_BUILD", "0") == "1":
+            p = _build.build()
+        else:
+            raise RuntimeError(
+                f"libmarnoldi is not built ({p} missing); run paper_1307_3218_gb300.build.build() "
+                "or __graft_entry__.build()")
+    L = C.CDLL(p)
+    P, i64, i32, d = C.c_void_p, C.c_int64, C.c_int, C.c_double
+    sig = {
+        "marnoldi_set_allocator": (i32, [ALLOC_FN, FREE_FN, P]),
+        "marnoldi_setup": (i32, [C.POINTER(P), i64, P, P, P, P, P, P, P, i32, P]),
+        "marnoldi_solve": (i32, [P, P, i64, i32, i32, d, d, P]),
+        "marnoldi_density": (i32, [P, P, P]),
+        "marnoldi_density_device": (i32, [P, P, P]),
+        "marnoldi_energy": (i32, [P, P, P, P]),
+        "marnoldi_green": (i32, [P, P, i32, P]),
+        "marnoldi_column_stats": (i32, [P, P, P, P]),
+        "marnoldi_solved_shape": (i32, [P, P, P]),
+        "marnoldi_set_batch": (i32, [P, i64]),
+        "marnoldi_set_profiling": (i32, [P, i32]),
+        "marnoldi_kernel_kinds": (i32, []),
+        "marnoldi_kernel_stats": (i32, [P, i32, C.POINTER(C.c_char_p), C.POINTER(i64),
+                                        C.POINTER(d), i32]),
+        "marnoldi_last_error": (C.c_char_p, [P]),
+        "marnoldi_destroy": (None, [P]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _LIB = L
+    return L
+
+
+def _check(rc: int, ctx=None):
+    if rc != MARNOLDI_OK:
+        msg = load().marnoldi_last_error(ctx.handle if ctx is not None else None)
+        raise MarnoldiError(rc, msg.decode() if msg else "")
+
+
+def _ptr(a) -> C.c_void_p:
+    if a is None:
+        return None
+    if isinstance(a, int):
+        return C.c_void_p(a)
+    if hasattr(a, "data_ptr"):
+        return C.c_void_p(a.data_ptr())
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def _current_stream():
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return torch.cuda.current_stream().cuda_stream
+    except Exception:
+        pass
+    return 0
+
+
+_LIVE = weakref.WeakSet()
+
+
+class Context:
+    """Owns one ``marnoldi_ctx``; destroyed with the object or by marnoldi_destroy."""
+
+    def __init__(self, handle: int, nnzb: int, n_block_rows: int, stream: int):
+        self.handle = C.c_void_p(handle)
+        self.nnzb = nnzb
+        self.n_block_rows = n_block_rows
+        self.stream = stream
+        _LIVE.add(self)
+
+    def __del__(self):
+        try:
+            marnoldi_destroy(self)
+        except Exception:
+            pass
+
+
+@atexit.register
+def _destroy_all():
+    # free device memory while PyTorch (which may back it) is still alive
+    for ctx in list(_LIVE):
+        try:
+            marnoldi_destroy(ctx)
+        except Exception:
+            pass
+
+
+def marnoldi_set_allocator(alloc=None, free=None, user=None) -> None:
+    """Install a device allocator (Python callables) or restore the default (None, None)."""
+    global _ALLOC_CB, _FREE_CB
+    L = load()
+    if alloc is None:
+        _ALLOC_CB = ALLOC_FN()
+        _FREE_CB = FREE_FN()
+        _check(L.marnoldi_set_allocator(C.cast(None, ALLOC_FN), C.cast(None, FREE_FN), None))
+        return
+    _ALLOC_CB = ALLOC_FN(alloc)
+    _FREE_CB = FREE_FN(free)
+    # contexts keep the hooks they were created with: never let a callback die
+    _KEEP_ALIVE.append((_ALLOC_CB, _FREE_CB))
+    _check(L.marnoldi_set_allocator(_ALLOC_CB, _FREE_CB, user))
+
+
+def use_torch_allocator() -> None:
+    """Back the library's device memory with PyTorch's caching allocator."""
+    import torch
+
+    def _alloc(nbytes, stream, user):
+        try:
+            return torch.cuda.caching_allocator_alloc(int(nbytes), torch.cuda.current_device(),
+                                                      int(stream or 0))
+        except Exception:
+            return None
+
+    def _free(ptr, nbytes, stream, user):
+        try:
+            torch.cuda.caching_allocator_delete(int(ptr))
+        except Exception:
+            pass
+
+    marnoldi_set_allocator(_alloc, _free)
+
+
+_ALLOCATOR_CHOSEN = False
+
+
+def _default_allocator():
+    """On first setup, route device memory through PyTorch's caching allocator
+    (MARNOLDI_ALLOCATOR=native keeps the library's cudaMallocAsync pool)."""
+    global _ALLOCATOR_CHOSEN
+    if _ALLOCATOR_CHOSEN:
+        return
+    _ALLOCATOR_CHOSEN = True
+    if os.environ.get("MARNOLDI_ALLOCATOR", "torch") == "native":
+        return
+    try:
+        import torch
+        ok = torch.cuda.is_available()
+    except Exception:
+        ok = False
+    if ok:
+        use_torch_allocator()
+
+
+def marnoldi_setup(n_block_rows: int, row_ptr, col_idx, H_vals, S_vals, orbital_mask=None,
+                   positions=None, box=None, precision: int = MARNOLDI_FP64,
+                   stream: int | None = None) -> Context:
+    L = load()
+    _default_allocator()
+    rp = np.ascontiguousarray(row_ptr, dtype=np.int64)
+    ci = np.ascontiguousarray(col_idx, dtype=np.int32)
+    H = np.ascontiguousarray(H_vals, dtype=np.float64)
+    S = np.ascontiguousarray(S_vals, dtype=np.float64)
+    mask = None if orbital_mask is None else np.ascontiguousarray(orbital_mask, dtype=np.uint8)
+    pos = None if positions is None else np.ascontiguousarray(positions, dtype=np.float64)
+    bx = None if box is None else np.ascontiguousarray(box, dtype=np.float64)
+    if rp.size != n_block_rows + 1:
+        raise MarnoldiError(MARNOLDI_EINVAL, "row_ptr must have n_block_rows + 1 entries")
+    nnzb = int(rp[-1])
+    if ci.size != nnzb or H.size != 16 * nnzb or S.size != 16 * nnzb:
+        raise MarnoldiError(MARNOLDI_EINVAL, "col_idx / H_vals / S_vals sizes do not match row_ptr")
+    if mask is not None and mask.size != 4 * n_block_rows:
+        raise MarnoldiError(MARNOLDI_EINVAL, "orbital_mask must have 4 n_block_rows entries")
+    st = _current_stream() if stream is None else int(stream)
+    out = C.c_void_p()
+    rc = L.marnoldi_setup(C.byref(out), int(n_block_rows), _ptr(rp), _ptr(ci), _ptr(H), _ptr(S),
+                          _ptr(mask), _ptr(pos), _ptr(bx), int(precision), C.c_void_p(st))
+    _check(rc)
+    return Context(out.value, nnzb, int(n_block_rows), st)
+
+
+def setup_system(sysm, precision: int = MARNOLDI_FP64, stream: int | None = None) -> Context:
+    """marnoldi_setup for a tbsynth.TBSystem-like object."""
+    s = getattr(sysm, "structure", None)
+    return marnoldi_setup(sysm.n_block_rows, sysm.row_ptr, sysm.col_idx, sysm.H, sysm.S,
+                          sysm.orbital_mask, None if s is None else s.positions,
+                          None if s is None else s.box, precision, stream)
+
+
+def marnoldi_solve(ctx: Context, columns=None, nu: int = 30, region_atoms: int = 0,
+                   electron_count: float = 0.0, kT: float = 0.1, mu_fixed: float | None = None):
+    L = load()
+    if columns is None:
+        cp, nc = None, -1
+        cols = None
+    else:
+        cols = np.ascontiguousarray(columns, dtype=np.int64)
+        cp, nc = _ptr(cols), cols.size
+    mu = None if mu_fixed is None else C.byref(C.c_double(float(mu_fixed)))
+    _check(L.marnoldi_solve(ctx.handle, cp, nc, int(nu), int(region_atoms), float(electron_count),
+                            float(kT), mu), ctx)
+
+
+def marnoldi_density(ctx: Context) -> tuple[np.ndarray, np.ndarray]:
+    rho = np.empty((ctx.nnzb, 4, 4))
+    rhoE = np.empty((ctx.nnzb, 4, 4))
+    _check(load().marnoldi_density(ctx.handle, _ptr(rho), _ptr(rhoE)), ctx)
+    return rho, rhoE
+
+
+def marnoldi_density_device(ctx: Context, rho_device, rhoE_device) -> None:
+    _check(load().marnoldi_density_device(ctx.handle, _ptr(rho_device), _ptr(rhoE_device)), ctx)
+
+
+def marnoldi_energy(ctx: Context) -> tuple[float, float, float]:
+    E, mu, N = C.c_double(), C.c_double(), C.c_double()
+    _check(load().marnoldi_energy(ctx.handle, C.byref(E), C.byref(mu), C.byref(N)), ctx)
+    return E.value, mu.value, N.value
+
+
+def marnoldi_green(ctx: Context, zs) -> np.ndarray:
+    z = np.asarray(zs, dtype=np.complex128).reshape(-1)
+    zri = np.ascontiguousarray(np.stack([z.real, z.imag], axis=1).reshape(-1))
+    G = np.empty((z.size, ctx.nnzb, 4, 4), np.complex128)
+    _check(load().marnoldi_green(ctx.handle, _ptr(zri), int(z.size), _ptr(G)), ctx)
+    return G
+
+
+def marnoldi_solved_shape(ctx: Context) -> tuple[int, int]:
+    n, nu = C.c_int64(), C.c_int()
+    _check(load().marnoldi_solved_shape(ctx.handle, C.byref(n), C.byref(nu)), ctx)
+    return n.value, nu.value
+
+
+def marnoldi_column_stats(ctx: Context) -> tuple[np.ndarray, np.ndarray, np.ndarray]:
+    n, nu = marnoldi_solved_shape(ctx)
+    nue = np.empty(n, np.int32)
+    eps = np.empty((n, nu))
+    w = np.empty((n, nu))
+    _check(load().marnoldi_column_stats(ctx.handle, _ptr(nue), _ptr(eps), _ptr(w)), ctx)
+    return nue, eps, w
+
+
+def marnoldi_set_batch(ctx: Context, batch_columns: int) -> None:
+    _check(load().marnoldi_set_batch(ctx.handle, int(batch_columns)), ctx)
+
+
+def marnoldi_set_profiling(ctx: Context, enable: bool) -> None:
+    _check(load().marnoldi_set_profiling(ctx.handle, int(bool(enable))), ctx)
+
+
+def marnoldi_kernel_kinds() -> int:
+    return int(load().marnoldi_kernel_kinds())
+
+
+def marnoldi_kernel_stats(ctx: Context, reset: bool = False) -> dict:
+    L = load()
+    out = {}
+    for k in range(L.marnoldi_kernel_kinds()):
+        name, n, ms = C.c_char_p(), C.c_int64(), C.c_double()
+        _check(L.marnoldi_kernel_stats(ctx.handle, k, C.byref(name), C.byref(n), C.byref(ms),
+                                       int(bool(reset))), ctx)
+        out[name.value.decode()] = (n.value, ms.value)
+    return out
+
+
+def marnoldi_last_error(ctx: Context | None = None) -> str:
+    r = load().marnoldi_last_error(None if ctx is None else ctx.handle)
+    return r.decode() if r else ""
+
+
+def marnoldi_destroy(ctx: Context) -> None:
+    if ctx is not None and ctx.handle is not None and ctx.handle.value:
+        load().marnoldi_destroy(ctx.handle)
+        ctx.handle = C.c_void_p(None)

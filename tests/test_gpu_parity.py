@@ -1,0 +1,266 @@
+"""GPU path (through the C ABI) against the CPU oracle, element by element.
+
+Tolerances (FP64 mode): 1e-10 relative on E_band and N; max |d rho| and
+max |d rho^E| <= 1e-10 max |.| of the oracle's values; subspace levels within
+1e-10 max|eps|.  Mixed mode: |dE_band| per atom <= 1e-6 eV, max |d rho| <= 1e-5,
+max |d rho^E| <= 1e-4 eV, |dN| <= 1e-8 N_e.
+"""
+
+import numpy as np
+import pytest
+
+import oracle
+from tbsynth import amorphous_system, config_c1, config_c2, tiny_system
+
+pytestmark = pytest.mark.gpu
+
+KT = 0.1
+FP64_REL = 1e-10
+
+
+@pytest.fixture(scope="module")
+def m():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1307_3218_gb300 as mm
+    from paper_1307_3218_gb300 import build as b
+    b.build()
+    mm.load()
+    return mm
+
+
+@pytest.fixture(scope="module")
+def c1():
+    return config_c1(seed=0)
+
+
+@pytest.fixture(scope="module")
+def c2():
+    return config_c2(seed=0)
+
+
+def gpu_solve(m, t, nu, prec=0, cols=None, mu_fixed=None, batch=0, Ne=None):
+    ctx = m.setup_system(t, prec)
+    if batch:
+        m.marnoldi_set_batch(ctx, batch)
+    m.marnoldi_solve(ctx, cols, nu, 0, t.n_electrons if Ne is None else Ne, KT, mu_fixed)
+    rho, rhoE = m.marnoldi_density(ctx)
+    E, mu, N = m.marnoldi_energy(ctx)
+    nue, eps, w = m.marnoldi_column_stats(ctx)
+    return dict(ctx=ctx, rho=rho, rhoE=rhoE, E=E, mu=mu, N=N, nu_eff=nue, eps=eps, w=w)
+
+
+def assert_close_fp64(g, ref, t):
+    assert g["N"] == pytest.approx(ref.N, rel=FP64_REL)
+    assert g["E"] == pytest.approx(ref.E_band, rel=FP64_REL)
+    mask = ~np.isnan(ref.rho)
+    s = np.abs(ref.rho[mask]).max()
+    sE = np.abs(ref.rhoE[mask]).max()
+    assert np.abs(g["rho"][mask] - ref.rho[mask]).max() <= FP64_REL * s
+    assert np.abs(g["rhoE"][mask] - ref.rhoE[mask]).max() <= FP64_REL * sE
+    np.testing.assert_array_equal(g["nu_eff"], ref.cols.nu_eff)
+    emax = np.abs(ref.cols.eps).max()
+    assert np.abs(g["eps"] - ref.cols.eps).max() <= FP64_REL * emax
+    assert np.abs(g["w"] - ref.cols.w).max() <= 1e-9
+
+
+def test_c1_fp64_full(m, c1):
+    g = gpu_solve(m, c1, 30)
+    ref = oracle.solve(c1, nu=30, kT=KT)
+    assert_close_fp64(g, ref, c1)
+    assert g["mu"] == pytest.approx(ref.mu, abs=1e-6)
+
+
+@pytest.mark.parametrize("nu", [1, 2, 7, 64])
+def test_c1_fp64_nu(m, c1, nu):
+    g = gpu_solve(m, c1, nu)
+    ref = oracle.solve(c1, nu=nu, kT=KT)
+    assert_close_fp64(g, ref, c1)
+
+
+def test_nu1_closed_form(m, c1):
+    H, S = c1.dense()
+    g = gpu_solve(m, c1, 1, mu_fixed=0.3)
+    np.testing.assert_allclose(g["eps"][:, 0], np.diag(H) / np.diag(S), rtol=1e-15)
+    np.testing.assert_allclose(g["w"][:, 0], 1.0, atol=1e-15)
+
+
+@pytest.mark.parametrize("n,seed", [(8, 0), (10, 3)])
+def test_dense_limit(m, n, seed):
+    """nu = M on a connected cluster: GPU equals the dense generalized eigensolve."""
+    import scipy.linalg as sl
+    t = tiny_system(n, seed=seed)
+    g = gpu_solve(m, t, t.M)
+    assert np.all(g["nu_eff"] == t.M)
+    H, S = t.dense()
+    ev, Phi = sl.eigh(H, S)
+    from scipy.special import expit
+    f2 = 2 * expit(-(ev - g["mu"]) / KT)
+    rho = (Phi * f2) @ Phi.T
+    rows = np.repeat(np.arange(t.n_block_rows), np.diff(t.row_ptr))
+    for k, (I, J) in enumerate(zip(rows, t.col_idx)):
+        np.testing.assert_allclose(g["rho"][k], rho[4 * I:4 * I + 4, 4 * J:4 * J + 4],
+                                   atol=1e-10 * np.abs(rho).max())
+    assert g["N"] == pytest.approx(t.n_electrons, rel=1e-12)
+
+
+def test_breakdown_isolated_atom(m):
+    t = tiny_system(8, seed=1)
+    g = gpu_solve(m, t, 12)
+    ref = oracle.solve(t, nu=12, kT=KT)
+    assert_close_fp64(g, ref, t)
+    assert g["nu_eff"].min() == 1
+
+
+def test_ragged_column_subset(m, c1):
+    rng = np.random.default_rng(3)
+    cols = rng.choice(c1.M, size=37, replace=False)      # unsorted, not a multiple of anything
+    g = gpu_solve(m, c1, 30, cols=cols, mu_fixed=1.7)
+    ref = oracle.solve(c1, nu=30, kT=KT, mu_fixed=1.7, cols=cols)
+    assert_close_fp64(g, ref, c1)
+    unsolved = np.isnan(ref.rho)
+    assert np.all(g["rho"][unsolved] == 0.0)
+
+
+def test_batching_and_determinism(m, c1):
+    a = gpu_solve(m, c1, 30)
+    b = gpu_solve(m, c1, 30, batch=7)
+    c = gpu_solve(m, c1, 30)
+    for k in ("rho", "rhoE", "eps", "w"):
+        np.testing.assert_array_equal(a[k], b[k])
+        np.testing.assert_array_equal(a[k], c[k])
+    assert a["E"] == b["E"] == c["E"]
+
+
+def test_green_function(m, c1):
+    g = gpu_solve(m, c1, 30)
+    ref = oracle.columns(c1, c1.real_columns(), 30)
+    zs = [g["mu"] + 0.2j, -20.0 + 1.5j, 5.0 - 0.01j]
+    G = m.marnoldi_green(g["ctx"], zs)
+    for q, z in enumerate(zs):
+        gr = oracle.scatter_pattern(c1, ref, oracle.green_rows(ref, z))
+        assert np.abs(G[q] - gr).max() <= FP64_REL * np.abs(gr).max()
+
+
+def test_density_device_matches_host(m, c1):
+    import torch
+    g = gpu_solve(m, c1, 16)
+    rho = torch.empty(c1.nnzb * 16, dtype=torch.float64, device="cuda")
+    rhoE = torch.empty_like(rho)
+    m.marnoldi_density_device(g["ctx"], rho, rhoE)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(rho.cpu().numpy().reshape(-1, 4, 4), g["rho"])
+    np.testing.assert_array_equal(rhoE.cpu().numpy().reshape(-1, 4, 4), g["rhoE"])
+
+
+def test_native_allocator_matches_torch_allocator(m, c1):
+    a = gpu_solve(m, c1, 20)
+    m.marnoldi_set_allocator(None, None)
+    try:
+        b = gpu_solve(m, c1, 20)
+    finally:
+        m.use_torch_allocator()
+    np.testing.assert_array_equal(a["rho"], b["rho"])
+
+
+def test_relabelling(m, c1):
+    perm = np.random.default_rng(5).permutation(c1.n_block_rows)
+    t2 = c1.permuted(perm)
+    a = gpu_solve(m, c1, 20)
+    b = gpu_solve(m, t2, 20)
+    assert b["E"] == pytest.approx(a["E"], rel=1e-11)
+    ia = oracle.block_index(c1)
+    ib = oracle.block_index(t2)
+    for (I2, J2), k2 in ib.items():
+        np.testing.assert_allclose(b["rho"][k2], a["rho"][ia[(int(perm[I2]), int(perm[J2]))]],
+                                   atol=1e-10)
+
+
+def test_errors(m, c1):
+    ctx = m.setup_system(c1, 0)
+    with pytest.raises(m.MarnoldiError) as ei:
+        m.marnoldi_density(ctx)
+    assert ei.value.code == m.marnoldi.MARNOLDI_ESTATE
+    with pytest.raises(m.MarnoldiError) as ei:
+        m.marnoldi_solve(ctx, None, 200, 0, c1.n_electrons, KT)
+    assert ei.value.code == m.marnoldi.MARNOLDI_EINVAL
+    with pytest.raises(m.MarnoldiError) as ei:
+        m.marnoldi_solve(ctx, None, 30, 64, c1.n_electrons, KT)
+    assert ei.value.code == m.marnoldi.MARNOLDI_EINVAL
+    with pytest.raises(m.MarnoldiError) as ei:
+        m.marnoldi_solve(ctx, [0, 5, 0], 30, 0, c1.n_electrons, KT)
+    assert ei.value.code == m.marnoldi.MARNOLDI_EINVAL
+    with pytest.raises(m.MarnoldiError) as ei:
+        m.marnoldi_solve(ctx, None, 30, 0, 3.0 * c1.M, KT)
+    assert ei.value.code == m.marnoldi.MARNOLDI_ENOCONV
+    with pytest.raises(m.MarnoldiError):
+        m.marnoldi_solve(ctx, np.zeros(0, np.int64), 30, 0, c1.n_electrons, KT)
+    # a failed solve leaves no stale results behind
+    with pytest.raises(m.MarnoldiError) as ei:
+        m.marnoldi_energy(ctx)
+    assert ei.value.code == m.marnoldi.MARNOLDI_ESTATE
+
+
+# ----------------------------------------------------------------- mixed precision
+
+def mixed_errors(g, ref, t):
+    n_atoms = t.n_block_rows
+    mask = ~np.isnan(ref.rho)
+    return dict(
+        dE_per_atom=abs(g["E"] - ref.E_band) / n_atoms,
+        drho=float(np.abs(g["rho"][mask] - ref.rho[mask]).max()),
+        drhoE=float(np.abs(g["rhoE"][mask] - ref.rhoE[mask]).max()),
+        dN=abs(g["N"] - ref.N),
+    )
+
+
+def test_c1_mixed(m, c1):
+    g = gpu_solve(m, c1, 30, prec=1)
+    ref = oracle.solve(c1, nu=30, kT=KT, mu_fixed=g["mu"])
+    e = mixed_errors(g, ref, c1)
+    print("mixed C1 errors", e)
+    assert e["dE_per_atom"] <= 1e-6
+    assert e["drho"] <= 1e-5
+    assert e["drhoE"] <= 1e-4
+    assert e["dN"] <= 1e-8 * c1.n_electrons
+
+
+# ----------------------------------------------------------------- full-size workload
+
+SAMPLE = 24
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_c2_full_size_sampled(m, c2, prec):
+    """4,096-atom amorphous carbon, every column on the GPU (the benchmark's launch
+    configuration); the oracle recomputes a seeded sample of columns at the GPU's mu."""
+    g = gpu_solve(m, c2, 30, prec=prec)
+    assert g["N"] == pytest.approx(c2.n_electrons, rel=1e-12 if prec == 0 else 1e-8)
+    rng = np.random.default_rng(11)
+    sample = np.sort(rng.choice(c2.M, size=SAMPLE, replace=False))
+    ref = oracle.solve(c2, nu=30, kT=KT, mu_fixed=g["mu"], cols=sample)
+    mask = ~np.isnan(ref.rho)
+    drho = np.abs(g["rho"][mask] - ref.rho[mask]).max()
+    drhoE = np.abs(g["rhoE"][mask] - ref.rhoE[mask]).max()
+    deps = np.abs(g["eps"][sample] - ref.cols.eps).max()
+    print(f"C2 prec={prec} sample: drho={drho:.3e} drhoE={drhoE:.3e} deps={deps:.3e}")
+    if prec == 0:
+        assert drho <= FP64_REL * np.abs(ref.rho[mask]).max()
+        assert drhoE <= FP64_REL * np.abs(ref.rhoE[mask]).max()
+        assert deps <= FP64_REL * np.abs(ref.cols.eps).max()
+    else:
+        assert drho <= 1e-5
+        assert drhoE <= 1e-4
+    # pattern traces of the GPU's own columns: (S rho)_jj = sum_a 2 f w_a
+    from scipy.special import expit
+    rows = np.repeat(np.arange(c2.n_block_rows), np.diff(c2.row_ptr))
+    bidx = oracle.block_index(c2)
+    for q, j in enumerate(sample):
+        J, b = j // 4, j % 4
+        tr = 0.0
+        for k in range(c2.row_ptr[J], c2.row_ptr[J + 1]):
+            I = c2.col_idx[k]
+            tr += c2.S[k][b, :] @ g["rho"][bidx[(int(I), int(J))]][:, b]
+        f2 = 2 * expit(-(g["eps"][j] - g["mu"]) / KT)
+        assert tr == pytest.approx(np.sum(f2 * g["w"][j]), abs=1e-10 if prec == 0 else 1e-6)
