@@ -1,0 +1,409 @@
+"""Benchmark of the mArnoldi hot path on GB300: columns per second.
+
+One step = one pass of the whole hot path over the workload: every column's
+Krylov subspace, S-orthonormalisation, subspace eigensolve, the Fermi level by
+bisection, and the density / energy-density columns written on H's pattern
+(device buffers) with the band energy reduced.
+
+Default workload: 4,096-atom random-packed amorphous carbon (M = 16,384), global
+mode, nu = 30, all 16,384 columns, kT = 0.1 eV, 4 electrons per atom.  The
+headline `value` is mixed precision; the FP64 path is timed beside it.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl marnoldi|reference]
+
+Under torchrun (N > 1) every rank solves its own copy of the workload
+(independent problems, no collective on the data path); rank 0 prints the
+whole-job rate from the slowest rank's time.  `--impl reference` times the CPU
+oracle instead (rank 0 only).
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+KT = 0.1
+REFERENCE_MU = 4.185   # Fermi level of the default workload (eV); the sampled oracle arm uses it fixed
+METRIC = "mArnoldi columns/s"
+UNIT = "columns/s"
+L2_FLUSH_BYTES = 256 << 20
+FP64_PEAK_NOTE = "152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz (nominal 1.25 TFLOP/s FP64)"
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="marnoldi", choices=["marnoldi", "reference"])
+    p.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    p.add_argument("--nu", type=int, default=30)
+    p.add_argument("--atoms", type=int, default=4096)
+    p.add_argument("--columns", type=int, default=0, help="solve only the first N columns (0 = all)")
+    p.add_argument("--no-fp64", action="store_true", help="skip the FP64 side measurement")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--cpu-seconds", type=float, default=15.0)
+    return p.parse_args()
+
+
+def workload(args):
+    from tbsynth import amorphous_system
+    t = amorphous_system(args.atoms, seed=0)
+    cols = t.real_columns()
+    if args.columns:
+        cols = cols[:args.columns]
+    return t, cols
+
+
+def electrons(t, cols) -> float:
+    """Target electron count of the solved columns: the structure's count scaled to the subset."""
+    return float(t.n_electrons) * len(cols) / len(t.real_columns())
+
+
+def workload_name(args, t, ncols):
+    return (f"amorphous sp2-sp3 carbon {t.n_block_rows} atoms (M={t.M}, 3.0 g/cm^3, seed 0), "
+            f"global mode, nu={args.nu}, {ncols} columns, kT={KT} eV, mu by bisection at 4 e/atom")
+
+
+# ------------------------------------------------------------------------ measurement helpers
+
+def read_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+class Clocks:
+    """Samples SM clocks and throttle reasons with nvidia-smi while the timed region runs."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.proc = None
+        self.path = None
+        self.dev = device_index
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for ln in open(self.path):
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 7:
+                continue
+            try:
+                rows.append((float(f[0]), float(f[1]), float(f[2]), f[3:7]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i, v in enumerate(r[3]) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "power_w_max": max(r[2] for r in rows), "samples": len(rows), "reasons": reasons}
+
+
+def mgs_algorithmic(nu: int, m: int, vbytes: int, ncols: int):
+    """Bytes the two-pass Gram-Schmidt step must stream and FP64 flops it must do.
+
+    Step n (0-based) with n < nu-1 reads u and, in each of the two passes, the
+    n+1 stored vectors k_i and S k_i, and writes w: (4 (n+1) + 2) m values.
+    The last step only forms h_{i,nu-1} = k_i . u: (nu + 1) m values.
+    Flops: pass 1 two dots and one update, pass 2 one dot and one update per
+    entry and stored vector; the last step one dot.
+    """
+    vals = sum(4 * (n + 1) + 2 for n in range(nu - 1)) + (nu + 1)
+    fmas = sum(5 * (n + 1) for n in range(nu - 1)) + nu
+    return vals * m * vbytes * ncols, 2.0 * fmas * m * ncols
+
+
+def spmm_algorithmic(nu: int, m: int, nnzb: int, nbr: int, vbytes: int, ncols: int):
+    """Per column and application: read x, write y (m values each); flops 2 * 16 nnzb."""
+    apps = 2 * nu - 1
+    return apps * 2 * m * vbytes * ncols, apps * 2.0 * 16 * nnzb * ncols
+
+
+# ------------------------------------------------------------------------ GPU arm
+
+def time_gpu(m, t, cols, args, prec, steps, warmup, dev, measure_clocks=False):
+    import torch
+    stream = torch.cuda.current_stream()
+    ctx = m.setup_system(t, prec)
+    rho = torch.empty(t.nnzb * 16, dtype=torch.float64, device=dev)
+    rhoE = torch.empty_like(rho)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    colsel = None if len(cols) == t.M else cols
+
+    ne = electrons(t, cols)
+
+    def step():
+        m.marnoldi_solve(ctx, colsel, args.nu, 0, ne, KT)
+        m.marnoldi_density_device(ctx, rho, rhoE)
+
+    for _ in range(warmup):
+        step()
+        flush.fill_(1.0)
+    torch.cuda.synchronize()
+    m.marnoldi_set_profiling(ctx, True)
+    m.marnoldi_kernel_stats(ctx, reset=True)
+    clk = Clocks(dev.index if dev.index is not None else 0) if measure_clocks else None
+    if clk:
+        clk.start()
+    times = []
+    if torch.distributed.is_initialized():
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    for _ in range(steps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        flush.fill_(float(len(times)))   # L2 flush between timed steps, outside the events
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    torch.cuda.synchronize()
+    if torch.distributed.is_initialized():
+        torch.distributed.barrier()
+    clocks = clk.stop() if clk else None
+    stats = m.marnoldi_kernel_stats(ctx)
+    E, mu, N = m.marnoldi_energy(ctx)
+    res = dict(times=times, stats=stats, E=E, mu=mu, N=N, clocks=clocks, ctx=ctx)
+    return res
+
+
+def time_e2e(m, t, cols, args, prec, steps, warmup):
+    """Through the public API with host buffers: upload, solve, density to host, energy."""
+    import torch
+    colsel = None if len(cols) == t.M else cols
+
+    ne = electrons(t, cols)
+
+    def step():
+        ctx = m.setup_system(t, prec)
+        m.marnoldi_solve(ctx, colsel, args.nu, 0, ne, KT)
+        rho, rhoE = m.marnoldi_density(ctx)
+        E, mu, N = m.marnoldi_energy(ctx)
+        m.marnoldi_destroy(ctx)
+        return rho
+
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(steps):
+        t0 = time.perf_counter()
+        step()
+        torch.cuda.synchronize()
+        ts.append(time.perf_counter() - t0)
+    h2d = (8 * (t.n_block_rows + 1) + 4 * t.nnzb + 2 * 128 * t.nnzb + 8 * t.M + 8 * t.nnzb
+           + (2 * 64 * t.nnzb if prec == 1 else 0) + (0 if colsel is None else 8 * len(cols)))
+    d2h = 2 * 128 * t.nnzb
+    return statistics.mean(ts), h2d, d2h
+
+
+# ------------------------------------------------------------------------ CPU oracle
+
+def oracle_sample(t, args, budget_s, mu=None):
+    """Time the oracle on a bounded seeded sample of columns (all host cores)."""
+    import oracle
+    rng = np.random.default_rng(1234)
+    allc = t.real_columns()
+    nth = oracle.threads()
+    n = max(nth, 16)
+    t0 = time.perf_counter()
+    oracle.columns(t, rng.choice(allc, size=n, replace=False), args.nu)
+    dt = time.perf_counter() - t0
+    n2 = int(min(len(allc), max(n, budget_s / max(dt / n, 1e-6))))
+    sample = np.sort(rng.choice(allc, size=n2, replace=False))
+    t0 = time.perf_counter()
+    c = oracle.columns(t, sample, args.nu)
+    if mu is not None:
+        oracle.density_rows(c, mu, KT)
+    dt = time.perf_counter() - t0
+    return dict(value=n2 / dt, cores=nth, n=n2, seconds=dt, cols=c, sample=sample)
+
+
+# ------------------------------------------------------------------------ main
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        return main_reference(args, world, rank)
+
+    import torch
+    import paper_1307_3218_gb300 as m
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    if world > 1:
+        torch.distributed.init_process_group("nccl", device_id=dev)
+    m.load()
+    t, cols = workload(args)
+    ncols = len(cols)
+    prec = 1 if args.precision == "mixed" else 0
+    res = time_gpu(m, t, cols, args, prec, args.steps, args.warmup, dev, measure_clocks=(rank == 0))
+    step_s = statistics.mean(res["times"]) / 1e3
+    tmax = torch.tensor([step_s], dtype=torch.float64, device=dev)
+    if world > 1:
+        torch.distributed.all_reduce(tmax, op=torch.distributed.ReduceOp.MAX)
+    step_s = float(tmax.item())
+    value = world * ncols / step_s
+    stats = res["stats"]
+    launches = sum(v[0] for v in stats.values())
+    peaks = read_peaks()
+
+    # roofline of the dominant kernel over the timed region
+    vb = 4 if prec == 1 else 8
+    dom = max(stats, key=lambda k: stats[k][1])
+    nlaunch, dom_ms = stats[dom]
+    steps = args.steps
+    if dom == "mgs":
+        by, fl = mgs_algorithmic(args.nu, t.M, vb, ncols)
+    elif dom in ("spmm_H", "spmm_S"):
+        by, fl = spmm_algorithmic(args.nu, t.M, t.nnzb, t.n_block_rows, vb, ncols)
+        by, fl = by / 2, fl / 2
+    else:
+        by, fl = None, None
+    if prec == 1 and by is not None:
+        bound, ach, peak, unit = "hbm", by * steps / (dom_ms / 1e3) / 1e9, peaks.get("hbm_gbs", 6800.0), "GB/s"
+        peak_src = "measured (MEASURED_PEAKS.json hbm_gbs)" if "hbm_gbs" in peaks else "fallback"
+    elif by is not None:
+        bound, ach, unit = "alu", fl * steps / (dom_ms / 1e3) / 1e12, "TFLOP/s"
+        peak, peak_src = 152 * 2 * 2 * 2.07e9 / 1e12, "derived: " + FP64_PEAK_NOTE
+    else:
+        bound = ach = peak = unit = peak_src = None
+    roof = None
+    if ach is not None:
+        roof = {"kernel": dom, "bound": bound, "achieved": round(ach, 3), "peak": round(peak, 3),
+                "unit": unit, "frac": round(ach / peak, 4), "traffic": None,
+                "peak_source": peak_src, "launches": nlaunch, "avg_launch_ms": round(dom_ms / nlaunch, 4),
+                "algorithmic_per_step": {"bytes": by, "flops": fl}}
+
+    line = {
+        "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(step_s * 1e3, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32+f64" if prec == 1 else "f64", "data": "synthetic",
+        "config": {"workload": workload_name(args, t, ncols), "precision": args.precision,
+                   "nu": args.nu, "columns": ncols, "atoms": t.n_block_rows, "M": t.M,
+                   "nnzb": t.nnzb, "mode": "global",
+                   "l2": f"flushed between timed steps ({L2_FLUSH_BYTES >> 20} MB write)",
+                   "parallelism": f"{world} independent replica(s)" if world > 1 else "1 GPU"},
+        "roofline": roof,
+        "gpu_launches": int(launches),
+        "kernel_ms_per_step": {k: round(v[1] / steps, 3) for k, v in stats.items() if v[0]},
+        "clocks": res["clocks"],
+        "result": {"E_band_eV": res["E"], "mu_eV": res["mu"], "N": res["N"]},
+    }
+    mu_gpu = res["mu"]
+    m.marnoldi_destroy(res["ctx"])
+
+    if not args.no_fp64 and prec == 1:
+        r64 = time_gpu(m, t, cols, args, 0, max(3, args.steps // 2), 3, dev)
+        s64 = statistics.mean(r64["times"]) / 1e3
+        st64 = r64["stats"]
+        ms64 = st64["mgs"][1]
+        by64, fl64 = mgs_algorithmic(args.nu, t.M, 8, ncols)
+        ach64 = fl64 * max(3, args.steps // 2) / (ms64 / 1e3) / 1e12
+        pk64 = 152 * 2 * 2 * 2.07e9 / 1e12
+        line["fp64"] = {"value": round(world * ncols / s64, 2), "ms_per_step": round(s64 * 1e3, 3),
+                        "kernel_ms_per_step": {k: round(v[1] / max(3, args.steps // 2), 3)
+                                               for k, v in st64.items() if v[0]},
+                        "mgs_roofline": {"bound": "alu", "achieved": round(ach64, 3), "peak": round(pk64, 3),
+                                         "unit": "TFLOP/s", "frac": round(ach64 / pk64, 4)},
+                        "result": {"E_band_eV": r64["E"], "mu_eV": r64["mu"], "N": r64["N"]}}
+        m.marnoldi_destroy(r64["ctx"])
+
+    if not args.no_e2e:
+        e2e_s, h2d, d2h = time_e2e(m, t, cols, args, prec, max(3, args.steps // 2), 1)
+        line["e2e"] = {"value": round(world * ncols / e2e_s, 2), "unit": UNIT,
+                       "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+                       "ms_per_step": round(e2e_s * 1e3, 3)}
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cb = oracle_sample(t, args, args.cpu_seconds, mu=mu_gpu)
+        line["cpu_baseline"] = {"value": round(cb["value"], 3), "unit": UNIT, "cores": cb["cores"],
+                                "kind": "oracle",
+                                "sample": f"{cb['n']} seeded columns of the same workload (Krylov build, "
+                                          f"eigensolve, weights, density columns at the GPU's mu), "
+                                          f"{cb['seconds']:.1f} s"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main_reference(args, world, rank):
+    """The CPU oracle as the reference arm: each step a bounded sample of the workload."""
+    if rank != 0:
+        return
+    import oracle
+    t, cols = workload(args)
+    oracle.build()
+    nth = oracle.threads()
+    rng = np.random.default_rng(99)
+    # size a step to ~args.cpu_seconds / steps of CPU work
+    probe = rng.choice(cols, size=max(nth, 16), replace=False)
+    t0 = time.perf_counter()
+    oracle.columns(t, probe, args.nu)
+    per_col = (time.perf_counter() - t0) / probe.size
+    per_step = int(max(nth, min(len(cols), (args.cpu_seconds / max(1, args.steps)) / per_col)))
+    for _ in range(args.warmup):
+        oracle.columns(t, rng.choice(cols, size=nth, replace=False), args.nu)
+    ts = []
+    for _ in range(args.steps):
+        sample = rng.choice(cols, size=per_step, replace=False)
+        t0 = time.perf_counter()
+        c = oracle.columns(t, sample, args.nu)
+        oracle.density_rows(c, REFERENCE_MU, KT)
+        ts.append(time.perf_counter() - t0)
+    v = per_step / statistics.mean(ts)
+    line = {"impl": "reference", "metric": METRIC, "value": round(v, 3), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(statistics.mean(ts) * 1e3, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": workload_name(args, t, len(cols)), "nu": args.nu, "mode": "global"},
+            "cpu_baseline": {"value": round(v, 3), "unit": UNIT, "cores": nth, "kind": "oracle",
+                             "sample": f"{per_step} seeded columns per step (Krylov build, eigensolve, "
+                                       f"weights, density columns at a fixed mu)"},
+            "e2e": {"value": round(v, 3), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()
