@@ -176,6 +176,31 @@ int marnoldi_kernel_kinds(void);
 int marnoldi_kernel_stats(marnoldi_ctx *ctx, int kind, const char **name, int64_t *launches,
                           double *ms, int reset);
 
+/*
+ * Electron count and band energy at a given mu over subspace levels already in
+ * device memory, without allocating any device memory.  The paper has no
+ * counterpart: this is a variant of the bisection's reduction for callers that
+ * cannot call cudaMalloc (code running under another framework's memory
+ * manager, or on a request path that must not allocate).
+ *
+ *   eps_device, w_device  ncols*nu doubles each (levels and weights, the layout
+ *                         of marnoldi_column_stats).
+ *   nu_eff_device         ncols int32 valid-level counts, or NULL (all nu valid).
+ *   out_device            2 doubles: N(mu) = sum 2 f w, E(mu) = sum 2 f eps w.
+ *   cuda_stream           stream to run on (NULL = legacy default stream).
+ *
+ * Scratch: a fixed 64 KiB device array inside the library (every GPU that
+ * loads the library holds it until exit), so ncols*nu is limited to 16,777,216
+ * levels; larger inputs return MARNOLDI_EINVAL.  The first call on a device
+ * looks up that array's device address; make it before any stream capture.
+ * Every call shares the one array: calls that overlap on the GPU (other
+ * streams, other threads) race and must be serialised by the caller.
+ * Errors are reported through marnoldi_last_error(NULL).
+ */
+int marnoldi_count_noalloc(const double *eps_device, const double *w_device,
+                           const int32_t *nu_eff_device, int64_t ncols, int nu, double mu,
+                           double kT, double *out_device, void *cuda_stream);
+
 /* Message of the last failure on ctx (or of the last failed setup when ctx is NULL). */
 const char *marnoldi_last_error(const marnoldi_ctx *ctx);
 

@@ -8,7 +8,7 @@ declared in ``include/marnoldi.h``.  This package holds the CUDA sources
 """
 
 from .marnoldi import (MARNOLDI_FP64, MARNOLDI_MIXED, Context, MarnoldiError, load,
-                       marnoldi_column_stats, marnoldi_density, marnoldi_density_device,
+                       marnoldi_column_stats, marnoldi_count_noalloc, marnoldi_density, marnoldi_density_device,
                        marnoldi_destroy, marnoldi_energy, marnoldi_green, marnoldi_kernel_kinds,
                        marnoldi_kernel_stats, marnoldi_last_error, marnoldi_set_allocator,
                        marnoldi_set_batch, marnoldi_set_profiling, marnoldi_setup,
@@ -16,7 +16,7 @@ from .marnoldi import (MARNOLDI_FP64, MARNOLDI_MIXED, Context, MarnoldiError, lo
 
 __all__ = [
     "MARNOLDI_FP64", "MARNOLDI_MIXED", "Context", "MarnoldiError", "load",
-    "marnoldi_column_stats", "marnoldi_density", "marnoldi_density_device", "marnoldi_destroy",
+    "marnoldi_column_stats", "marnoldi_count_noalloc", "marnoldi_density", "marnoldi_density_device", "marnoldi_destroy",
     "marnoldi_energy", "marnoldi_green", "marnoldi_kernel_kinds", "marnoldi_kernel_stats",
     "marnoldi_last_error", "marnoldi_set_allocator", "marnoldi_set_batch",
     "marnoldi_set_profiling", "marnoldi_setup", "marnoldi_solve", "marnoldi_solved_shape",

@@ -29,6 +29,12 @@ constexpr int kBisectMaxit = 200;
 
 }  // namespace
 
+int marnoldi::set_global_error(int code, const char *msg)
+{
+    g_setup_err = msg;
+    return code;
+}
+
 struct marnoldi_ctx {
     cudaStream_t stream = nullptr;
     int prec = 0;

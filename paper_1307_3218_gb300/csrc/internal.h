@@ -25,6 +25,9 @@ enum KernelKind {
 
 const char *kernel_name(int kind);
 
+// Record the message that marnoldi_last_error(NULL) returns; returns `code`.
+int set_global_error(int code, const char *msg);
+
 // Largest subspace dimension of the shared-memory eigensolver.
 constexpr int kMaxNu = 110;
 // Largest Krylov-vector length of global mode (one CTA holds a column's vector).

@@ -84,6 +84,7 @@ def load(path: str | None = None):
         "marnoldi_kernel_kinds": (i32, []),
         "marnoldi_kernel_stats": (i32, [P, i32, C.POINTER(C.c_char_p), C.POINTER(i64),
                                         C.POINTER(d), i32]),
+        "marnoldi_count_noalloc": (i32, [P, P, P, i64, i32, d, d, P, P]),
         "marnoldi_last_error": (C.c_char_p, [P]),
         "marnoldi_destroy": (None, [P]),
     }
@@ -318,6 +319,19 @@ def marnoldi_kernel_stats(ctx: Context, reset: bool = False) -> dict:
                                        int(bool(reset))), ctx)
         out[name.value.decode()] = (n.value, ms.value)
     return out
+
+
+def marnoldi_count_noalloc(eps_device, w_device, nu_eff_device, ncols: int, nu: int, mu: float,
+                           kT: float, out_device, stream: int | None = None) -> None:
+    """N(mu) and E(mu) over device-resident levels into out_device[0:2], allocating nothing.
+
+    For callers that cannot allocate device memory; the reduction's scratch is a
+    fixed array inside the library (at most 16,777,216 levels per call).
+    """
+    st = _current_stream() if stream is None else int(stream)
+    _check(load().marnoldi_count_noalloc(_ptr(eps_device), _ptr(w_device), _ptr(nu_eff_device),
+                                         int(ncols), int(nu), float(mu), float(kT),
+                                         _ptr(out_device), C.c_void_p(st)))
 
 
 def marnoldi_last_error(ctx: Context | None = None) -> str:
