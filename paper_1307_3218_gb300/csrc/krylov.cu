@@ -39,7 +39,7 @@ ColumnShape column_shape(int64_t m)
     for (int v = 1; v <= 16; v *= 2) {
         int64_t t = (m + v - 1) / v;
         if (t <= 1024 || v == 16) {
-            t = ((t + 31) / 32) * 32;
+            t = v >= 8 ? 1024 : ((t + 31) / 32) * 32;   // vpt >= 8: T fixed at compile time
             s.vpt = v;
             s.threads = (int)t;
             s.m_pad = t * v;
@@ -53,29 +53,107 @@ namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 
-// Sum of (a, b) over the CTA.  Every thread returns the same values, summed in
-// a fixed order.  `red` is [2][32] and `buf` alternates so that one barrier per
-// reduction suffices.
-__device__ __forceinline__ double2 block_sum2(double a, double b, double2 (*red)[32], int &buf)
+// ------------------------------------------------------------------ dot accumulators
+// Per-thread partial inner products.  FP64 vectors: fused multiply-adds in
+// FP64.  FP32 vectors (mixed precision): the product a*b of two floats is
+// split exactly into p + e (p = fl(a*b), e = fma(a, b, -p)) and p is added to
+// the running sum with an exact two-sum, so the pair (hi, lo) carries the sum
+// to about 2^-48 relative.  The reduction across the CTA stays in such pairs
+// and only the CTA total is converted to FP64, so the inner products are
+// FP64-accurate on FP32 data with no per-element FP64 work (GB300 issues
+// FP32 at about 64 times its FP64 rate).  The _rn intrinsics keep the
+// compiler from contracting the error-free steps into FMAs.
+__device__ __forceinline__ void df_add(float &hi, float &lo, float h2, float l2)
 {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        a += __shfl_xor_sync(kFull, a, o);
-        b += __shfl_xor_sync(kFull, b, o);
-    }
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-    if (lane == 0) red[buf][warp] = make_double2(a, b);
-    __syncthreads();
-    double sa = 0.0, sb = 0.0;
-    for (int q = 0; q < nw; ++q) {
-        const double2 t = red[buf][q];
-        sa += t.x;
-        sb += t.y;
-    }
-    buf ^= 1;
-    return make_double2(sa, sb);
+    const float s = __fadd_rn(hi, h2);
+    const float bb = __fsub_rn(s, hi);
+    const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(h2, bb));
+    hi = s;
+    lo = __fadd_rn(lo, __fadd_rn(l2, err));
 }
 
+template <typename VT> struct DotAcc;
+template <> struct DotAcc<double> {
+    double s = 0.0;
+    __device__ __forceinline__ void add(double a, double b) { s = fma(a, b, s); }
+    __device__ __forceinline__ double value() const { return s; }
+    __device__ __forceinline__ void warp_reduce()
+    {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(kFull, s, o);
+    }
+    __device__ __forceinline__ static double2 pack(const DotAcc &a, const DotAcc &b)
+    {
+        return make_double2(a.s, b.s);
+    }
+    __device__ __forceinline__ static void unpack(double2 p, DotAcc &a, DotAcc &b)
+    {
+        a.s = p.x;
+        b.s = p.y;
+    }
+};
+template <> struct DotAcc<float> {
+    float hi = 0.f, lo = 0.f;
+    __device__ __forceinline__ void add(float a, float b)
+    {
+        const float p = __fmul_rn(a, b);
+        const float e = __fmaf_rn(a, b, -p);
+        df_add(hi, lo, p, e);
+    }
+    __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+    __device__ __forceinline__ void warp_reduce()
+    {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const float h2 = __shfl_xor_sync(kFull, hi, o);
+            const float l2 = __shfl_xor_sync(kFull, lo, o);
+            df_add(hi, lo, h2, l2);
+        }
+    }
+    __device__ __forceinline__ static double2 pack(const DotAcc &a, const DotAcc &b)
+    {
+        union { float4 f; double2 d; } u;
+        u.f = make_float4(a.hi, a.lo, b.hi, b.lo);
+        return u.d;
+    }
+    __device__ __forceinline__ static void unpack(double2 p, DotAcc &a, DotAcc &b)
+    {
+        union { float4 f; double2 d; } u;
+        u.d = p;
+        a.hi = u.f.x; a.lo = u.f.y; b.hi = u.f.z; b.lo = u.f.w;
+    }
+};
+
+// Sum of two per-thread accumulators over the CTA, in a fixed order (warp
+// butterflies, then warp 0 over the warps' partials); every thread returns
+// the same FP64 totals.  Only warp 0 touches the warps' partials, so the
+// cross-warp step costs one warp's work, not one per thread.  `buf`
+// alternates the shared slots so that two barriers per reduction suffice.
+struct RedShared {
+    double2 part[2][32];
+    double2 total[2];
+};
+
+template <typename VT>
+__device__ __forceinline__ double2 block_sum2(DotAcc<VT> a, DotAcc<VT> b, RedShared &sh, int &buf)
+{
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    a.warp_reduce();
+    b.warp_reduce();
+    if (lane == 0) sh.part[buf][warp] = DotAcc<VT>::pack(a, b);
+    __syncthreads();
+    if (warp == 0) {
+        DotAcc<VT> x, y;
+        if (lane < nw) DotAcc<VT>::unpack(sh.part[buf][lane], x, y);
+        x.warp_reduce();
+        y.warp_reduce();
+        if (lane == 0) sh.total[buf] = make_double2(x.value(), y.value());
+    }
+    __syncthreads();
+    const double2 r = sh.total[buf];
+    buf ^= 1;
+    return r;
+}
 __device__ __forceinline__ void load4(const double *p, double (&v)[4])
 {
     const double2 a = __ldg(reinterpret_cast<const double2 *>(p));
@@ -172,57 +250,98 @@ __global__ void __launch_bounds__(256) spmm_kernel(int64_t nbr, const int64_t *_
 
 // ------------------------------------------------------------------ MGS
 // One CTA per column; thread t owns entries r = t + v T (v < VPT) of the
-// column's vectors, keeping w in registers and u in shared memory.
+// column's vectors.  Small VPT keeps w in registers.  VPT = 16 (m > 8192)
+// keeps w in shared memory instead (1024 threads leave 64 registers each),
+// with u in shared memory too when both fit, else re-read from global memory
+// (an L2 hit: the SpMM has just written it).  Entries are visited in chunks
+// with a compiler barrier between chunks so that only one chunk's loads are
+// live per thread.  k_i is held across the reduction when it fits in
+// registers, else re-read after it (an L2 hit).
 template <typename VT, int VPT>
-__global__ void __launch_bounds__(1024) mgs_kernel(const VT *__restrict__ K,
-                                                   const VT *__restrict__ SK,
-                                                   const VT *__restrict__ U, VT *__restrict__ W,
-                                                   double *__restrict__ Hsub,
-                                                   double *__restrict__ cn2,
-                                                   const int *__restrict__ status, int n, int nu,
-                                                   int64_t m_pad, int need_w)
+struct MgsCfg {
+    static constexpr bool kWs = VPT >= 16;                                   // w in smem
+    static constexpr bool kUs = !kWs || 2 * VPT * 1024 * sizeof(VT) <= 160 * 1024;  // u in smem
+    static constexpr bool kHold = VPT * sizeof(VT) <= 64;
+    static constexpr int kChunk = sizeof(VT) == 8 ? 4 : 8;
+};
+
+template <typename VT, int VPT>
+__global__ void __launch_bounds__(1024, 1) mgs_kernel(const VT *__restrict__ K,
+                                                      const VT *__restrict__ SK,
+                                                      const VT *__restrict__ U,
+                                                      VT *__restrict__ W,
+                                                      double *__restrict__ Hsub,
+                                                      double *__restrict__ cn2,
+                                                      const int *__restrict__ status, int n,
+                                                      int nu, int64_t m_pad, int need_w)
 {
+    using Cfg = MgsCfg<VT, VPT>;
+    constexpr bool kWs = Cfg::kWs, kUs = Cfg::kUs, kHold = Cfg::kHold;
+    constexpr int kChunk = Cfg::kChunk;
     const int c = blockIdx.x;
     if (status[c] != 0) return;
+    // VPT >= 8 always runs 1024 threads: a compile-time T turns the per-entry
+    // offsets v * T into load immediates instead of live registers.
+    const int T = VPT >= 8 ? 1024 : (int)blockDim.x;
+    const int tid = threadIdx.x;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    VT *us = reinterpret_cast<VT *>(smem_raw);
-    __shared__ double2 red[2][32];
+    VT *us = reinterpret_cast<VT *>(smem_raw);             // u (if kUs)
+    VT *ws = us + (kUs ? m_pad : 0);                        // w (if kWs)
+    __shared__ RedShared red;
     __shared__ double ctot[kMaxNu];
-    const int T = blockDim.x, tid = threadIdx.x;
     const int64_t base = (int64_t)c * nu * m_pad;
-    constexpr bool kHold = VPT * sizeof(VT) <= 64;
-
-    VT w[VPT];
     const VT *u = U + (int64_t)c * m_pad;
+
+    VT wr[kWs ? 1 : VPT];
 #pragma unroll
     for (int v = 0; v < VPT; ++v) {
-        const VT x = u[tid + v * T];
-        w[v] = x;
-        us[tid + v * T] = x;
+        const int r = tid + v * T;
+        const VT x = u[r];
+        if constexpr (kWs) ws[r] = x; else wr[v] = x;
+        if constexpr (kUs) us[r] = x;
     }
     int buf = 0;
     // pass 1: h_{i,n} = k_i . u and the first Gram-Schmidt sweep
     for (int i = 0; i <= n; ++i) {
         const VT *ki = K + base + (int64_t)i * m_pad;
         const VT *ski = SK + base + (int64_t)i * m_pad;
-        double pc = 0.0, ph = 0.0;
+        DotAcc<VT> ac, ah;
         VT kv[kHold ? VPT : 1];
 #pragma unroll
-        for (int v = 0; v < VPT; ++v) {
-            const int r = tid + v * T;
-            const VT kr = ki[r];
-            if constexpr (kHold) kv[v] = kr;
-            ph = fma((double)kr, (double)us[r], ph);
-            if (need_w) pc = fma((double)ski[r], (double)w[v], pc);
+        for (int v0 = 0; v0 < VPT; v0 += kChunk) {
+#pragma unroll
+            for (int q = 0; q < kChunk; ++q) {
+                const int v = v0 + q;
+                if (v >= VPT) break;
+                const int r = tid + v * T;
+                const VT kr = ki[r];
+                if constexpr (kHold) kv[v] = kr;
+                VT uu;
+                if constexpr (kUs) uu = us[r]; else uu = u[r];
+                ah.add(kr, uu);
+                if (need_w) {
+                    VT wv;
+                    if constexpr (kWs) wv = ws[r]; else wv = wr[v];
+                    ac.add(ski[r], wv);
+                }
+            }
+            if (v0 + kChunk < VPT) asm volatile("" ::: "memory");
         }
-        const double2 s = block_sum2(pc, ph, red, buf);
+        const double2 s = block_sum2(ac, ah, red, buf);
         if (need_w) {
             const VT cc = (VT)s.x;
 #pragma unroll
-            for (int v = 0; v < VPT; ++v) {
-                VT kr;
-                if constexpr (kHold) kr = kv[v]; else kr = ki[tid + v * T];
-                w[v] = fma(-cc, kr, w[v]);
+            for (int v0 = 0; v0 < VPT; v0 += kChunk) {
+#pragma unroll
+                for (int q = 0; q < kChunk; ++q) {
+                    const int v = v0 + q;
+                    if (v >= VPT) break;
+                    const int r = tid + v * T;
+                    VT kr;
+                    if constexpr (kHold) kr = kv[v]; else kr = ki[r];
+                    if constexpr (kWs) ws[r] = fma(-cc, kr, ws[r]); else wr[v] = fma(-cc, kr, wr[v]);
+                }
+                if (v0 + kChunk < VPT) asm volatile("" ::: "memory");
             }
         }
         if (tid == 0) {
@@ -236,18 +355,45 @@ __global__ void __launch_bounds__(1024) mgs_kernel(const VT *__restrict__ K,
     for (int i = 0; i <= n; ++i) {
         const VT *ki = K + base + (int64_t)i * m_pad;
         const VT *ski = SK + base + (int64_t)i * m_pad;
-        double pc = 0.0;
+        DotAcc<VT> ac;
+        VT kv[kHold ? VPT : 1];
 #pragma unroll
-        for (int v = 0; v < VPT; ++v) pc = fma((double)ski[tid + v * T], (double)w[v], pc);
-        const double2 s = block_sum2(pc, 0.0, red, buf);
+        for (int v0 = 0; v0 < VPT; v0 += kChunk) {
+#pragma unroll
+            for (int q = 0; q < kChunk; ++q) {
+                const int v = v0 + q;
+                if (v >= VPT) break;
+                const int r = tid + v * T;
+                if constexpr (kHold) kv[v] = ki[r];
+                VT wv;
+                if constexpr (kWs) wv = ws[r]; else wv = wr[v];
+                ac.add(ski[r], wv);
+            }
+            if (v0 + kChunk < VPT) asm volatile("" ::: "memory");
+        }
+        const double2 s = block_sum2(ac, DotAcc<VT>(), red, buf);
         const VT cc = (VT)s.x;
 #pragma unroll
-        for (int v = 0; v < VPT; ++v) w[v] = fma(-cc, ki[tid + v * T], w[v]);
+        for (int v0 = 0; v0 < VPT; v0 += kChunk) {
+#pragma unroll
+            for (int q = 0; q < kChunk; ++q) {
+                const int v = v0 + q;
+                if (v >= VPT) break;
+                const int r = tid + v * T;
+                VT kr;
+                if constexpr (kHold) kr = kv[v]; else kr = ki[r];
+                if constexpr (kWs) ws[r] = fma(-cc, kr, ws[r]); else wr[v] = fma(-cc, kr, wr[v]);
+            }
+            if (v0 + kChunk < VPT) asm volatile("" ::: "memory");
+        }
         if (tid == 0) ctot[i] += s.x;
     }
     VT *wo = W + (int64_t)c * m_pad;
 #pragma unroll
-    for (int v = 0; v < VPT; ++v) wo[tid + v * T] = w[v];
+    for (int v = 0; v < VPT; ++v) {
+        const int r = tid + v * T;
+        if constexpr (kWs) wo[r] = ws[r]; else wo[r] = wr[v];
+    }
     if (tid == 0) {
         double q = 0.0;
         for (int i = 0; i <= n; ++i) q += ctot[i] * ctot[i];
@@ -267,15 +413,15 @@ __global__ void __launch_bounds__(1024) normalize_kernel(const VT *__restrict__ 
 {
     const int c = blockIdx.x;
     if (status[c] != 0) return;
-    __shared__ double2 red[2][32];
-    const int T = blockDim.x, tid = threadIdx.x;
+    __shared__ RedShared red;
+    const int T = VPT >= 8 ? 1024 : (int)blockDim.x, tid = threadIdx.x;
     const VT *w = W + (int64_t)c * m_pad;
     const VT *sw = SW + (int64_t)c * m_pad;
-    double p = 0.0;
-#pragma unroll
-    for (int v = 0; v < VPT; ++v) p = fma((double)w[tid + v * T], (double)sw[tid + v * T], p);
+    DotAcc<VT> acc;
+#pragma unroll 4
+    for (int v = 0; v < VPT; ++v) acc.add(w[tid + v * T], sw[tid + v * T]);
     int buf = 0;
-    const double beta2 = block_sum2(p, 0.0, red, buf).x;
+    const double beta2 = block_sum2(acc, DotAcc<VT>(), red, buf).x;
     VT *kn = K + ((int64_t)c * nu + n + 1) * m_pad;
     VT *skn = SK + ((int64_t)c * nu + n + 1) * m_pad;
     if (!(beta2 > 0.0) || beta2 <= tau2 * (beta2 + cn2[c])) {
@@ -283,7 +429,7 @@ __global__ void __launch_bounds__(1024) normalize_kernel(const VT *__restrict__ 
             status[c] = (beta2 >= 0.0) ? 1 : 2;   // 2: negative or NaN S-norm
             nu_eff[c] = n + 1;
         }
-#pragma unroll
+#pragma unroll 4
         for (int v = 0; v < VPT; ++v) {
             kn[tid + v * T] = VT(0);
             skn[tid + v * T] = VT(0);
@@ -291,17 +437,24 @@ __global__ void __launch_bounds__(1024) normalize_kernel(const VT *__restrict__ 
         return;
     }
     const double inv = 1.0 / sqrt(beta2);
-#pragma unroll
+    const VT vinv = (VT)inv;
+#pragma unroll 4
     for (int v = 0; v < VPT; ++v) {
-        kn[tid + v * T] = (VT)((double)w[tid + v * T] * inv);
-        skn[tid + v * T] = (VT)((double)sw[tid + v * T] * inv);
+        if constexpr (sizeof(VT) == 8) {
+            kn[tid + v * T] = w[tid + v * T] * vinv;
+            skn[tid + v * T] = sw[tid + v * T] * vinv;
+        } else {
+            kn[tid + v * T] = (VT)((double)w[tid + v * T] * inv);
+            skn[tid + v * T] = (VT)((double)sw[tid + v * T] * inv);
+        }
     }
 }
 
 template <typename VT, int VPT>
 cudaError_t mgs_dispatch(const KrylovBatch &b, int n, int need_w, cudaStream_t s)
 {
-    const size_t smem = (size_t)b.shape.m_pad * sizeof(VT);
+    using Cfg = MgsCfg<VT, VPT>;
+    const size_t smem = (size_t)b.shape.m_pad * sizeof(VT) * ((Cfg::kUs ? 1 : 0) + (Cfg::kWs ? 1 : 0));
     static bool configured = false;
     if (!configured) {
         cudaError_t e = cudaFuncSetAttribute(mgs_kernel<VT, VPT>,
