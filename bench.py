@@ -135,16 +135,17 @@ class Clocks:
 
 
 def mgs_algorithmic(nu: int, m: int, vbytes: int, ncols: int):
-    """Bytes the two-pass Gram-Schmidt step must stream and FP64 flops it must do.
+    """Bytes the Gram-Schmidt step must stream and FP64 flops it must do.
 
-    Step n (0-based) with n < nu-1 reads u and, in each of the two passes, the
-    n+1 stored vectors k_i and S k_i, and writes w: (4 (n+1) + 2) m values.
-    The last step only forms h_{i,nu-1} = k_i . u: (nu + 1) m values.
-    Flops: pass 1 two dots and one update, pass 2 one dot and one update per
-    entry and stored vector; the last step one dot.
+    Step n (0-based) reads w_n and S w_n for beta_n = ||w_n||_S (n >= 1) and u;
+    for n < nu-1 it reads, in each of the two passes, the n+1 stored vectors
+    w_i and S w_i, and writes the new w: (4 (n+1) + 2 + 2 [n >= 1]) m values.
+    The last step forms h_{i,nu-1} = k_i . u only: (nu + 1 + 2) m values.
+    Flops: beta one dot; pass 1 two dots and one update, pass 2 one dot and one
+    update per entry and stored vector; the last step beta and one dot.
     """
-    vals = sum(4 * (n + 1) + 2 for n in range(nu - 1)) + (nu + 1)
-    fmas = sum(5 * (n + 1) for n in range(nu - 1)) + nu
+    vals = sum(4 * (n + 1) + 2 + (2 if n >= 1 else 0) for n in range(nu - 1)) + (nu + 1 + 2)
+    fmas = sum(5 * (n + 1) + (1 if n >= 1 else 0) for n in range(nu - 1)) + nu + 1
     return vals * m * vbytes * ncols, 2.0 * fmas * m * ncols
 
 
@@ -228,7 +229,7 @@ def time_e2e(m, t, cols, args, prec, steps, warmup):
         torch.cuda.synchronize()
         ts.append(time.perf_counter() - t0)
     h2d = (8 * (t.n_block_rows + 1) + 4 * t.nnzb + 2 * 128 * t.nnzb + 8 * t.M + 8 * t.nnzb
-           + (2 * 64 * t.nnzb if prec == 1 else 0) + (0 if colsel is None else 8 * len(cols)))
+           + (2 * 128 * t.nnzb if prec == 1 else 0) + (0 if colsel is None else 8 * len(cols)))
     d2h = 2 * 128 * t.nnzb
     return statistics.mean(ts), h2d, d2h
 

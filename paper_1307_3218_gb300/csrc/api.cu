@@ -449,11 +449,16 @@ int marnoldi_setup(marnoldi_ctx **out, int64_t n_block_rows, const int64_t *row_
     c->A.sdiag = dsd;
     c->A.tmap = dtm;
     if (precision == MARNOLDI_MIXED) {
-        std::vector<float> hf(16 * nnzb), sf(16 * nnzb);
-        for (int64_t k = 0; k < 16 * nnzb; ++k) {
-            hf[k] = (float)H_vals[k];
-            sf[k] = (float)S_vals[k];
-        }
+        // each block as 16 FP32 "hi" values then 16 "lo" values, hi + lo = the FP64 value
+        std::vector<float> hf(32 * nnzb), sf(32 * nnzb);
+        for (int64_t k = 0; k < nnzb; ++k)
+            for (int q = 0; q < 16; ++q) {
+                const double h = H_vals[16 * k + q], s = S_vals[16 * k + q];
+                hf[32 * k + q] = (float)h;
+                hf[32 * k + 16 + q] = (float)(h - (double)hf[32 * k + q]);
+                sf[32 * k + q] = (float)s;
+                sf[32 * k + 16 + q] = (float)(s - (double)sf[32 * k + q]);
+            }
         float *dHf = nullptr, *dSf = nullptr;
         if ((rc = dupload(c, &dHf, hf.data(), hf.size(), "H fp32")) ||
             (rc = dupload(c, &dSf, sf.data(), sf.size(), "S fp32"))) {
@@ -614,8 +619,8 @@ int marnoldi_solve(marnoldi_ctx *c, const int64_t *columns, int64_t ncols, int n
     // batch workspace
     const ColumnShape shape = column_shape(c->m);
     const size_t vs = c->prec == 0 ? 8 : 4;
-    const size_t per_col = al((size_t)2 * nu * shape.m_pad * vs) + (size_t)3 * shape.m_pad * vs +
-                           (size_t)nu * nu * 8 + 64;
+    const size_t per_col = al((size_t)2 * nu * shape.m_pad * vs) + (size_t)2 * shape.m_pad * vs +
+                           (size_t)nu * nu * 8 + (size_t)nu * 8 + 64;
     int64_t B = c->batch_override;
     if (B <= 0) {
         size_t freeb = 0, totb = 0;
@@ -627,9 +632,11 @@ int marnoldi_solve(marnoldi_ctx *c, const int64_t *columns, int64_t ncols, int n
     B = std::min<int64_t>(B, 65535 * 32);
     c->last_batch = B;
     const size_t oK = 0, oSK = oK + al((size_t)B * nu * shape.m_pad * vs),
-                 oU = oSK + al((size_t)B * nu * shape.m_pad * vs), oW = oU + al((size_t)B * shape.m_pad * vs),
-                 oSW = oW + al((size_t)B * shape.m_pad * vs), oH = oSW + al((size_t)B * shape.m_pad * vs),
-                 oC = oH + al((size_t)B * nu * nu * 8), oS = oC + al((size_t)B * 8),
+                 oU = oSK + al((size_t)B * nu * shape.m_pad * vs),
+                 oUl = oU + al((size_t)B * shape.m_pad * vs),
+                 oH = oUl + (c->prec == 1 ? al((size_t)B * shape.m_pad * vs) : 0),
+                 oSc = oH + al((size_t)B * nu * nu * 8),
+                 oC = oSc + al((size_t)B * nu * 8), oS = oC + al((size_t)B * 8),
                  oN = oS + al((size_t)B * 4), wtot = oN + al((size_t)B * 4);
     if (c->ws_bytes < wtot) {
         if (c->ws) dfree(c, c->ws, c->ws_bytes);
@@ -649,9 +656,9 @@ int marnoldi_solve(marnoldi_ctx *c, const int64_t *columns, int64_t ncols, int n
     kb.K = wb + oK;
     kb.SK = wb + oSK;
     kb.U = wb + oU;
-    kb.W = wb + oW;
-    kb.SW = wb + oSW;
+    kb.Ulo = c->prec == 1 ? (void *)(wb + oUl) : nullptr;
     kb.Hsub = (double *)(wb + oH);
+    kb.scale = (double *)(wb + oSc);
     kb.cn2 = (double *)(wb + oC);
     kb.status = (int *)(wb + oS);
     kb.nu_eff = (int *)(wb + oN);
@@ -663,19 +670,22 @@ int marnoldi_solve(marnoldi_ctx *c, const int64_t *columns, int64_t ncols, int n
         kb.cols = c->d_cols + start;
         if ((rc = launch(c, KK_INIT, [&] { return launch_init(c->A, kb, c->stream); }))) return rc;
         for (int n = 0; n < nu; ++n) {
+            // slot n holds w_n (unnormalised); the MGS of step n scales it
             const char *Kn = (const char *)kb.K + (size_t)n * mp * vs;
             if ((rc = launch(c, KK_SPMM_H, [&] {
                      return launch_spmm(c->A, 0, kb, Kn, (int64_t)nu * mp, kb.U, mp, c->stream);
                  })))
                 return rc;
             const int need_w = n + 1 < nu;
-            if ((rc = launch(c, KK_MGS, [&] { return launch_mgs(kb, n, need_w, c->stream); }))) return rc;
-            if (!need_w) break;
-            if ((rc = launch(c, KK_SPMM_S, [&] {
-                     return launch_spmm(c->A, 1, kb, kb.W, mp, kb.SW, mp, c->stream);
-                 })))
+            if ((rc = launch(c, KK_MGS, [&] { return launch_mgs(kb, n, need_w, tau, c->stream); })))
                 return rc;
-            if ((rc = launch(c, KK_NORMALIZE, [&] { return launch_normalize(kb, n, tau, c->stream); })))
+            if (!need_w) break;
+            char *Kn1 = (char *)kb.K + (size_t)(n + 1) * mp * vs;
+            char *SKn1 = (char *)kb.SK + (size_t)(n + 1) * mp * vs;
+            if ((rc = launch(c, KK_SPMM_S, [&] {
+                     return launch_spmm(c->A, 1, kb, Kn1, (int64_t)nu * mp, SKn1, (int64_t)nu * mp,
+                                        c->stream);
+                 })))
                 return rc;
         }
         if ((rc = launch(c, KK_EIG, [&] { return launch_eig(c->A, kb, c->st, start, c->stream); }))) return rc;

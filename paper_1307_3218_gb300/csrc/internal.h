@@ -14,7 +14,6 @@ enum KernelKind {
     KK_SPMM_H,
     KK_MGS,
     KK_SPMM_S,
-    KK_NORMALIZE,
     KK_EIG,
     KK_MINMAX,
     KK_COUNT,
@@ -44,8 +43,10 @@ ColumnShape column_shape(int64_t m);
 
 // ---------------------------------------------------------------- Krylov build
 // All pointers are device pointers.  Batch layout (c = batch column):
-//   K[c][i][r], SK[c][i][r] at ((c * nu) + i) * m_pad + r  (i < nu)
-//   U[c][r], W[c][r], SW[c][r] at c * m_pad + r
+//   K[c][i][r], SK[c][i][r] at ((c * nu) + i) * m_pad + r  (i < nu): the
+//     basis vectors *unnormalised*, w_i and S w_i; the S-orthonormal basis is
+//     k_i = scale[c][i] * w_i (scale = 1 / ||w_i||_S, set by the MGS of step i)
+//   U[c][r] at c * m_pad + r: H w_n of the current step
 //   Hsub[c][i][l] at (c * nu + i) * nu + l (double)
 // status[c]: 0 active, 1 stopped (breakdown), 2 non-positive S norm.
 struct KrylovBatch {
@@ -54,8 +55,10 @@ struct KrylovBatch {
     int nu;
     int64_t m;            // vector length
     ColumnShape shape;
-    void *K, *SK, *U, *W, *SW;
+    void *K, *SK, *U;
+    void *Ulo;            // mixed precision: lo word of H w_n (u = U + Ulo to ~2^-48)
     double *Hsub;
+    double *scale;        // [c][nu]
     double *cn2;          // per column: sum_i (c1_i + c2_i)^2 of the last MGS
     int *status;
     int *nu_eff;
@@ -67,7 +70,9 @@ struct DeviceMatrix {
     const int64_t *rp;
     const int32_t *ci;
     const double *Hd, *Sd;   // FP64 values
-    const float *Hf, *Sf;    // FP32 copies (mixed precision), else null
+    // Mixed precision: per block 16 "hi" then 16 "lo" FP32 values with
+    // hi + lo = the FP64 value to about 2^-48 (else null).
+    const float *Hf, *Sf;
     const double *sdiag;     // S_jj, length 4 nbr
     const int64_t *tmap;     // block (J, I) -> index of block (I, J)
 };
@@ -75,8 +80,7 @@ struct DeviceMatrix {
 cudaError_t launch_init(const DeviceMatrix &A, const KrylovBatch &b, cudaStream_t s);
 cudaError_t launch_spmm(const DeviceMatrix &A, int which /*0 H, 1 S*/, const KrylovBatch &b,
                         const void *X, int64_t ldx, void *Y, int64_t ldy, cudaStream_t s);
-cudaError_t launch_mgs(const KrylovBatch &b, int n, int need_w, cudaStream_t s);
-cudaError_t launch_normalize(const KrylovBatch &b, int n, double tau, cudaStream_t s);
+cudaError_t launch_mgs(const KrylovBatch &b, int n, int need_w, double tau, cudaStream_t s);
 
 // ---------------------------------------------------------------- subspace eigensolve
 // Per solved column c (global index col0 + batch column):

@@ -5,16 +5,18 @@
 // L_nu^(j) containing e_j whose nu x nu *standard* eigenproblem replaces
 // H phi = eps S phi, Eq. 2) and the explicit subspace matrix H_sub = K^T H K.
 //
-// One Krylov step n, for every column of the batch:
-//   spmm(H):    u = H k_n                                (BSR 4x4 x batch panel)
-//   mgs:        h_{i,n} = k_i . u (i <= n), then two passes of modified
-//               Gram-Schmidt in the S inner product using the stored S k_i:
-//               c_i = (S k_i) . w, w -= c_i k_i
-//   spmm(S):    S w
-//   normalize:  beta = sqrt(w . S w), k_{n+1} = w / beta, S k_{n+1} = S w / beta,
-//               or stop the column when beta^2 <= tau^2 (beta^2 + sum_i c_i^2),
-//               i.e. ||w||_S <= tau ||u||_S (S-orthogonality of K splits
-//               ||u||_S^2 into beta^2 plus the squared projection coefficients).
+// The basis is stored unnormalised: slot i holds w_i and S w_i, and
+// k_i = s_i w_i with s_i = 1 / ||w_i||_S.  One Krylov step n, for every column:
+//   spmm(H):    H w_n                                    (BSR 4x4 x batch panel)
+//   mgs:        beta_n = sqrt(w_n . S w_n); stop the column when
+//               beta_n^2 <= tau^2 (beta_n^2 + sum_i c_i^2), i.e.
+//               ||w_n||_S <= tau ||u_{n-1}||_S (S-orthogonality of K splits
+//               ||u||_S^2 into beta^2 plus the squared projection coefficients);
+//               else s_n = 1 / beta_n, u = s_n H w_n, h_{i,n} = k_i . u (i <= n),
+//               and two passes of modified Gram-Schmidt in the S inner product
+//               using the stored S w_i: c_i = (S k_i) . w, w -= c_i k_i;
+//               w is written to slot n+1
+//   spmm(S):    S w into slot n+1
 //
 // Inner products are always accumulated in FP64; in mixed precision the
 // vectors, the SpMM and the Gram-Schmidt updates are FP32.  Reductions use a
@@ -28,8 +30,8 @@ namespace marnoldi {
 
 const char *kernel_name(int kind)
 {
-    static const char *names[KK_NKINDS] = {"init",   "spmm_H",  "mgs",   "spmm_S",  "normalize",
-                                           "eigsub", "minmax",  "count", "density", "green"};
+    static const char *names[KK_NKINDS] = {"init",   "spmm_H", "mgs",     "spmm_S", "eigsub",
+                                           "minmax", "count",  "density", "green"};
     return (kind >= 0 && kind < KK_NKINDS) ? names[kind] : "?";
 }
 
@@ -182,8 +184,9 @@ template <typename VT>
 __global__ void init_kernel(const int64_t *__restrict__ rp, const int32_t *__restrict__ ci,
                             const double *__restrict__ Sv, const double *__restrict__ sdiag,
                             const int64_t *__restrict__ cols, VT *__restrict__ K,
-                            VT *__restrict__ SK, int *__restrict__ status,
-                            int *__restrict__ nu_eff, int nu, int64_t m_pad)
+                            VT *__restrict__ SK, double *__restrict__ scale,
+                            int *__restrict__ status, int *__restrict__ nu_eff, int nu,
+                            int64_t m_pad)
 {
     const int c = blockIdx.x;
     const int64_t j = cols[c];
@@ -199,6 +202,7 @@ __global__ void init_kernel(const int64_t *__restrict__ rp, const int32_t *__res
     const double inv = 1.0 / sqrt(sdiag[j]);
     if (threadIdx.x == 0) {
         k0[j] = (VT)inv;
+        scale[(int64_t)c * nu] = 1.0;
         status[c] = 0;
         nu_eff[c] = nu;
     }
@@ -248,6 +252,89 @@ __global__ void __launch_bounds__(256) spmm_kernel(int64_t nbr, const int64_t *_
     store4(Y + (int64_t)c * ldy + 4 * I, acc);
 }
 
+// Mixed precision, matrix blocks stored as 16 "hi" then 16 "lo" FP32 values
+// (hi + lo = the FP64 value to about 2^-48; one 128-byte line per block).
+//
+// S w (spmm_f32_kernel): plain FP32 with the hi values.  Its rounding only
+// perturbs the Gram-Schmidt coefficients and the norms, which the second pass
+// and the subspace Galerkin step absorb.
+//
+// H w (spmm_f32_accurate_kernel): the subspace matrix entries h_{i,n} = k_i . u
+// take u = H k_n at face value, so u is formed to about 2^-48: each product
+// with hi is split exactly (p + e, e = fma(h, x, -p)) and summed with exact
+// two-sums, the lo products and the errors collect in a second FP32 word, and
+// u is written as a normalised (hi, lo) FP32 pair.  The Krylov vector itself
+// continues from the hi word.  The extra FP32 work is hidden behind the
+// gather, which bounds this kernel.
+__global__ void __launch_bounds__(256) spmm_f32_kernel(int64_t nbr, const int64_t *__restrict__ rp,
+                                                       const int32_t *__restrict__ ci,
+                                                       const float *__restrict__ vals,
+                                                       const float *__restrict__ X, int64_t ldx,
+                                                       float *__restrict__ Y, int64_t ldy, int ncols)
+{
+    const int c = blockIdx.y * 32 + threadIdx.x;
+    const int64_t I = (int64_t)blockIdx.x * 8 + threadIdx.y;
+    if (c >= ncols || I >= nbr) return;
+    const float *x = X + (int64_t)c * ldx;
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+    const int64_t k1 = rp[I + 1];
+    for (int64_t k = rp[I]; k < k1; ++k) {
+        const float *B = vals + 32 * k;
+        float r0[4], r1[4], r2[4], r3[4], xv[4];
+        load4(x + 4 * (int64_t)ci[k], xv);
+        load4(B, r0);
+        load4(B + 4, r1);
+        load4(B + 8, r2);
+        load4(B + 12, r3);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            acc[0] = fmaf(r0[q], xv[q], acc[0]);
+            acc[1] = fmaf(r1[q], xv[q], acc[1]);
+            acc[2] = fmaf(r2[q], xv[q], acc[2]);
+            acc[3] = fmaf(r3[q], xv[q], acc[3]);
+        }
+    }
+    store4(Y + (int64_t)c * ldy + 4 * I, acc);
+}
+
+__global__ void __launch_bounds__(256) spmm_f32_accurate_kernel(
+    int64_t nbr, const int64_t *__restrict__ rp, const int32_t *__restrict__ ci,
+    const float *__restrict__ vals, const float *__restrict__ X, int64_t ldx,
+    float *__restrict__ Y, float *__restrict__ Ylo, int64_t ldy, int ncols)
+{
+    const int c = blockIdx.y * 32 + threadIdx.x;
+    const int64_t I = (int64_t)blockIdx.x * 8 + threadIdx.y;
+    if (c >= ncols || I >= nbr) return;
+    const float *x = X + (int64_t)c * ldx;
+    float hi[4] = {0.f, 0.f, 0.f, 0.f}, lo[4] = {0.f, 0.f, 0.f, 0.f};
+    const int64_t k1 = rp[I + 1];
+    for (int64_t k = rp[I]; k < k1; ++k) {
+        const float *B = vals + 32 * k;
+        float xv[4];
+        load4(x + 4 * (int64_t)ci[k], xv);
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+            float h[4], l[4];
+            load4(B + 4 * a, h);
+            load4(B + 16 + 4 * a, l);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const float p = __fmul_rn(h[q], xv[q]);
+                const float e = __fmaf_rn(h[q], xv[q], -p);
+                df_add(hi[a], lo[a], p, __fmaf_rn(l[q], xv[q], e));
+            }
+        }
+    }
+    float yh[4], yl[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {   // renormalise: yh = fl(hi + lo), yl = the rest
+        yh[a] = __fadd_rn(hi[a], lo[a]);
+        yl[a] = __fsub_rn(lo[a], __fsub_rn(yh[a], hi[a]));
+    }
+    store4(Y + (int64_t)c * ldy + 4 * I, yh);
+    store4(Ylo + (int64_t)c * ldy + 4 * I, yl);
+}
+
 // ------------------------------------------------------------------ MGS
 // One CTA per column; thread t owns entries r = t + v T (v < VPT) of the
 // column's vectors.  Small VPT keeps w in registers.  VPT = 16 (m > 8192)
@@ -255,28 +342,52 @@ __global__ void __launch_bounds__(256) spmm_kernel(int64_t nbr, const int64_t *_
 // with u in shared memory too when both fit, else re-read from global memory
 // (an L2 hit: the SpMM has just written it).  Entries are visited in chunks
 // with a compiler barrier between chunks so that only one chunk's loads are
-// live per thread.  k_i is held across the reduction when it fits in
-// registers, else re-read after it (an L2 hit).
+// live per thread.  The stored w_i is held across the reduction when it fits
+// in registers, else re-read after it (an L2 hit).
 template <typename VT, int VPT>
 struct MgsCfg {
+    static constexpr bool kLo = sizeof(VT) == 4;                             // u as (hi, lo) pair
     static constexpr bool kWs = VPT >= 16;                                   // w in smem
-    static constexpr bool kUs = !kWs || 2 * VPT * 1024 * sizeof(VT) <= 160 * 1024;  // u in smem
+    static constexpr bool kUs = kLo || !kWs || 2 * VPT * 1024 * sizeof(VT) <= 160 * 1024;  // u in smem
     static constexpr bool kHold = VPT * sizeof(VT) <= 64;
     static constexpr int kChunk = sizeof(VT) == 8 ? 4 : 8;
+    static constexpr int kSmemVectors = (kUs ? 1 : 0) + (kLo ? 1 : 0) + (kWs ? 1 : 0);
 };
 
+// y -= a x over the thread's entries (x from registers or re-read).
+template <typename VT, int VPT, int kChunk, bool kHold, bool kWs>
+__device__ __forceinline__ void axpy_entries(VT (&wr)[kWs ? 1 : VPT], VT *ws,
+                                             const VT (&kv)[kHold ? VPT : 1],
+                                             const VT *__restrict__ x, int tid, int T, VT a)
+{
+#pragma unroll
+    for (int v0 = 0; v0 < VPT; v0 += kChunk) {
+#pragma unroll
+        for (int q = 0; q < kChunk; ++q) {
+            const int v = v0 + q;
+            if (v >= VPT) break;
+            const int r = tid + v * T;
+            VT kr;
+            if constexpr (kHold) kr = kv[v]; else kr = x[r];
+            if constexpr (kWs) ws[r] = fma(-a, kr, ws[r]); else wr[v] = fma(-a, kr, wr[v]);
+        }
+        if (v0 + kChunk < VPT) asm volatile("" ::: "memory");
+    }
+}
+
 template <typename VT, int VPT>
-__global__ void __launch_bounds__(1024, 1) mgs_kernel(const VT *__restrict__ K,
-                                                      const VT *__restrict__ SK,
+__global__ void __launch_bounds__(1024, 1) mgs_kernel(VT *__restrict__ K, VT *__restrict__ SK,
                                                       const VT *__restrict__ U,
-                                                      VT *__restrict__ W,
+                                                      const VT *__restrict__ Ulo,
                                                       double *__restrict__ Hsub,
+                                                      double *__restrict__ scale,
                                                       double *__restrict__ cn2,
-                                                      const int *__restrict__ status, int n,
-                                                      int nu, int64_t m_pad, int need_w)
+                                                      int *__restrict__ status,
+                                                      int *__restrict__ nu_eff, int n, int nu,
+                                                      int64_t m_pad, int need_w, double tau2)
 {
     using Cfg = MgsCfg<VT, VPT>;
-    constexpr bool kWs = Cfg::kWs, kUs = Cfg::kUs, kHold = Cfg::kHold;
+    constexpr bool kWs = Cfg::kWs, kUs = Cfg::kUs, kHold = Cfg::kHold, kLo = Cfg::kLo;
     constexpr int kChunk = Cfg::kChunk;
     const int c = blockIdx.x;
     if (status[c] != 0) return;
@@ -285,24 +396,61 @@ __global__ void __launch_bounds__(1024, 1) mgs_kernel(const VT *__restrict__ K,
     const int T = VPT >= 8 ? 1024 : (int)blockDim.x;
     const int tid = threadIdx.x;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    VT *us = reinterpret_cast<VT *>(smem_raw);             // u (if kUs)
-    VT *ws = us + (kUs ? m_pad : 0);                        // w (if kWs)
+    VT *us = reinterpret_cast<VT *>(smem_raw);             // u = H w_n, unscaled (if kUs)
+    VT *uls = us + (kUs ? m_pad : 0);                       // its lo word (mixed precision)
+    VT *ws = uls + (kLo ? m_pad : 0);                       // w (if kWs)
     __shared__ RedShared red;
     __shared__ double ctot[kMaxNu];
+    __shared__ double ssc[kMaxNu];
     const int64_t base = (int64_t)c * nu * m_pad;
-    const VT *u = U + (int64_t)c * m_pad;
+    int buf = 0;
 
+    for (int i = tid; i < n; i += T) ssc[i] = scale[(int64_t)c * nu + i];
+    // beta_n = ||w_n||_S and the breakdown test (slot 0 is stored normalised)
+    double sn = 1.0;
+    if (n > 0) {
+        const VT *wn = K + base + (int64_t)n * m_pad;
+        const VT *swn = SK + base + (int64_t)n * m_pad;
+        DotAcc<VT> acc;
+#pragma unroll
+        for (int v0 = 0; v0 < VPT; v0 += kChunk) {
+#pragma unroll
+            for (int q = 0; q < kChunk; ++q) {
+                const int v = v0 + q;
+                if (v >= VPT) break;
+                acc.add(wn[tid + v * T], swn[tid + v * T]);
+            }
+            if (v0 + kChunk < VPT) asm volatile("" ::: "memory");
+        }
+        const double beta2 = block_sum2(acc, DotAcc<VT>(), red, buf).x;
+        if (!(beta2 > 0.0) || beta2 <= tau2 * (beta2 + cn2[c])) {
+            if (tid == 0) {
+                status[c] = (beta2 >= 0.0) ? 1 : 2;   // 2: negative or NaN S-norm
+                nu_eff[c] = n;
+            }
+            return;
+        }
+        sn = 1.0 / sqrt(beta2);
+        if (tid == 0) scale[(int64_t)c * nu + n] = sn;
+    }
+    __syncthreads();   // ssc visible
+    // w starts as u = s_n H w_n; the h dots use H w_n unscaled (with its lo
+    // word in mixed precision) and apply s_i s_n in FP64 after the reduction
+    const VT vsn = (VT)sn;
+    const VT *u = U + (int64_t)c * m_pad;
+    const VT *ul = kLo ? Ulo + (int64_t)c * m_pad : nullptr;
     VT wr[kWs ? 1 : VPT];
 #pragma unroll
     for (int v = 0; v < VPT; ++v) {
         const int r = tid + v * T;
         const VT x = u[r];
-        if constexpr (kWs) ws[r] = x; else wr[v] = x;
+        if constexpr (kWs) ws[r] = x * vsn; else wr[v] = x * vsn;
         if constexpr (kUs) us[r] = x;
+        if constexpr (kLo) uls[r] = ul[r];
     }
-    int buf = 0;
     // pass 1: h_{i,n} = k_i . u and the first Gram-Schmidt sweep
     for (int i = 0; i <= n; ++i) {
+        const double si = i == n ? sn : ssc[i];
         const VT *ki = K + base + (int64_t)i * m_pad;
         const VT *ski = SK + base + (int64_t)i * m_pad;
         DotAcc<VT> ac, ah;
@@ -319,6 +467,7 @@ __global__ void __launch_bounds__(1024, 1) mgs_kernel(const VT *__restrict__ K,
                 VT uu;
                 if constexpr (kUs) uu = us[r]; else uu = u[r];
                 ah.add(kr, uu);
+                if constexpr (kLo) ah.add(kr, uls[r]);
                 if (need_w) {
                     VT wv;
                     if constexpr (kWs) wv = ws[r]; else wv = wr[v];
@@ -328,31 +477,19 @@ __global__ void __launch_bounds__(1024, 1) mgs_kernel(const VT *__restrict__ K,
             if (v0 + kChunk < VPT) asm volatile("" ::: "memory");
         }
         const double2 s = block_sum2(ac, ah, red, buf);
-        if (need_w) {
-            const VT cc = (VT)s.x;
-#pragma unroll
-            for (int v0 = 0; v0 < VPT; v0 += kChunk) {
-#pragma unroll
-                for (int q = 0; q < kChunk; ++q) {
-                    const int v = v0 + q;
-                    if (v >= VPT) break;
-                    const int r = tid + v * T;
-                    VT kr;
-                    if constexpr (kHold) kr = kv[v]; else kr = ki[r];
-                    if constexpr (kWs) ws[r] = fma(-cc, kr, ws[r]); else wr[v] = fma(-cc, kr, wr[v]);
-                }
-                if (v0 + kChunk < VPT) asm volatile("" ::: "memory");
-            }
-        }
+        const double ci = s.x * si, hi = s.y * si * sn;
+        if (need_w)
+            axpy_entries<VT, VPT, kChunk, kHold, kWs>(wr, ws, kv, ki, tid, T, (VT)(ci * si));
         if (tid == 0) {
-            ctot[i] = s.x;
-            Hsub[((int64_t)c * nu + i) * nu + n] = s.y;
-            Hsub[((int64_t)c * nu + n) * nu + i] = s.y;
+            ctot[i] = ci;
+            Hsub[((int64_t)c * nu + i) * nu + n] = hi;
+            Hsub[((int64_t)c * nu + n) * nu + i] = hi;
         }
     }
     if (!need_w) return;
     // pass 2: second Gram-Schmidt sweep
     for (int i = 0; i <= n; ++i) {
+        const double si = i == n ? sn : ssc[i];
         const VT *ki = K + base + (int64_t)i * m_pad;
         const VT *ski = SK + base + (int64_t)i * m_pad;
         DotAcc<VT> ac;
@@ -371,24 +508,11 @@ __global__ void __launch_bounds__(1024, 1) mgs_kernel(const VT *__restrict__ K,
             }
             if (v0 + kChunk < VPT) asm volatile("" ::: "memory");
         }
-        const double2 s = block_sum2(ac, DotAcc<VT>(), red, buf);
-        const VT cc = (VT)s.x;
-#pragma unroll
-        for (int v0 = 0; v0 < VPT; v0 += kChunk) {
-#pragma unroll
-            for (int q = 0; q < kChunk; ++q) {
-                const int v = v0 + q;
-                if (v >= VPT) break;
-                const int r = tid + v * T;
-                VT kr;
-                if constexpr (kHold) kr = kv[v]; else kr = ki[r];
-                if constexpr (kWs) ws[r] = fma(-cc, kr, ws[r]); else wr[v] = fma(-cc, kr, wr[v]);
-            }
-            if (v0 + kChunk < VPT) asm volatile("" ::: "memory");
-        }
-        if (tid == 0) ctot[i] += s.x;
+        const double ci = block_sum2(ac, DotAcc<VT>(), red, buf).x * si;
+        axpy_entries<VT, VPT, kChunk, kHold, kWs>(wr, ws, kv, ki, tid, T, (VT)(ci * si));
+        if (tid == 0) ctot[i] += ci;
     }
-    VT *wo = W + (int64_t)c * m_pad;
+    VT *wo = K + base + (int64_t)(n + 1) * m_pad;   // the next slot, unnormalised
 #pragma unroll
     for (int v = 0; v < VPT; ++v) {
         const int r = tid + v * T;
@@ -401,105 +525,35 @@ __global__ void __launch_bounds__(1024, 1) mgs_kernel(const VT *__restrict__ K,
     }
 }
 
-// ------------------------------------------------------------------ normalize
 template <typename VT, int VPT>
-__global__ void __launch_bounds__(1024) normalize_kernel(const VT *__restrict__ W,
-                                                         const VT *__restrict__ SW,
-                                                         VT *__restrict__ K, VT *__restrict__ SK,
-                                                         const double *__restrict__ cn2,
-                                                         int *__restrict__ status,
-                                                         int *__restrict__ nu_eff, int n, int nu,
-                                                         int64_t m_pad, double tau2)
-{
-    const int c = blockIdx.x;
-    if (status[c] != 0) return;
-    __shared__ RedShared red;
-    const int T = VPT >= 8 ? 1024 : (int)blockDim.x, tid = threadIdx.x;
-    const VT *w = W + (int64_t)c * m_pad;
-    const VT *sw = SW + (int64_t)c * m_pad;
-    DotAcc<VT> acc;
-#pragma unroll 4
-    for (int v = 0; v < VPT; ++v) acc.add(w[tid + v * T], sw[tid + v * T]);
-    int buf = 0;
-    const double beta2 = block_sum2(acc, DotAcc<VT>(), red, buf).x;
-    VT *kn = K + ((int64_t)c * nu + n + 1) * m_pad;
-    VT *skn = SK + ((int64_t)c * nu + n + 1) * m_pad;
-    if (!(beta2 > 0.0) || beta2 <= tau2 * (beta2 + cn2[c])) {
-        if (tid == 0) {
-            status[c] = (beta2 >= 0.0) ? 1 : 2;   // 2: negative or NaN S-norm
-            nu_eff[c] = n + 1;
-        }
-#pragma unroll 4
-        for (int v = 0; v < VPT; ++v) {
-            kn[tid + v * T] = VT(0);
-            skn[tid + v * T] = VT(0);
-        }
-        return;
-    }
-    const double inv = 1.0 / sqrt(beta2);
-    const VT vinv = (VT)inv;
-#pragma unroll 4
-    for (int v = 0; v < VPT; ++v) {
-        if constexpr (sizeof(VT) == 8) {
-            kn[tid + v * T] = w[tid + v * T] * vinv;
-            skn[tid + v * T] = sw[tid + v * T] * vinv;
-        } else {
-            kn[tid + v * T] = (VT)((double)w[tid + v * T] * inv);
-            skn[tid + v * T] = (VT)((double)sw[tid + v * T] * inv);
-        }
-    }
-}
-
-template <typename VT, int VPT>
-cudaError_t mgs_dispatch(const KrylovBatch &b, int n, int need_w, cudaStream_t s)
+cudaError_t mgs_dispatch(const KrylovBatch &b, int n, int need_w, double tau, cudaStream_t s)
 {
     using Cfg = MgsCfg<VT, VPT>;
-    const size_t smem = (size_t)b.shape.m_pad * sizeof(VT) * ((Cfg::kUs ? 1 : 0) + (Cfg::kWs ? 1 : 0));
+    const size_t smem = (size_t)b.shape.m_pad * sizeof(VT) * Cfg::kSmemVectors;
     static bool configured = false;
     if (!configured) {
+        const int maxs = (int)((size_t)VPT * 1024 * sizeof(VT) * Cfg::kSmemVectors);
         cudaError_t e = cudaFuncSetAttribute(mgs_kernel<VT, VPT>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)(kMaxGlobalM * sizeof(double)));
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, maxs);
         if (e != cudaSuccess) return e;
         configured = true;
     }
     mgs_kernel<VT, VPT><<<b.nb, b.shape.threads, smem, s>>>(
-        (const VT *)b.K, (const VT *)b.SK, (const VT *)b.U, (VT *)b.W, b.Hsub, b.cn2, b.status, n,
-        b.nu, b.shape.m_pad, need_w);
-    return cudaGetLastError();
-}
-
-template <typename VT, int VPT>
-cudaError_t normalize_dispatch(const KrylovBatch &b, int n, double tau, cudaStream_t s)
-{
-    normalize_kernel<VT, VPT><<<b.nb, b.shape.threads, 0, s>>>(
-        (const VT *)b.W, (const VT *)b.SW, (VT *)b.K, (VT *)b.SK, b.cn2, b.status, b.nu_eff, n,
-        b.nu, b.shape.m_pad, tau * tau);
+        (VT *)b.K, (VT *)b.SK, (const VT *)b.U, (const VT *)b.Ulo, b.Hsub, b.scale, b.cn2,
+        b.status, b.nu_eff, n,
+        b.nu, b.shape.m_pad, need_w, tau * tau);
     return cudaGetLastError();
 }
 
 template <typename VT>
-cudaError_t mgs_vpt(const KrylovBatch &b, int n, int need_w, cudaStream_t s)
+cudaError_t mgs_vpt(const KrylovBatch &b, int n, int need_w, double tau, cudaStream_t s)
 {
     switch (b.shape.vpt) {
-    case 1: return mgs_dispatch<VT, 1>(b, n, need_w, s);
-    case 2: return mgs_dispatch<VT, 2>(b, n, need_w, s);
-    case 4: return mgs_dispatch<VT, 4>(b, n, need_w, s);
-    case 8: return mgs_dispatch<VT, 8>(b, n, need_w, s);
-    case 16: return mgs_dispatch<VT, 16>(b, n, need_w, s);
-    default: return cudaErrorInvalidValue;
-    }
-}
-
-template <typename VT>
-cudaError_t normalize_vpt(const KrylovBatch &b, int n, double tau, cudaStream_t s)
-{
-    switch (b.shape.vpt) {
-    case 1: return normalize_dispatch<VT, 1>(b, n, tau, s);
-    case 2: return normalize_dispatch<VT, 2>(b, n, tau, s);
-    case 4: return normalize_dispatch<VT, 4>(b, n, tau, s);
-    case 8: return normalize_dispatch<VT, 8>(b, n, tau, s);
-    case 16: return normalize_dispatch<VT, 16>(b, n, tau, s);
+    case 1: return mgs_dispatch<VT, 1>(b, n, need_w, tau, s);
+    case 2: return mgs_dispatch<VT, 2>(b, n, need_w, tau, s);
+    case 4: return mgs_dispatch<VT, 4>(b, n, need_w, tau, s);
+    case 8: return mgs_dispatch<VT, 8>(b, n, need_w, tau, s);
+    case 16: return mgs_dispatch<VT, 16>(b, n, need_w, tau, s);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -510,11 +564,11 @@ cudaError_t launch_init(const DeviceMatrix &A, const KrylovBatch &b, cudaStream_
 {
     if (b.prec == 0)
         init_kernel<double><<<b.nb, 256, 0, s>>>(A.rp, A.ci, A.Sd, A.sdiag, b.cols, (double *)b.K,
-                                                 (double *)b.SK, b.status, b.nu_eff, b.nu,
+                                                 (double *)b.SK, b.scale, b.status, b.nu_eff, b.nu,
                                                  b.shape.m_pad);
     else
         init_kernel<float><<<b.nb, 256, 0, s>>>(A.rp, A.ci, A.Sd, A.sdiag, b.cols, (float *)b.K,
-                                                (float *)b.SK, b.status, b.nu_eff, b.nu,
+                                                (float *)b.SK, b.scale, b.status, b.nu_eff, b.nu,
                                                 b.shape.m_pad);
     return cudaGetLastError();
 }
@@ -527,20 +581,18 @@ cudaError_t launch_spmm(const DeviceMatrix &A, int which, const KrylovBatch &b, 
     if (b.prec == 0)
         spmm_kernel<double><<<grid, block, 0, s>>>(A.nbr, A.rp, A.ci, which ? A.Sd : A.Hd,
                                                    (const double *)X, ldx, (double *)Y, ldy, b.nb);
+    else if (which == 0)
+        spmm_f32_accurate_kernel<<<grid, block, 0, s>>>(A.nbr, A.rp, A.ci, A.Hf, (const float *)X,
+                                                        ldx, (float *)Y, (float *)b.Ulo, ldy, b.nb);
     else
-        spmm_kernel<float><<<grid, block, 0, s>>>(A.nbr, A.rp, A.ci, which ? A.Sf : A.Hf,
-                                                  (const float *)X, ldx, (float *)Y, ldy, b.nb);
+        spmm_f32_kernel<<<grid, block, 0, s>>>(A.nbr, A.rp, A.ci, A.Sf, (const float *)X, ldx,
+                                               (float *)Y, ldy, b.nb);
     return cudaGetLastError();
 }
 
-cudaError_t launch_mgs(const KrylovBatch &b, int n, int need_w, cudaStream_t s)
+cudaError_t launch_mgs(const KrylovBatch &b, int n, int need_w, double tau, cudaStream_t s)
 {
-    return b.prec == 0 ? mgs_vpt<double>(b, n, need_w, s) : mgs_vpt<float>(b, n, need_w, s);
-}
-
-cudaError_t launch_normalize(const KrylovBatch &b, int n, double tau, cudaStream_t s)
-{
-    return b.prec == 0 ? normalize_vpt<double>(b, n, tau, s) : normalize_vpt<float>(b, n, tau, s);
+    return b.prec == 0 ? mgs_vpt<double>(b, n, need_w, tau, s) : mgs_vpt<float>(b, n, need_w, tau, s);
 }
 
 }  // namespace marnoldi

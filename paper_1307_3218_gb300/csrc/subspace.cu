@@ -48,7 +48,8 @@ __device__ __forceinline__ double fermi(double x)
 template <typename VT>
 __global__ void __launch_bounds__(kEigThreads) eig_kernel(
     const double *__restrict__ Hsub, const int *__restrict__ bnu_eff,
-    const int *__restrict__ bstatus, const VT *__restrict__ K, int64_t m_pad, int nu, const int64_t *__restrict__ bcols,
+    const int *__restrict__ bstatus, const double *__restrict__ bscale, const VT *__restrict__ K,
+    int64_t m_pad, int nu, const int64_t *__restrict__ bcols,
     const double *__restrict__ sdiag, const int64_t *__restrict__ rp,
     const int32_t *__restrict__ ci, int64_t col0, int *__restrict__ nu_eff_out,
     double *__restrict__ eps_out, double *__restrict__ w_out, double *__restrict__ t_out,
@@ -241,10 +242,15 @@ __global__ void __launch_bounds__(kEigThreads) eig_kernel(
         A[i * nu + a] = Q[i * nu + perm[a]];
     }
     for (int a = tid; a < n; a += T) pp[a] = d[perm[a]];
-    // q = K^T e_j: entry j of every basis vector (global mode: local row = j)
+    // basis scales k_i = s_i w_i (e is free after QL); q = K^T e_j: entry j of
+    // every basis vector (global mode: local row = j)
     const int64_t j = bcols[c];
     const VT *Kc = K + (int64_t)c * nu * m_pad;
-    for (int i = tid; i < n; i += T) vv[i] = (double)Kc[(int64_t)i * m_pad + j];
+    for (int i = tid; i < n; i += T) {
+        const double si = bscale[(int64_t)c * nu + i];
+        e[i] = si;
+        vv[i] = si * (double)Kc[(int64_t)i * m_pad + j];
+    }
     __syncthreads();
     const double sq = sqrt(sdiag[j]);
     for (int a = tid; a < nu; a += T) {
@@ -269,7 +275,8 @@ __global__ void __launch_bounds__(kEigThreads) eig_kernel(
         double s = 0.0;
         if (a < n) {
             const int64_t row = 4 * (int64_t)ci[kb + (r >> 2)] + (r & 3);
-            for (int i = 0; i < n; ++i) s = fma((double)Kc[(int64_t)i * m_pad + row], A[i * nu + a], s);
+            for (int i = 0; i < n; ++i)
+                s = fma(e[i] * (double)Kc[(int64_t)i * m_pad + row], A[i * nu + a], s);
         }
         P[idx] = s;
     }
@@ -461,7 +468,7 @@ cudaError_t eig_dispatch(const DeviceMatrix &A, const KrylovBatch &b, const Colu
         configured = true;
     }
     eig_kernel<VT><<<b.nb, kEigThreads, smem, s>>>(
-        b.Hsub, b.nu_eff, b.status, (const VT *)b.K, b.shape.m_pad, nu, b.cols, A.sdiag, A.rp, A.ci, col0,
+        b.Hsub, b.nu_eff, b.status, b.scale, (const VT *)b.K, b.shape.m_pad, nu, b.cols, A.sdiag, A.rp, A.ci, col0,
         st.nu_eff, st.eps, st.w, st.t, st.P, st.p_off, st.eig_status);
     return cudaGetLastError();
 }
