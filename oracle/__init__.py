@@ -189,6 +189,95 @@ def columns(sysm, cols, nu: int, tau: float = TAU_FP64, full_rows: bool = False,
     return Columns(cols, nu, nu_eff, eps, w, t, row_off, rows, Y)
 
 
+def region(positions: np.ndarray, box: np.ndarray, J: int, n_reg: int) -> np.ndarray:
+    """Projection region of atom J: the n_reg atoms nearest J, ascending atom index.
+
+    Distance: squared minimum-image distance, each component
+    d = x_i - x_J - L rint((x_i - x_J) / L), summed as (dx^2 + dy^2) + dz^2;
+    ties go to the lower atom index.  J itself (distance 0) is always inside.
+    """
+    d = positions - positions[J]
+    d = d - box * np.round(d / box)
+    d2 = (d[:, 0] * d[:, 0] + d[:, 1] * d[:, 1]) + d[:, 2] * d[:, 2]
+    order = np.lexsort((np.arange(positions.shape[0]), d2))[:n_reg]
+    return np.sort(order)
+
+
+def local_system(sysm, R: np.ndarray):
+    """Principal sub-pair of (H, S) on the atoms R (ascending): BSR arrays in local numbering."""
+    R = np.asarray(R, dtype=np.int64)
+    rows, cols, ks = [], [], []
+    for q, I in enumerate(R):
+        k0, k1 = int(sysm.row_ptr[I]), int(sysm.row_ptr[I + 1])
+        J = sysm.col_idx[k0:k1].astype(np.int64)
+        pos = np.searchsorted(R, J)
+        ok = (pos < R.size) & (R[np.minimum(pos, R.size - 1)] == J)
+        rows.append(np.full(ok.sum(), q))
+        cols.append(pos[ok])
+        ks.append(np.arange(k0, k1)[ok])
+    rows = np.concatenate(rows)
+    rp = np.zeros(R.size + 1, np.int64)
+    np.add.at(rp, rows + 1, 1)
+    rp = np.cumsum(rp)
+    ks = np.concatenate(ks)
+    return (R.size, rp, np.concatenate(cols).astype(np.int32),
+            np.ascontiguousarray(sysm.H[ks]), np.ascontiguousarray(sysm.S[ks]))
+
+
+def regional_columns(sysm, cols, nu: int, n_reg: int, positions=None, box=None,
+                     tau: float = TAU_FP64, nthreads: int = 0) -> Columns:
+    """Columns solved in regional mode: each column's Krylov process runs on the
+    principal sub-pair of (H, S) over its atom's projection region.  Pattern rows
+    of atoms outside the region are zero."""
+    import concurrent.futures as cf
+    s = sysm.structure
+    positions = s.positions if positions is None else positions
+    box = s.box if box is None else box
+    cols = np.ascontiguousarray(cols, dtype=np.int64)
+    nc = cols.size
+    rows_l = [pattern_rows(sysm, int(j)) for j in cols]
+    row_off = np.zeros(nc + 1, np.int64)
+    row_off[1:] = np.cumsum([r.size for r in rows_l])
+    rows = np.concatenate(rows_l) if nc else np.zeros(0, np.int64)
+    nu_eff = np.zeros(nc, np.int32)
+    eps = np.zeros((nc, nu)); w = np.zeros((nc, nu)); t = np.zeros((nc, nu))
+    Y = np.zeros((int(row_off[-1]), nu))
+    cache: dict = {}
+
+    def one(q):
+        j = int(cols[q])
+        J, b = j // 4, j % 4
+        if J not in cache:
+            R = region(positions, box, J, n_reg)
+            cache[J] = (R, local_system(sysm, R))
+        R, (nb, lrp, lci, lH, lS) = cache[J]
+        jl = 4 * int(np.searchsorted(R, J)) + b
+        grows = rows_l[q]
+        gatoms = grows // 4
+        pos = np.searchsorted(R, gatoms)
+        inside = (pos < R.size) & (R[np.minimum(pos, R.size - 1)] == gatoms)
+        lrows = np.ascontiguousarray(4 * pos[inside] + grows[inside] % 4, dtype=np.int64)
+        e_ = np.zeros(nu); w_ = np.zeros(nu); t_ = np.zeros(nu)
+        Yl = np.zeros((lrows.size, nu))
+        r = _lib().oracle_column(nb, _p(lrp), _p(lci), _p(lH), _p(lS), jl, int(nu), float(tau),
+                                 lrows.size, _p(lrows), _p(e_), _p(w_), _p(t_), _p(Yl), None, None)
+        if r < 0:
+            raise RuntimeError(f"oracle column {j} failed: {r}")
+        nu_eff[q] = r
+        eps[q], w[q], t[q] = e_, w_, t_
+        seg = np.zeros((grows.size, nu))
+        seg[inside] = Yl
+        Y[row_off[q]:row_off[q + 1]] = seg
+
+    # per-atom regions first (serial), then the columns in parallel (the C calls release the GIL)
+    for J in sorted({int(j) // 4 for j in cols}):
+        R = region(positions, box, J, n_reg)
+        cache[J] = (R, local_system(sysm, R))
+    with cf.ThreadPoolExecutor(max_workers=nthreads or os.cpu_count() or 1) as ex:
+        list(ex.map(one, range(nc)))
+    return Columns(cols, nu, nu_eff, eps, w, t, row_off, rows, Y)
+
+
 def valid_levels(c: Columns) -> tuple[np.ndarray, np.ndarray]:
     """(eps, w) of the nu_eff valid levels of every column, concatenated."""
     mask = np.arange(c.nu)[None, :] < c.nu_eff[:, None]
@@ -266,11 +355,14 @@ class Solution:
 
 
 def solve(sysm, nu: int, kT: float, Ne: float | None = None, mu_fixed: float | None = None,
-          cols=None, tau: float = TAU_FP64, nthreads: int = 0) -> Solution:
+          cols=None, tau: float = TAU_FP64, nthreads: int = 0, region_atoms: int = 0) -> Solution:
     """The whole path: every column's subspace, the Fermi level, rho and rho^E on H's pattern, E_band."""
     if cols is None:
         cols = sysm.real_columns()
-    c = columns(sysm, cols, nu, tau=tau, nthreads=nthreads)
+    if region_atoms:
+        c = regional_columns(sysm, cols, nu, region_atoms, tau=tau, nthreads=nthreads)
+    else:
+        c = columns(sysm, cols, nu, tau=tau, nthreads=nthreads)
     e, w = valid_levels(c)
     if mu_fixed is None:
         Ne = sysm.n_electrons if Ne is None else Ne

@@ -74,6 +74,12 @@ struct marnoldi_ctx {
     int64_t batch_override = 0;
     int64_t last_batch = 0;
 
+    // regional mode: positions, box, cell list (built on first use) and the
+    // last search radius that worked
+    bool cells_ready = false;
+    RegionMaps rm{};
+    double region_rs = 0.0;
+
     // instrumentation
     int64_t launches[KK_NKINDS] = {};
     double ms[KK_NKINDS] = {};
@@ -323,6 +329,93 @@ int validate_structure(marnoldi_ctx *c, const double *H, const double *S)
     return MARNOLDI_OK;
 }
 
+// Regional mode, once per context: positions wrapped into the box, a cell list
+// of edge >= 2.6 A (counting sort of atoms by cell), and the longest block row.
+int build_cells(marnoldi_ctx *c)
+{
+    if (c->cells_ready) return MARNOLDI_OK;
+    const int64_t n = c->nbr;
+    for (int d = 0; d < 3; ++d)
+        if (!(c->box[d] > 0.0) || !std::isfinite(c->box[d]))
+            return fail(c, MARNOLDI_EINVAL, "box lengths must be positive and finite");
+    std::vector<double> pos(3 * n);
+    for (int64_t a = 0; a < n; ++a)
+        for (int d = 0; d < 3; ++d) {
+            double x = std::fmod(c->pos[3 * a + d], c->box[d]);
+            if (x < 0.0) x += c->box[d];
+            if (!std::isfinite(x)) return fail(c, MARNOLDI_EINVAL, "non-finite atom position");
+            pos[3 * a + d] = x;
+        }
+    RegionMaps &rm = c->rm;
+    for (int d = 0; d < 3; ++d) {
+        rm.ncell[d] = (int)std::max(1.0, std::min(256.0, std::floor(c->box[d] / 2.6)));
+        rm.cell_edge[d] = c->box[d] / rm.ncell[d];
+    }
+    const int64_t ncells = (int64_t)rm.ncell[0] * rm.ncell[1] * rm.ncell[2];
+    std::vector<int> cell_of(n), start(ncells + 1, 0), atoms(n);
+    for (int64_t a = 0; a < n; ++a) {
+        int ix[3];
+        for (int d = 0; d < 3; ++d)
+            ix[d] = std::min(rm.ncell[d] - 1, std::max(0, (int)(pos[3 * a + d] / rm.cell_edge[d])));
+        cell_of[a] = (ix[2] * rm.ncell[1] + ix[1]) * rm.ncell[0] + ix[0];
+        ++start[cell_of[a] + 1];
+    }
+    for (int64_t q = 0; q < ncells; ++q) start[q + 1] += start[q];
+    std::vector<int> fill(start.begin(), start.end() - 1);
+    for (int64_t a = 0; a < n; ++a) atoms[fill[cell_of[a]]++] = (int)a;
+    int maxrow = 1;
+    for (int64_t I = 0; I < n; ++I) maxrow = std::max<int>(maxrow, (int)(c->rp[I + 1] - c->rp[I]));
+    rm.maxrow = maxrow;
+    double *dpos = nullptr, *dbox = nullptr;
+    int *dst = nullptr, *dat = nullptr;
+    int rc;
+    if ((rc = dupload(c, &dpos, pos.data(), pos.size(), "positions")) ||
+        (rc = dupload(c, &dbox, c->box.data(), 3, "box")) ||
+        (rc = dupload(c, &dst, start.data(), start.size(), "cell starts")) ||
+        (rc = dupload(c, &dat, atoms.data(), atoms.size(), "cell atoms")))
+        return rc;
+    rm.pos = dpos;
+    rm.box = dbox;
+    rm.cell_start = dst;
+    rm.cell_atoms = dat;
+    c->cells_ready = true;
+    return MARNOLDI_OK;
+}
+
+// Regions of a batch: search radius from the mean density (or the last one
+// that worked), widened when some region finds fewer than n_reg atoms inside
+// it and narrowed when the candidates overflow the kernel's buffer.
+int find_regions(marnoldi_ctx *c, const KrylovBatch &kb)
+{
+    const double vol = c->box[0] * c->box[1] * c->box[2];
+    const double rho = (double)c->nbr / vol;
+    double rs = c->region_rs;
+    if (!(rs > 0.0)) rs = 1.3 * std::cbrt(3.0 * c->rm.n_reg / (4.0 * M_PI * rho)) + 1.0;
+    std::vector<int> st(kb.nb);
+    for (int attempt = 0; attempt < 16; ++attempt) {
+        int rc = launch(c, KK_REGION, [&] { return launch_region(c->rm, kb, rs, kRegionCap, c->stream); });
+        if (rc) return rc;
+        cudaError_t e = cudaMemcpyAsync(st.data(), c->rm.rstat, (size_t)kb.nb * sizeof(int),
+                                        cudaMemcpyDeviceToHost, c->stream);
+        if (e != cudaSuccess) return fail_cuda(c, e, "region status read-back");
+        if ((rc = sync(c, "region search"))) return rc;
+        bool few = false, many = false;
+        for (int v : st) {
+            few |= v == 1;
+            many |= v == 2;
+        }
+        if (!few && !many) {
+            c->region_rs = rs;
+            return MARNOLDI_OK;
+        }
+        if (few && many)
+            return fail(c, MARNOLDI_EINVAL, "region search: density too uneven for %d candidates per region",
+                        kRegionCap);
+        rs *= few ? 1.4 : 0.85;
+    }
+    return fail(c, MARNOLDI_ENOCONV, "region search radius did not settle");
+}
+
 void free_state(marnoldi_ctx *c)
 {
     if (c->state) dfree(c, c->state, c->state_bytes);
@@ -546,10 +639,18 @@ int marnoldi_solve(marnoldi_ctx *c, const int64_t *columns, int64_t ncols, int n
     if (!c) return MARNOLDI_EINVAL;
     c->err.clear();
     c->solved = false;   // a failed solve leaves no stale results
-    if (region_atoms != 0)
-        return fail(c, MARNOLDI_EINVAL, "regional mode (region_atoms > 0) is not available in this build");
-    if (c->m > kMaxGlobalM)
-        return fail(c, MARNOLDI_EINVAL, "global mode supports M <= %lld (got %lld)", (long long)kMaxGlobalM, (long long)c->m);
+    const bool regional = region_atoms > 0;
+    if (region_atoms < 0) return fail(c, MARNOLDI_EINVAL, "region_atoms must be >= 0");
+    if (regional) {
+        if (c->pos.empty())
+            return fail(c, MARNOLDI_EINVAL, "regional mode needs positions and box at setup");
+        if (region_atoms > c->nbr || region_atoms > kMaxRegion)
+            return fail(c, MARNOLDI_EINVAL, "region_atoms = %d outside [1, min(n_block_rows, %d)]",
+                        region_atoms, kMaxRegion);
+    } else if (c->m > kMaxGlobalM) {
+        return fail(c, MARNOLDI_EINVAL, "global mode supports M <= %lld (got %lld); use region_atoms > 0",
+                    (long long)kMaxGlobalM, (long long)c->m);
+    }
     if (!(kT > 0.0) || !std::isfinite(kT)) return fail(c, MARNOLDI_EINVAL, "kT must be positive and finite");
     if (mu_fixed && !std::isfinite(*mu_fixed)) return fail(c, MARNOLDI_EINVAL, "mu_fixed must be finite");
     if (!mu_fixed && !(electron_count > 0.0 && std::isfinite(electron_count)))
@@ -580,6 +681,13 @@ int marnoldi_solve(marnoldi_ctx *c, const int64_t *columns, int64_t ncols, int n
         for (auto v : c->mask) m_real += v;
     if (nu < 1 || nu > kMaxNu || nu > m_real)
         return fail(c, MARNOLDI_EINVAL, "nu = %d outside [1, min(M_real = %lld, %d)]", nu, (long long)m_real, kMaxNu);
+    if (regional && nu > 4 * region_atoms)
+        return fail(c, MARNOLDI_EINVAL, "nu = %d exceeds the region's %d orbitals", nu, 4 * region_atoms);
+    if (regional) {
+        int rc0 = build_cells(c);
+        if (rc0) return rc0;
+        c->rm.n_reg = region_atoms;
+    }
 
     free_state(c);
     const int64_t nc = (int64_t)cols.size();
@@ -617,10 +725,12 @@ int marnoldi_solve(marnoldi_ctx *c, const int64_t *columns, int64_t ncols, int n
     if (e != cudaSuccess) return fail_cuda(c, e, "column state upload");
 
     // batch workspace
-    const ColumnShape shape = column_shape(c->m);
+    const int64_t m_vec = regional ? 4 * (int64_t)region_atoms : c->m;
+    const ColumnShape shape = column_shape(m_vec);
     const size_t vs = c->prec == 0 ? 8 : 4;
+    const size_t reg_per_col = regional ? (size_t)region_atoms * (12 + 8 * (size_t)c->rm.maxrow) : 0;
     const size_t per_col = al((size_t)2 * nu * shape.m_pad * vs) + (size_t)2 * shape.m_pad * vs +
-                           (size_t)nu * nu * 8 + (size_t)nu * 8 + 64;
+                           (size_t)nu * nu * 8 + (size_t)nu * 8 + 64 + reg_per_col;
     int64_t B = c->batch_override;
     if (B <= 0) {
         size_t freeb = 0, totb = 0;
@@ -629,7 +739,7 @@ int marnoldi_solve(marnoldi_ctx *c, const int64_t *columns, int64_t ncols, int n
         B = std::max<int64_t>(1, (int64_t)(budget / per_col));
     }
     B = std::min<int64_t>(B, nc);
-    B = std::min<int64_t>(B, 65535 * 32);
+    B = std::min<int64_t>(B, regional ? 65535 : 65535 * 32);
     c->last_batch = B;
     const size_t oK = 0, oSK = oK + al((size_t)B * nu * shape.m_pad * vs),
                  oU = oSK + al((size_t)B * nu * shape.m_pad * vs),
@@ -637,7 +747,12 @@ int marnoldi_solve(marnoldi_ctx *c, const int64_t *columns, int64_t ncols, int n
                  oH = oUl + (c->prec == 1 ? al((size_t)B * shape.m_pad * vs) : 0),
                  oSc = oH + al((size_t)B * nu * nu * 8),
                  oC = oSc + al((size_t)B * nu * 8), oS = oC + al((size_t)B * 8),
-                 oN = oS + al((size_t)B * 4), wtot = oN + al((size_t)B * 4);
+                 oN = oS + al((size_t)B * 4), oRg = oN + al((size_t)B * 4),
+                 oRc = oRg + (regional ? al((size_t)B * region_atoms * 4) : 0),
+                 oRi = oRc + (regional ? al((size_t)B * region_atoms * 4) : 0),
+                 oRk = oRi + (regional ? al((size_t)B * region_atoms * c->rm.maxrow * 4) : 0),
+                 oRs = oRk + (regional ? al((size_t)B * region_atoms * c->rm.maxrow * 4) : 0),
+                 wtot = oRs + (regional ? al((size_t)B * 4) : 0);
     if (c->ws_bytes < wtot) {
         if (c->ws) dfree(c, c->ws, c->ws_bytes);
         c->ws = dalloc(c, wtot);
@@ -662,18 +777,38 @@ int marnoldi_solve(marnoldi_ctx *c, const int64_t *columns, int64_t ncols, int n
     kb.cn2 = (double *)(wb + oC);
     kb.status = (int *)(wb + oS);
     kb.nu_eff = (int *)(wb + oN);
+    kb.m = m_vec;
+    RegionMaps *rmp = nullptr;
+    if (regional) {
+        c->rm.reg = (int *)(wb + oRg);
+        c->rm.lcnt = (int *)(wb + oRc);
+        c->rm.lci = (int *)(wb + oRi);
+        c->rm.lgk = (int *)(wb + oRk);
+        c->rm.rstat = (int *)(wb + oRs);
+        rmp = &c->rm;
+    }
     const double tau = c->prec == 0 ? kTauFp64 : kTauMixed;
     const int64_t mp = shape.m_pad;
     int rc = MARNOLDI_OK;
     for (int64_t start = 0; start < nc; start += B) {
         kb.nb = (int)std::min<int64_t>(B, nc - start);
         kb.cols = c->d_cols + start;
-        if ((rc = launch(c, KK_INIT, [&] { return launch_init(c->A, kb, c->stream); }))) return rc;
+        if (regional) {
+            if ((rc = find_regions(c, kb))) return rc;
+            if ((rc = launch(c, KK_REGION, [&] { return launch_local_bsr(c->A, c->rm, kb, c->stream); })))
+                return rc;
+            if ((rc = launch(c, KK_INIT, [&] { return launch_init_regional(c->A, c->rm, kb, c->stream); })))
+                return rc;
+        } else if ((rc = launch(c, KK_INIT, [&] { return launch_init(c->A, kb, c->stream); }))) {
+            return rc;
+        }
         for (int n = 0; n < nu; ++n) {
             // slot n holds w_n (unnormalised); the MGS of step n scales it
             const char *Kn = (const char *)kb.K + (size_t)n * mp * vs;
             if ((rc = launch(c, KK_SPMM_H, [&] {
-                     return launch_spmm(c->A, 0, kb, Kn, (int64_t)nu * mp, kb.U, mp, c->stream);
+                     return regional ? launch_spmm_regional(c->A, c->rm, 0, kb, Kn, (int64_t)nu * mp,
+                                                            kb.U, mp, c->stream)
+                                     : launch_spmm(c->A, 0, kb, Kn, (int64_t)nu * mp, kb.U, mp, c->stream);
                  })))
                 return rc;
             const int need_w = n + 1 < nu;
@@ -683,12 +818,15 @@ int marnoldi_solve(marnoldi_ctx *c, const int64_t *columns, int64_t ncols, int n
             char *Kn1 = (char *)kb.K + (size_t)(n + 1) * mp * vs;
             char *SKn1 = (char *)kb.SK + (size_t)(n + 1) * mp * vs;
             if ((rc = launch(c, KK_SPMM_S, [&] {
-                     return launch_spmm(c->A, 1, kb, Kn1, (int64_t)nu * mp, SKn1, (int64_t)nu * mp,
-                                        c->stream);
+                     return regional ? launch_spmm_regional(c->A, c->rm, 1, kb, Kn1, (int64_t)nu * mp,
+                                                            SKn1, (int64_t)nu * mp, c->stream)
+                                     : launch_spmm(c->A, 1, kb, Kn1, (int64_t)nu * mp, SKn1,
+                                                   (int64_t)nu * mp, c->stream);
                  })))
                 return rc;
         }
-        if ((rc = launch(c, KK_EIG, [&] { return launch_eig(c->A, kb, c->st, start, c->stream); }))) return rc;
+        if ((rc = launch(c, KK_EIG, [&] { return launch_eig(c->A, kb, c->st, start, rmp, c->stream); })))
+            return rc;
     }
     // ---- Fermi level
     double mu = 0.0, N = 0.0, E = 0.0;

@@ -19,6 +19,7 @@ enum KernelKind {
     KK_COUNT,
     KK_DENSITY,
     KK_GREEN,
+    KK_REGION,
     KK_NKINDS
 };
 
@@ -77,6 +78,32 @@ struct DeviceMatrix {
     const int64_t *tmap;     // block (J, I) -> index of block (I, J)
 };
 
+// ---------------------------------------------------------------- regional mode
+// Per batch column c: reg[c][p] (region atoms, ascending), lcnt[c][p] local
+// blocks of local row p, lci/lgk[c][slot][p] their local column and global
+// block index; rstat[c] 0 ok, 1 fewer than n_reg atoms within r_s, 2 more
+// candidates than kRegionCap.
+constexpr int kRegionCap = 8192;      // candidates per region search (power of two)
+constexpr int kMaxRegion = 1024;      // n_reg limit (local vectors <= 4096)
+struct RegionMaps {
+    int n_reg = 0, maxrow = 0;
+    const double *pos = nullptr, *box = nullptr;
+    const int *cell_start = nullptr, *cell_atoms = nullptr;
+    int ncell[3] = {1, 1, 1};
+    double cell_edge[3] = {1.0, 1.0, 1.0};
+    int *reg = nullptr, *lcnt = nullptr, *lci = nullptr, *lgk = nullptr, *rstat = nullptr;
+};
+
+cudaError_t launch_region(const RegionMaps &rm, const KrylovBatch &b, double rs, int cap,
+                          cudaStream_t s);
+cudaError_t launch_local_bsr(const DeviceMatrix &A, const RegionMaps &rm, const KrylovBatch &b,
+                             cudaStream_t s);
+cudaError_t launch_init_regional(const DeviceMatrix &A, const RegionMaps &rm, const KrylovBatch &b,
+                                 cudaStream_t s);
+cudaError_t launch_spmm_regional(const DeviceMatrix &A, const RegionMaps &rm, int which,
+                                 const KrylovBatch &b, const void *X, int64_t ldx, void *Y,
+                                 int64_t ldy, cudaStream_t s);
+
 cudaError_t launch_init(const DeviceMatrix &A, const KrylovBatch &b, cudaStream_t s);
 cudaError_t launch_spmm(const DeviceMatrix &A, int which /*0 H, 1 S*/, const KrylovBatch &b,
                         const void *X, int64_t ldx, void *Y, int64_t ldy, cudaStream_t s);
@@ -96,7 +123,7 @@ struct ColumnState {
 };
 
 cudaError_t launch_eig(const DeviceMatrix &A, const KrylovBatch &b, const ColumnState &st,
-                       int64_t col0, cudaStream_t s);
+                       int64_t col0, const RegionMaps *rm /* null in global mode */, cudaStream_t s);
 
 // ---------------------------------------------------------------- Fermi level, outputs
 // Deterministic two-level reductions; `partial` holds 2 * kReduceBlocks doubles,

@@ -31,7 +31,7 @@ namespace marnoldi {
 const char *kernel_name(int kind)
 {
     static const char *names[KK_NKINDS] = {"init",   "spmm_H", "mgs",     "spmm_S", "eigsub",
-                                           "minmax", "count",  "density", "green"};
+                                           "minmax", "count",  "density", "green", "region"};
     return (kind >= 0 && kind < KK_NKINDS) ? names[kind] : "?";
 }
 

@@ -36,6 +36,17 @@ __device__ __forceinline__ double warp_sum(double s)
     return s;
 }
 
+// Position of a in the ascending list R[0..n), or -1.
+__device__ __forceinline__ int find_sorted(const int *__restrict__ R, int n, int a)
+{
+    int lo = 0, hi = n;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (R[mid] < a) lo = mid + 1; else hi = mid;
+    }
+    return (lo < n && R[lo] == a) ? lo : -1;
+}
+
 __device__ __forceinline__ double fermi(double x)
 {
     if (x >= 0.0) {
@@ -53,7 +64,8 @@ __global__ void __launch_bounds__(kEigThreads) eig_kernel(
     const double *__restrict__ sdiag, const int64_t *__restrict__ rp,
     const int32_t *__restrict__ ci, int64_t col0, int *__restrict__ nu_eff_out,
     double *__restrict__ eps_out, double *__restrict__ w_out, double *__restrict__ t_out,
-    double *__restrict__ P_out, const int64_t *__restrict__ p_off, int *__restrict__ eig_status)
+    double *__restrict__ P_out, const int64_t *__restrict__ p_off, int *__restrict__ eig_status,
+    const int *__restrict__ reg, int n_reg)
 {
     const int c = blockIdx.x;
     const int64_t g = col0 + c;
@@ -242,14 +254,18 @@ __global__ void __launch_bounds__(kEigThreads) eig_kernel(
         A[i * nu + a] = Q[i * nu + perm[a]];
     }
     for (int a = tid; a < n; a += T) pp[a] = d[perm[a]];
-    // basis scales k_i = s_i w_i (e is free after QL); q = K^T e_j: entry j of
-    // every basis vector (global mode: local row = j)
+    // basis scales k_i = s_i w_i (e is free after QL); q = K^T e_j: entry jl of
+    // every basis vector, jl = j in global mode, j's local index in a region
     const int64_t j = bcols[c];
+    const int64_t J = j >> 2;
+    const int *R = reg ? reg + (int64_t)c * n_reg : nullptr;
+    const int pJ = R ? find_sorted(R, n_reg, (int)J) : 0;
+    const int64_t jl = R ? 4 * (int64_t)(pJ < 0 ? 0 : pJ) + (j & 3) : j;
     const VT *Kc = K + (int64_t)c * nu * m_pad;
     for (int i = tid; i < n; i += T) {
         const double si = bscale[(int64_t)c * nu + i];
         e[i] = si;
-        vv[i] = si * (double)Kc[(int64_t)i * m_pad + j];
+        vv[i] = si * (double)Kc[(int64_t)i * m_pad + jl];
     }
     __syncthreads();
     const double sq = sqrt(sdiag[j]);
@@ -265,16 +281,18 @@ __global__ void __launch_bounds__(kEigThreads) eig_kernel(
         w_out[g * nu + a] = wa;
     }
     if (tid == 0) nu_eff_out[g] = n;
-    // P_j = K_pat V on the 4 * (blocks of row j/4) pattern rows
-    const int64_t J = j >> 2;
+    // P_j = K_pat V on the 4 * (blocks of row j/4) pattern rows; in a region,
+    // rows of atoms outside it are zero
     const int64_t kb = rp[J];
     const int npat = 4 * (int)(rp[J + 1] - kb);
     double *P = P_out + p_off[g];
     for (int idx = tid; idx < npat * nu; idx += T) {
         const int r = idx / nu, a = idx - (idx / nu) * nu;
         double s = 0.0;
-        if (a < n) {
-            const int64_t row = 4 * (int64_t)ci[kb + (r >> 2)] + (r & 3);
+        const int atom = ci[kb + (r >> 2)];
+        const int64_t lr = R ? find_sorted(R, n_reg, atom) : atom;
+        if (a < n && lr >= 0) {
+            const int64_t row = 4 * lr + (r & 3);
             for (int i = 0; i < n; ++i)
                 s = fma(e[i] * (double)Kc[(int64_t)i * m_pad + row], A[i * nu + a], s);
         }
@@ -454,7 +472,7 @@ __global__ void __launch_bounds__(128) green_kernel(
 
 template <typename VT>
 cudaError_t eig_dispatch(const DeviceMatrix &A, const KrylovBatch &b, const ColumnState &st,
-                         int64_t col0, cudaStream_t s)
+                         int64_t col0, const RegionMaps *rm, cudaStream_t s)
 {
     const int nu = b.nu;
     const size_t smem = (size_t)(2 * nu * nu + 6 * nu) * sizeof(double) + (size_t)nu * sizeof(int);
@@ -469,17 +487,18 @@ cudaError_t eig_dispatch(const DeviceMatrix &A, const KrylovBatch &b, const Colu
     }
     eig_kernel<VT><<<b.nb, kEigThreads, smem, s>>>(
         b.Hsub, b.nu_eff, b.status, b.scale, (const VT *)b.K, b.shape.m_pad, nu, b.cols, A.sdiag, A.rp, A.ci, col0,
-        st.nu_eff, st.eps, st.w, st.t, st.P, st.p_off, st.eig_status);
+        st.nu_eff, st.eps, st.w, st.t, st.P, st.p_off, st.eig_status, rm ? rm->reg : nullptr,
+        rm ? rm->n_reg : 0);
     return cudaGetLastError();
 }
 
 }  // namespace
 
 cudaError_t launch_eig(const DeviceMatrix &A, const KrylovBatch &b, const ColumnState &st,
-                       int64_t col0, cudaStream_t s)
+                       int64_t col0, const RegionMaps *rm, cudaStream_t s)
 {
-    return b.prec == 0 ? eig_dispatch<double>(A, b, st, col0, s)
-                       : eig_dispatch<float>(A, b, st, col0, s);
+    return b.prec == 0 ? eig_dispatch<double>(A, b, st, col0, rm, s)
+                       : eig_dispatch<float>(A, b, st, col0, rm, s);
 }
 
 cudaError_t launch_minmax(const ColumnState &st, double *partial, unsigned *ticket, double *out,

@@ -186,7 +186,7 @@ def test_errors(m, c1):
         m.marnoldi_solve(ctx, None, 200, 0, c1.n_electrons, KT)
     assert ei.value.code == m.marnoldi.MARNOLDI_EINVAL
     with pytest.raises(m.MarnoldiError) as ei:
-        m.marnoldi_solve(ctx, None, 30, 64, c1.n_electrons, KT)
+        m.marnoldi_solve(ctx, None, 30, 65, c1.n_electrons, KT)     # region larger than the system
     assert ei.value.code == m.marnoldi.MARNOLDI_EINVAL
     with pytest.raises(m.MarnoldiError) as ei:
         m.marnoldi_solve(ctx, [0, 5, 0], 30, 0, c1.n_electrons, KT)
@@ -264,3 +264,64 @@ def test_c2_full_size_sampled(m, c2, prec):
             tr += c2.S[k][b, :] @ g["rho"][bidx[(int(I), int(J))]][:, b]
         f2 = 2 * expit(-(g["eps"][j] - g["mu"]) / KT)
         assert tr == pytest.approx(np.sum(f2 * g["w"][j]), abs=1e-10 if prec == 0 else 1e-6)
+
+
+# ----------------------------------------------------------------- regional mode
+
+def gpu_solve_regional(m, t, nu, n_reg, prec=0, cols=None, mu_fixed=None):
+    ctx = m.setup_system(t, prec)
+    m.marnoldi_solve(ctx, cols, nu, n_reg, t.n_electrons, KT, mu_fixed)
+    rho, rhoE = m.marnoldi_density(ctx)
+    E, mu, N = m.marnoldi_energy(ctx)
+    nue, eps, w = m.marnoldi_column_stats(ctx)
+    return dict(ctx=ctx, rho=rho, rhoE=rhoE, E=E, mu=mu, N=N, nu_eff=nue, eps=eps, w=w)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_region_of_all_atoms_equals_global(m, c1, prec):
+    a = gpu_solve(m, c1, 20, prec=prec)
+    b = gpu_solve_regional(m, c1, 20, c1.n_block_rows, prec=prec)
+    for k in ("rho", "rhoE", "eps", "w"):
+        np.testing.assert_array_equal(a[k], b[k])
+
+
+@pytest.mark.parametrize("n_reg", [12, 33])
+def test_regional_fp64_matches_oracle(m, c1, n_reg):
+    g = gpu_solve_regional(m, c1, 16, n_reg)
+    ref = oracle.solve(c1, nu=16, kT=KT, region_atoms=n_reg)
+    assert_close_fp64(g, ref, c1)
+
+
+def test_regional_errors(m, c1):
+    ctx = m.setup_system(c1, 0)
+    with pytest.raises(m.MarnoldiError) as ei:
+        m.marnoldi_solve(ctx, None, 16, c1.n_block_rows + 1, c1.n_electrons, KT)
+    assert ei.value.code == m.marnoldi.MARNOLDI_EINVAL
+    with pytest.raises(m.MarnoldiError) as ei:
+        m.marnoldi_solve(ctx, None, 64, 8, c1.n_electrons, KT)      # nu > 4 n_reg
+    assert ei.value.code == m.marnoldi.MARNOLDI_EINVAL
+    ctx2 = m.marnoldi_setup(c1.n_block_rows, c1.row_ptr, c1.col_idx, c1.H, c1.S)
+    with pytest.raises(m.MarnoldiError) as ei:
+        m.marnoldi_solve(ctx2, None, 16, 8, c1.n_electrons, KT)      # no positions
+    assert ei.value.code == m.marnoldi.MARNOLDI_EINVAL
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_c2_regional_sampled(m, c2, prec):
+    """4,096-atom amorphous carbon, regions of 256 atoms, every column on the GPU;
+    the regional oracle recomputes a seeded sample at the GPU's mu."""
+    g = gpu_solve_regional(m, c2, 30, 256, prec=prec)
+    assert g["N"] == pytest.approx(c2.n_electrons, rel=1e-12 if prec == 0 else 1e-8)
+    sample = np.sort(np.random.default_rng(5).choice(c2.M, size=16, replace=False))
+    ref = oracle.solve(c2, nu=30, kT=KT, mu_fixed=g["mu"], cols=sample, region_atoms=256)
+    mask = ~np.isnan(ref.rho)
+    drho = np.abs(g["rho"][mask] - ref.rho[mask]).max()
+    drhoE = np.abs(g["rhoE"][mask] - ref.rhoE[mask]).max()
+    print(f"C2 regional prec={prec}: drho={drho:.3e} drhoE={drhoE:.3e}")
+    if prec == 0:
+        assert drho <= FP64_REL * np.abs(ref.rho[mask]).max()
+        assert drhoE <= FP64_REL * np.abs(ref.rhoE[mask]).max()
+        np.testing.assert_array_equal(g["nu_eff"][sample], ref.cols.nu_eff)
+    else:
+        assert drho <= 1e-5
+        assert drhoE <= 1e-4

@@ -364,3 +364,34 @@ def test_p1_p3_p5_rescaled_orbitals():
     for (I, J), v in blocks.items():
         np.testing.assert_allclose(v, rho[4 * I:4 * I + 4, 4 * J:4 * J + 4],
                                    atol=1e-11 * np.abs(rho).max())
+
+
+def test_p11_region_of_all_atoms_is_global(c1):
+    """Regional mode with the region = every atom is the global problem, bit for bit."""
+    a = oracle.solve(c1, nu=20, kT=KT)
+    b = oracle.solve(c1, nu=20, kT=KT, region_atoms=c1.n_block_rows)
+    assert b.E_band == a.E_band and b.N == a.N
+    np.testing.assert_array_equal(b.rho, a.rho)
+    np.testing.assert_array_equal(b.rhoE, a.rhoE)
+
+
+def test_region_definition_and_convergence(c1):
+    """Regions hold the n nearest atoms (ties by index), contain the column's atom and
+    every pattern neighbour once large enough; the error shrinks as regions grow."""
+    s = c1.structure
+    for J in (0, 17, 63):
+        R = oracle.region(s.positions, s.box, J, 20)
+        assert R.size == 20 and J in R and np.all(np.diff(R) > 0)
+        d = s.positions - s.positions[J]
+        d -= s.box * np.round(d / s.box)
+        d2 = np.sum(d * d, axis=1)
+        outside = np.setdiff1d(np.arange(c1.n_block_rows), R)
+        assert d2[R].max() <= d2[outside].min()
+        nbrs = c1.col_idx[c1.row_ptr[J]:c1.row_ptr[J + 1]]
+        assert set(nbrs.tolist()) <= set(R.tolist())
+    ref = oracle.solve(c1, nu=16, kT=KT)
+    errs = []
+    for nr in (16, 40, 64):
+        r = oracle.solve(c1, nu=16, kT=KT, region_atoms=nr, mu_fixed=ref.mu)
+        errs.append(np.nanmax(np.abs(r.rho - ref.rho)))
+    assert errs[-1] == 0.0 and errs[1] < errs[0]
