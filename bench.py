@@ -55,6 +55,8 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=15.0)
+    p.add_argument("--region", type=int, default=0,
+                   help="regional mode with this many atoms per region (0 = global mode)")
     return p.parse_args()
 
 
@@ -74,7 +76,11 @@ def electrons(t, cols) -> float:
 
 def workload_name(args, t, ncols):
     return (f"amorphous sp2-sp3 carbon {t.n_block_rows} atoms (M={t.M}, 3.0 g/cm^3, seed 0), "
-            f"global mode, nu={args.nu}, {ncols} columns, kT={KT} eV, mu by bisection at 4 e/atom")
+            f"{mode_name(args)}, nu={args.nu}, {ncols} columns, kT={KT} eV, mu by bisection at 4 e/atom")
+
+
+def mode_name(args) -> str:
+    return f"regional mode ({args.region}-atom regions)" if args.region else "global mode"
 
 
 # ------------------------------------------------------------------------ measurement helpers
@@ -169,7 +175,7 @@ def time_gpu(m, t, cols, args, prec, steps, warmup, dev, measure_clocks=False):
     ne = electrons(t, cols)
 
     def step():
-        m.marnoldi_solve(ctx, colsel, args.nu, 0, ne, KT)
+        m.marnoldi_solve(ctx, colsel, args.nu, args.region, ne, KT)
         m.marnoldi_density_device(ctx, rho, rhoE)
 
     for _ in range(warmup):
@@ -213,7 +219,7 @@ def time_e2e(m, t, cols, args, prec, steps, warmup):
 
     def step():
         ctx = m.setup_system(t, prec)
-        m.marnoldi_solve(ctx, colsel, args.nu, 0, ne, KT)
+        m.marnoldi_solve(ctx, colsel, args.nu, args.region, ne, KT)
         rho, rhoE = m.marnoldi_density(ctx)
         E, mu, N = m.marnoldi_energy(ctx)
         m.marnoldi_destroy(ctx)
@@ -288,15 +294,16 @@ def main():
     launches = sum(v[0] for v in stats.values())
     peaks = read_peaks()
 
-    # roofline of the dominant kernel over the timed region
+    # roofline of the dominant kernel over the timed region (vector length: M, or 4 n_reg)
+    m_vec = 4 * args.region if args.region else t.M
     vb = 4 if prec == 1 else 8
     dom = max(stats, key=lambda k: stats[k][1])
     nlaunch, dom_ms = stats[dom]
     steps = args.steps
     if dom == "mgs":
-        by, fl = mgs_algorithmic(args.nu, t.M, vb, ncols)
+        by, fl = mgs_algorithmic(args.nu, m_vec, vb, ncols)
     elif dom in ("spmm_H", "spmm_S"):
-        by, fl = spmm_algorithmic(args.nu, t.M, t.nnzb, t.n_block_rows, vb, ncols)
+        by, fl = spmm_algorithmic(args.nu, m_vec, t.nnzb, t.n_block_rows, vb, ncols)
         by, fl = by / 2, fl / 2
     else:
         by, fl = None, None
@@ -322,7 +329,7 @@ def main():
         "dtype": "f32+f64" if prec == 1 else "f64", "data": "synthetic",
         "config": {"workload": workload_name(args, t, ncols), "precision": args.precision,
                    "nu": args.nu, "columns": ncols, "atoms": t.n_block_rows, "M": t.M,
-                   "nnzb": t.nnzb, "mode": "global",
+                   "nnzb": t.nnzb, "mode": mode_name(args),
                    "l2": f"flushed between timed steps ({L2_FLUSH_BYTES >> 20} MB write)",
                    "parallelism": f"{world} independent replica(s)" if world > 1 else "1 GPU"},
         "roofline": roof,
@@ -339,7 +346,7 @@ def main():
         s64 = statistics.mean(r64["times"]) / 1e3
         st64 = r64["stats"]
         ms64 = st64["mgs"][1]
-        by64, fl64 = mgs_algorithmic(args.nu, t.M, 8, ncols)
+        by64, fl64 = mgs_algorithmic(args.nu, m_vec, 8, ncols)
         ach64 = fl64 * max(3, args.steps // 2) / (ms64 / 1e3) / 1e12
         pk64 = 152 * 2 * 2 * 2.07e9 / 1e12
         line["fp64"] = {"value": round(world * ncols / s64, 2), "ms_per_step": round(s64 * 1e3, 3),
@@ -398,7 +405,7 @@ def main_reference(args, world, rank):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(statistics.mean(ts) * 1e3, 3),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": workload_name(args, t, len(cols)), "nu": args.nu, "mode": "global"},
+            "config": {"workload": workload_name(args, t, len(cols)), "nu": args.nu, "mode": mode_name(args)},
             "cpu_baseline": {"value": round(v, 3), "unit": UNIT, "cores": nth, "kind": "oracle",
                              "sample": f"{per_step} seeded columns per step (Krylov build, eigensolve, "
                                        f"weights, density columns at a fixed mu)"},

@@ -18,9 +18,9 @@
 //               w is written to slot n+1
 //   spmm(S):    S w into slot n+1
 //
-// Inner products are always accumulated in FP64; in mixed precision the
-// vectors, the SpMM and the Gram-Schmidt updates are FP32.  Reductions use a
-// fixed order (warp butterfly, then warps in index order), so results do not
+// Inner products are always accumulated to FP64 accuracy; in mixed precision
+// the vectors, the SpMM and the Gram-Schmidt updates are FP32.  Reductions use
+// a fixed order (warp butterfly, then warp 0 over the warps), so results do not
 // depend on scheduling.
 #include "internal.h"
 
@@ -35,20 +35,15 @@ const char *kernel_name(int kind)
     return (kind >= 0 && kind < KK_NKINDS) ? names[kind] : "?";
 }
 
+// Vectors up to 4096 entries run 256-thread CTAs (several columns share an SM
+// and overlap each other's barriers); longer ones 1024-thread CTAs.  VPT is
+// the power of two that covers m.
 ColumnShape column_shape(int64_t m)
 {
-    ColumnShape s{1, 32, 32};
-    for (int v = 1; v <= 16; v *= 2) {
-        int64_t t = (m + v - 1) / v;
-        if (t <= 1024 || v == 16) {
-            t = v >= 8 ? 1024 : ((t + 31) / 32) * 32;   // vpt >= 8: T fixed at compile time
-            s.vpt = v;
-            s.threads = (int)t;
-            s.m_pad = t * v;
-            break;
-        }
-    }
-    return s;
+    const int T = m <= 4096 ? 256 : 1024;
+    int v = 1;
+    while (v < 16 && (int64_t)v * T < m) v *= 2;
+    return ColumnShape{v, T, (int64_t)v * T};
 }
 
 namespace {
@@ -127,17 +122,24 @@ template <> struct DotAcc<float> {
 };
 
 // Sum of two per-thread accumulators over the CTA, in a fixed order (warp
-// butterflies, then warp 0 over the warps' partials); every thread returns
-// the same FP64 totals.  Only warp 0 touches the warps' partials, so the
-// cross-warp step costs one warp's work, not one per thread.  `buf`
-// alternates the shared slots so that two barriers per reduction suffice.
+// butterflies, then warp 0 over the warps' partials).  Thread 0 of warp 0 runs
+// `epi(totals, slot)` before the final barrier: the scalar FP64 work that
+// follows a reduction (scales, coefficients, the breakdown test) is done once
+// there and handed to the CTA through shared memory, instead of by every
+// thread on GB300's narrow FP64 pipe.  `buf` alternates the shared slots so
+// that two barriers per reduction suffice.
 struct RedShared {
     double2 part[2][32];
     double2 total[2];
 };
 
-template <typename VT>
-__device__ __forceinline__ double2 block_sum2(DotAcc<VT> a, DotAcc<VT> b, RedShared &sh, int &buf)
+struct NoEpilogue {
+    __device__ __forceinline__ void operator()(double2, int) const {}
+};
+
+template <typename VT, typename Epi = NoEpilogue>
+__device__ __forceinline__ double2 block_sum2(DotAcc<VT> a, DotAcc<VT> b, RedShared &sh, int &buf,
+                                              Epi epi = Epi())
 {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     a.warp_reduce();
@@ -149,13 +151,18 @@ __device__ __forceinline__ double2 block_sum2(DotAcc<VT> a, DotAcc<VT> b, RedSha
         if (lane < nw) DotAcc<VT>::unpack(sh.part[buf][lane], x, y);
         x.warp_reduce();
         y.warp_reduce();
-        if (lane == 0) sh.total[buf] = make_double2(x.value(), y.value());
+        if (lane == 0) {
+            const double2 t = make_double2(x.value(), y.value());
+            sh.total[buf] = t;
+            epi(t, buf);
+        }
     }
     __syncthreads();
     const double2 r = sh.total[buf];
     buf ^= 1;
     return r;
 }
+
 __device__ __forceinline__ void load4(const double *p, double (&v)[4])
 {
     const double2 a = __ldg(reinterpret_cast<const double2 *>(p));
@@ -336,25 +343,27 @@ __global__ void __launch_bounds__(256) spmm_f32_accurate_kernel(
 }
 
 // ------------------------------------------------------------------ MGS
-// One CTA per column; thread t owns entries r = t + v T (v < VPT) of the
-// column's vectors.  Small VPT keeps w in registers.  VPT = 16 (m > 8192)
-// keeps w in shared memory instead (1024 threads leave 64 registers each),
-// with u in shared memory too when both fit, else re-read from global memory
-// (an L2 hit: the SpMM has just written it).  Entries are visited in chunks
-// with a compiler barrier between chunks so that only one chunk's loads are
-// live per thread.  The stored w_i is held across the reduction when it fits
-// in registers, else re-read after it (an L2 hit).
-template <typename VT, int VPT>
+// One CTA of T threads per column; thread t owns entries r = t + v T
+// (v < VPT) of the column's vectors.  T is a compile-time constant, so the
+// per-entry offsets v T are load immediates rather than live registers.
+// Small VPT keeps w in registers; VPT = 16 keeps w in shared memory instead
+// (64 registers per thread do not hold it), with u in shared memory too when
+// both fit, else re-read from global memory (an L2 hit: the SpMM has just
+// written it).  Entries are visited in chunks with a compiler barrier between
+// chunks so that only one chunk's loads are live per thread.  The stored w_i
+// is held across the reduction when it fits in registers, else re-read after
+// it (an L2 hit).
+template <typename VT, int VPT, int T>
 struct MgsCfg {
-    static constexpr bool kLo = sizeof(VT) == 4;                             // u as (hi, lo) pair
-    static constexpr bool kWs = VPT >= 16;                                   // w in smem
-    static constexpr bool kUs = kLo || !kWs || 2 * VPT * 1024 * sizeof(VT) <= 160 * 1024;  // u in smem
+    static constexpr bool kLo = sizeof(VT) == 4;                    // u as (hi, lo) pair
+    static constexpr bool kWs = VPT >= 16;                          // w in smem
+    static constexpr bool kUs = kLo || !kWs || 2 * VPT * T * sizeof(VT) <= 160 * 1024;
     static constexpr bool kHold = VPT * sizeof(VT) <= 64;
     static constexpr int kChunk = sizeof(VT) == 8 ? 4 : 8;
     static constexpr int kSmemVectors = (kUs ? 1 : 0) + (kLo ? 1 : 0) + (kWs ? 1 : 0);
 };
 
-// y -= a x over the thread's entries (x from registers or re-read).
+// w -= a x over the thread's entries (x from registers or re-read).
 template <typename VT, int VPT, int kChunk, bool kHold, bool kWs>
 __device__ __forceinline__ void axpy_entries(VT (&wr)[kWs ? 1 : VPT], VT *ws,
                                              const VT (&kv)[kHold ? VPT : 1],
@@ -375,25 +384,18 @@ __device__ __forceinline__ void axpy_entries(VT (&wr)[kWs ? 1 : VPT], VT *ws,
     }
 }
 
-template <typename VT, int VPT>
-__global__ void __launch_bounds__(1024, 1) mgs_kernel(VT *__restrict__ K, VT *__restrict__ SK,
-                                                      const VT *__restrict__ U,
-                                                      const VT *__restrict__ Ulo,
-                                                      double *__restrict__ Hsub,
-                                                      double *__restrict__ scale,
-                                                      double *__restrict__ cn2,
-                                                      int *__restrict__ status,
-                                                      int *__restrict__ nu_eff, int n, int nu,
-                                                      int64_t m_pad, int need_w, double tau2)
+template <typename VT, int VPT, int T>
+__global__ void __launch_bounds__(T, T == 256 ? 4 : 1) mgs_kernel(
+    VT *__restrict__ K, VT *__restrict__ SK, const VT *__restrict__ U, const VT *__restrict__ Ulo,
+    double *__restrict__ Hsub, double *__restrict__ scale, double *__restrict__ cn2,
+    int *__restrict__ status, int *__restrict__ nu_eff, int n, int nu, int64_t m_pad, int need_w,
+    double tau2)
 {
-    using Cfg = MgsCfg<VT, VPT>;
+    using Cfg = MgsCfg<VT, VPT, T>;
     constexpr bool kWs = Cfg::kWs, kUs = Cfg::kUs, kHold = Cfg::kHold, kLo = Cfg::kLo;
     constexpr int kChunk = Cfg::kChunk;
     const int c = blockIdx.x;
     if (status[c] != 0) return;
-    // VPT >= 8 always runs 1024 threads: a compile-time T turns the per-entry
-    // offsets v * T into load immediates instead of live registers.
-    const int T = VPT >= 8 ? 1024 : (int)blockDim.x;
     const int tid = threadIdx.x;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     VT *us = reinterpret_cast<VT *>(smem_raw);             // u = H w_n, unscaled (if kUs)
@@ -402,6 +404,9 @@ __global__ void __launch_bounds__(1024, 1) mgs_kernel(VT *__restrict__ K, VT *__
     __shared__ RedShared red;
     __shared__ double ctot[kMaxNu];
     __shared__ double ssc[kMaxNu];
+    __shared__ VT bc_coef[2];     // the FP32/FP64 update coefficient of the last reduction
+    __shared__ double bc_sn;
+    __shared__ int bc_stop;
     const int64_t base = (int64_t)c * nu * m_pad;
     int buf = 0;
 
@@ -422,16 +427,21 @@ __global__ void __launch_bounds__(1024, 1) mgs_kernel(VT *__restrict__ K, VT *__
             }
             if (v0 + kChunk < VPT) asm volatile("" ::: "memory");
         }
-        const double beta2 = block_sum2(acc, DotAcc<VT>(), red, buf).x;
-        if (!(beta2 > 0.0) || beta2 <= tau2 * (beta2 + cn2[c])) {
-            if (tid == 0) {
+        block_sum2(acc, DotAcc<VT>(), red, buf, [&](double2 t, int) {
+            const double beta2 = t.x;
+            if (!(beta2 > 0.0) || beta2 <= tau2 * (beta2 + cn2[c])) {
                 status[c] = (beta2 >= 0.0) ? 1 : 2;   // 2: negative or NaN S-norm
                 nu_eff[c] = n;
+                bc_stop = 1;
+            } else {
+                const double s = 1.0 / sqrt(beta2);
+                scale[(int64_t)c * nu + n] = s;
+                bc_sn = s;
+                bc_stop = 0;
             }
-            return;
-        }
-        sn = 1.0 / sqrt(beta2);
-        if (tid == 0) scale[(int64_t)c * nu + n] = sn;
+        });
+        if (bc_stop) return;   // uniform: read after the reduction's last barrier
+        sn = bc_sn;
     }
     __syncthreads();   // ssc visible
     // w starts as u = s_n H w_n; the h dots use H w_n unscaled (with its lo
@@ -476,15 +486,15 @@ __global__ void __launch_bounds__(1024, 1) mgs_kernel(VT *__restrict__ K, VT *__
             }
             if (v0 + kChunk < VPT) asm volatile("" ::: "memory");
         }
-        const double2 s = block_sum2(ac, ah, red, buf);
-        const double ci = s.x * si, hi = s.y * si * sn;
-        if (need_w)
-            axpy_entries<VT, VPT, kChunk, kHold, kWs>(wr, ws, kv, ki, tid, T, (VT)(ci * si));
-        if (tid == 0) {
+        block_sum2(ac, ah, red, buf, [&](double2 t, int slot) {
+            const double ci = t.x * si, h = t.y * si * sn;
             ctot[i] = ci;
-            Hsub[((int64_t)c * nu + i) * nu + n] = hi;
-            Hsub[((int64_t)c * nu + n) * nu + i] = hi;
-        }
+            bc_coef[slot] = (VT)(ci * si);
+            Hsub[((int64_t)c * nu + i) * nu + n] = h;
+            Hsub[((int64_t)c * nu + n) * nu + i] = h;
+        });
+        if (need_w)
+            axpy_entries<VT, VPT, kChunk, kHold, kWs>(wr, ws, kv, ki, tid, T, bc_coef[buf ^ 1]);
     }
     if (!need_w) return;
     // pass 2: second Gram-Schmidt sweep
@@ -508,9 +518,12 @@ __global__ void __launch_bounds__(1024, 1) mgs_kernel(VT *__restrict__ K, VT *__
             }
             if (v0 + kChunk < VPT) asm volatile("" ::: "memory");
         }
-        const double ci = block_sum2(ac, DotAcc<VT>(), red, buf).x * si;
-        axpy_entries<VT, VPT, kChunk, kHold, kWs>(wr, ws, kv, ki, tid, T, (VT)(ci * si));
-        if (tid == 0) ctot[i] += ci;
+        block_sum2(ac, DotAcc<VT>(), red, buf, [&](double2 t, int slot) {
+            const double ci = t.x * si;
+            ctot[i] += ci;
+            bc_coef[slot] = (VT)(ci * si);
+        });
+        axpy_entries<VT, VPT, kChunk, kHold, kWs>(wr, ws, kv, ki, tid, T, bc_coef[buf ^ 1]);
     }
     VT *wo = K + base + (int64_t)(n + 1) * m_pad;   // the next slot, unnormalised
 #pragma unroll
@@ -525,35 +538,45 @@ __global__ void __launch_bounds__(1024, 1) mgs_kernel(VT *__restrict__ K, VT *__
     }
 }
 
-template <typename VT, int VPT>
+template <typename VT, int VPT, int T>
 cudaError_t mgs_dispatch(const KrylovBatch &b, int n, int need_w, double tau, cudaStream_t s)
 {
-    using Cfg = MgsCfg<VT, VPT>;
+    using Cfg = MgsCfg<VT, VPT, T>;
     const size_t smem = (size_t)b.shape.m_pad * sizeof(VT) * Cfg::kSmemVectors;
     static bool configured = false;
     if (!configured) {
-        const int maxs = (int)((size_t)VPT * 1024 * sizeof(VT) * Cfg::kSmemVectors);
-        cudaError_t e = cudaFuncSetAttribute(mgs_kernel<VT, VPT>,
+        const int maxs = (int)((size_t)VPT * T * sizeof(VT) * Cfg::kSmemVectors);
+        cudaError_t e = cudaFuncSetAttribute(mgs_kernel<VT, VPT, T>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, maxs);
         if (e != cudaSuccess) return e;
         configured = true;
     }
-    mgs_kernel<VT, VPT><<<b.nb, b.shape.threads, smem, s>>>(
+    mgs_kernel<VT, VPT, T><<<b.nb, T, smem, s>>>(
         (VT *)b.K, (VT *)b.SK, (const VT *)b.U, (const VT *)b.Ulo, b.Hsub, b.scale, b.cn2,
-        b.status, b.nu_eff, n,
-        b.nu, b.shape.m_pad, need_w, tau * tau);
+        b.status, b.nu_eff, n, b.nu, b.shape.m_pad, need_w, tau * tau);
     return cudaGetLastError();
 }
 
 template <typename VT>
-cudaError_t mgs_vpt(const KrylovBatch &b, int n, int need_w, double tau, cudaStream_t s)
+cudaError_t mgs_shape(const KrylovBatch &b, int n, int need_w, double tau, cudaStream_t s)
 {
+    if (b.shape.threads == 1024) {
+        switch (b.shape.vpt) {
+        case 1: return mgs_dispatch<VT, 1, 1024>(b, n, need_w, tau, s);
+        case 2: return mgs_dispatch<VT, 2, 1024>(b, n, need_w, tau, s);
+        case 4: return mgs_dispatch<VT, 4, 1024>(b, n, need_w, tau, s);
+        case 8: return mgs_dispatch<VT, 8, 1024>(b, n, need_w, tau, s);
+        case 16: return mgs_dispatch<VT, 16, 1024>(b, n, need_w, tau, s);
+        default: return cudaErrorInvalidValue;
+        }
+    }
+    if (b.shape.threads != 256) return cudaErrorInvalidValue;
     switch (b.shape.vpt) {
-    case 1: return mgs_dispatch<VT, 1>(b, n, need_w, tau, s);
-    case 2: return mgs_dispatch<VT, 2>(b, n, need_w, tau, s);
-    case 4: return mgs_dispatch<VT, 4>(b, n, need_w, tau, s);
-    case 8: return mgs_dispatch<VT, 8>(b, n, need_w, tau, s);
-    case 16: return mgs_dispatch<VT, 16>(b, n, need_w, tau, s);
+    case 1: return mgs_dispatch<VT, 1, 256>(b, n, need_w, tau, s);
+    case 2: return mgs_dispatch<VT, 2, 256>(b, n, need_w, tau, s);
+    case 4: return mgs_dispatch<VT, 4, 256>(b, n, need_w, tau, s);
+    case 8: return mgs_dispatch<VT, 8, 256>(b, n, need_w, tau, s);
+    case 16: return mgs_dispatch<VT, 16, 256>(b, n, need_w, tau, s);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -592,7 +615,7 @@ cudaError_t launch_spmm(const DeviceMatrix &A, int which, const KrylovBatch &b, 
 
 cudaError_t launch_mgs(const KrylovBatch &b, int n, int need_w, double tau, cudaStream_t s)
 {
-    return b.prec == 0 ? mgs_vpt<double>(b, n, need_w, tau, s) : mgs_vpt<float>(b, n, need_w, tau, s);
+    return b.prec == 0 ? mgs_shape<double>(b, n, need_w, tau, s) : mgs_shape<float>(b, n, need_w, tau, s);
 }
 
 }  // namespace marnoldi

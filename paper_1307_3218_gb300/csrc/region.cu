@@ -98,13 +98,13 @@ __global__ void __launch_bounds__(1024) region_kernel(
     // distinct cells of the cube [c - h, c + h] (the whole axis when it wraps onto itself)
     const int nx = min(2 * hx + 1, ncell.x), ny = min(2 * hy + 1, ncell.y), nz = min(2 * hz + 1, ncell.z);
     const int ncube = nx * ny * nz;
-    for (int q = 0; q < ncube; ++q) {
+    for (int q = threadIdx.x; q < ncube; q += blockDim.x) {   // one cell per thread
         const int ox = q % nx, oy = (q / nx) % ny, oz = q / (nx * ny);
         const int gx = ((nx == ncell.x ? ox : cx - hx + ox) % ncell.x + ncell.x) % ncell.x;
         const int gy = ((ny == ncell.y ? oy : cy - hy + oy) % ncell.y + ncell.y) % ncell.y;
         const int gz = ((nz == ncell.z ? oz : cz - hz + oz) % ncell.z + ncell.z) % ncell.z;
         const int cell = (gz * ncell.y + gy) * ncell.x + gx;
-        for (int s = cell_start[cell] + threadIdx.x; s < cell_start[cell + 1]; s += blockDim.x) {
+        for (int s = cell_start[cell]; s < cell_start[cell + 1]; ++s) {
             const int a = cell_atoms[s];
             const double d2 = min_image_d2(pos + 3 * (int64_t)a, pj, bx);
             if (d2 <= rs2) {
