@@ -39,6 +39,7 @@ struct marnoldi_ctx {
     cudaStream_t stream = nullptr;
     int prec = 0;
     int64_t nbr = 0, nnzb = 0, m = 0;
+    int maxrow = 1;   // most blocks in a block row
     std::vector<int64_t> rp;
     std::vector<int32_t> ci;
     std::vector<uint8_t> mask;
@@ -363,9 +364,7 @@ int build_cells(marnoldi_ctx *c)
     for (int64_t q = 0; q < ncells; ++q) start[q + 1] += start[q];
     std::vector<int> fill(start.begin(), start.end() - 1);
     for (int64_t a = 0; a < n; ++a) atoms[fill[cell_of[a]]++] = (int)a;
-    int maxrow = 1;
-    for (int64_t I = 0; I < n; ++I) maxrow = std::max<int>(maxrow, (int)(c->rp[I + 1] - c->rp[I]));
-    rm.maxrow = maxrow;
+    rm.maxrow = c->maxrow;
     double *dpos = nullptr, *dbox = nullptr;
     int *dst = nullptr, *dat = nullptr;
     int rc;
@@ -501,6 +500,8 @@ int marnoldi_setup(marnoldi_ctx **out, int64_t n_block_rows, const int64_t *row_
     }
     int rc = validate_structure(c, H_vals, S_vals);
     if (rc != MARNOLDI_OK) { delete c; return rc; }
+    for (int64_t I = 0; I < n_block_rows; ++I)
+        c->maxrow = std::max<int>(c->maxrow, (int)(c->rp[I + 1] - c->rp[I]));
     // transpose map: block (I, J) at k -> index of block (J, I)
     std::vector<int64_t> tmap(nnzb);
     for (int64_t I = 0; I < n_block_rows; ++I)
@@ -752,7 +753,22 @@ int marnoldi_solve(marnoldi_ctx *c, const int64_t *columns, int64_t ncols, int n
                  oRi = oRc + (regional ? al((size_t)B * region_atoms * 4) : 0),
                  oRk = oRi + (regional ? al((size_t)B * region_atoms * c->rm.maxrow * 4) : 0),
                  oRs = oRk + (regional ? al((size_t)B * region_atoms * c->rm.maxrow * 4) : 0),
-                 wtot = oRs + (regional ? al((size_t)B * 4) : 0);
+                 oEg = oRs + (regional ? al((size_t)B * 4) : 0);
+    // eigensolve scratch, for chunks of at most ceig subspaces
+    EigScratch es;
+    es.nr_max = 4 * c->maxrow + 2;
+    es.rcap = (int64_t)8 * nu * nu;
+    es.scap = (int64_t)40 * nu;
+    const size_t per_sub = al((size_t)(2 + es.nr_max) * nu * 8) + al((size_t)es.rcap * 16) +
+                           al((size_t)es.scap * 8) + 8;
+    es.chunk = (int)std::max<int64_t>(32, std::min<int64_t>(B, (int64_t)(((size_t)3 << 30) / per_sub)));
+    if (eig_smem_bytes(nu, es.nr_max) > (size_t)227 * 1024)
+        return fail(c, MARNOLDI_EINVAL, "nu = %d with %d blocks per row exceeds the eigensolver's shared memory",
+                    nu, c->maxrow);
+    const size_t ceig = (size_t)es.chunk;
+    const size_t oED = oEg, oEE = oED + al(ceig * nu * 8), oERQ = oEE + al(ceig * nu * 8),
+                 oERot = oERQ + al(ceig * es.nr_max * nu * 8), oESw = oERot + al(ceig * es.rcap * 16),
+                 oENs = oESw + al(ceig * es.scap * 8), wtot = oENs + al(ceig * 4);
     if (c->ws_bytes < wtot) {
         if (c->ws) dfree(c, c->ws, c->ws_bytes);
         c->ws = dalloc(c, wtot);
@@ -778,6 +794,12 @@ int marnoldi_solve(marnoldi_ctx *c, const int64_t *columns, int64_t ncols, int n
     kb.status = (int *)(wb + oS);
     kb.nu_eff = (int *)(wb + oN);
     kb.m = m_vec;
+    es.D = (double *)(wb + oED);
+    es.E = (double *)(wb + oEE);
+    es.RQ = (double *)(wb + oERQ);
+    es.rot = (double2 *)(wb + oERot);
+    es.sweep = (int2 *)(wb + oESw);
+    es.nsweep = (int *)(wb + oENs);
     RegionMaps *rmp = nullptr;
     if (regional) {
         c->rm.reg = (int *)(wb + oRg);
@@ -825,7 +847,7 @@ int marnoldi_solve(marnoldi_ctx *c, const int64_t *columns, int64_t ncols, int n
                  })))
                 return rc;
         }
-        if ((rc = launch(c, KK_EIG, [&] { return launch_eig(c->A, kb, c->st, start, rmp, c->stream); })))
+        if ((rc = launch(c, KK_EIG, [&] { return launch_eig(c->A, kb, c->st, start, rmp, es, c->stream); })))
             return rc;
     }
     // ---- Fermi level

@@ -122,8 +122,24 @@ struct ColumnState {
     int *eig_status;     // 0 ok, 1 QL did not converge
 };
 
+// Scratch of the three-kernel eigensolve, per chunk of subspaces:
+//   D, E [chunk][nu] (tridiagonal, then levels), RQ [chunk][nr_max][nu] (rows
+//   e_1, q, K_pat times Q, then times Z), rot [chunk][rcap] Givens (c, s),
+//   sweep [chunk][scap] (m, lo), nsweep [chunk] (-1: QL failed).
+struct EigScratch {
+    int chunk = 0, nr_max = 0;
+    int64_t rcap = 0, scap = 0;
+    double *D = nullptr, *E = nullptr, *RQ = nullptr;
+    double2 *rot = nullptr;
+    int2 *sweep = nullptr;
+    int *nsweep = nullptr;
+};
+// Largest dynamic shared memory the eigensolve kernels need.
+size_t eig_smem_bytes(int nu, int nr_max);
+
 cudaError_t launch_eig(const DeviceMatrix &A, const KrylovBatch &b, const ColumnState &st,
-                       int64_t col0, const RegionMaps *rm /* null in global mode */, cudaStream_t s);
+                       int64_t col0, const RegionMaps *rm /* null in global mode */,
+                       const EigScratch &es, cudaStream_t s);
 
 // ---------------------------------------------------------------- Fermi level, outputs
 // Deterministic two-level reductions; `partial` holds 2 * kReduceBlocks doubles,

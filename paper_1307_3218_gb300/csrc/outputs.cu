@@ -1,0 +1,232 @@
+// Fermi level and output columns of the multiple Arnoldi method on sm_103a.
+//
+// From each solved column's subspace levels eps_a, weights
+// w_a = sqrt(S_jj) V[0][a] t_a and P_j = K_pat V (arXiv:1307.3218, Section 2:
+// the Green's function determined by the subspace levels and vectors):
+//   N(mu)       = sum_j sum_a 2 f w_a,   E = sum_j sum_a 2 f eps_a w_a
+//   rho e_j     = P_j diag(2 f) t,   rho^E e_j = P_j diag(2 f eps) t
+//   G(z) e_j    = P_j diag(1 / (z - eps)) t      (Eq. 1 inside L_nu^(j))
+// with t = V^T K^T e_j and f(x) = 1 / (1 + e^x) at x = (eps - mu) / kT.
+#include "internal.h"
+
+namespace marnoldi {
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+__device__ __forceinline__ double fermi(double x)
+{
+    if (x >= 0.0) {
+        const double e = exp(-x);
+        return e / (1.0 + e);
+    }
+    return 1.0 / (1.0 + exp(x));
+}
+
+// Fixed-order block reduction of two values; thread 0 gets the totals.
+template <int OP>  // 0 sum, 1 (min, max)
+__device__ __forceinline__ double2 block_reduce2(double a, double b)
+{
+    __shared__ double2 red[32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const double ao = __shfl_xor_sync(kFull, a, o), bo = __shfl_xor_sync(kFull, b, o);
+        if (OP == 0) { a += ao; b += bo; } else { a = fmin(a, ao); b = fmax(b, bo); }
+    }
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    if (lane == 0) red[warp] = make_double2(a, b);
+    __syncthreads();
+    double2 r = red[0];
+    if (threadIdx.x == 0)
+        for (int q = 1; q < nw; ++q) {
+            if (OP == 0) { r.x += red[q].x; r.y += red[q].y; }
+            else { r.x = fmin(r.x, red[q].x); r.y = fmax(r.y, red[q].y); }
+        }
+    return r;
+}
+
+// Per-block partials, then the last block to finish (atomic ticket) combines
+// them in block order; no thread waits on another block.
+template <int OP>
+__device__ void finish_reduce(double a, double b, double *partial, unsigned *ticket, double *out)
+{
+    __shared__ int last;
+    const double2 r = block_reduce2<OP>(a, b);
+    if (threadIdx.x == 0) {
+        partial[2 * blockIdx.x] = r.x;
+        partial[2 * blockIdx.x + 1] = r.y;
+        __threadfence();
+        last = (atomicAdd(ticket, 1u) == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (last && threadIdx.x == 0) {
+        __threadfence();
+        const volatile double *vp = partial;
+        double x = vp[0], y = vp[1];
+        for (unsigned q = 1; q < gridDim.x; ++q) {
+            if (OP == 0) { x += vp[2 * q]; y += vp[2 * q + 1]; }
+            else { x = fmin(x, vp[2 * q]); y = fmax(y, vp[2 * q + 1]); }
+        }
+        out[0] = x;
+        out[1] = y;
+        *ticket = 0u;
+    }
+}
+
+__global__ void __launch_bounds__(256) minmax_kernel(int64_t total, int nu,
+                                                     const int *__restrict__ nu_eff,
+                                                     const double *__restrict__ eps,
+                                                     double *partial, unsigned *ticket, double *out)
+{
+    double lo = INFINITY, hi = -INFINITY;
+    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t c = idx / nu;
+        if (idx - c * nu < nu_eff[c]) {
+            lo = fmin(lo, eps[idx]);
+            hi = fmax(hi, eps[idx]);
+        }
+    }
+    finish_reduce<1>(lo, hi, partial, ticket, out);
+}
+
+__global__ void __launch_bounds__(256) count_kernel(int64_t total, int nu,
+                                                    const int *__restrict__ nu_eff,
+                                                    const double *__restrict__ eps,
+                                                    const double *__restrict__ w, double mu,
+                                                    double kT, double *partial, unsigned *ticket,
+                                                    double *out)
+{
+    double sn = 0.0, se = 0.0;
+    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t c = idx / nu;
+        if (idx - c * nu < nu_eff[c]) {
+            const double ea = eps[idx];
+            const double f2w = 2.0 * fermi((ea - mu) / kT) * w[idx];
+            sn += f2w;
+            se = fma(f2w, ea, se);
+        }
+    }
+    finish_reduce<0>(sn, se, partial, ticket, out);
+}
+
+// One CTA per solved column: y = 2 f t (and 2 f eps t), then the pattern rows
+// P_j y written to block (I, J) entry [a][b] of the BSR output.
+__global__ void __launch_bounds__(128) density_kernel(
+    int nu, const int64_t *__restrict__ cols, const int *__restrict__ nu_eff,
+    const double *__restrict__ eps, const double *__restrict__ t, const double *__restrict__ P,
+    const int64_t *__restrict__ p_off, const int64_t *__restrict__ rp,
+    const int64_t *__restrict__ tmap, double mu, double kT, double *__restrict__ rho,
+    double *__restrict__ rhoE)
+{
+    extern __shared__ double ys[];
+    double *y = ys, *ye = ys + nu;
+    const int64_t c = blockIdx.x;
+    const int64_t j = cols[c], J = j >> 2;
+    const int b = (int)(j & 3), n = nu_eff[c];
+    for (int a = threadIdx.x; a < nu; a += blockDim.x) {
+        double v = 0.0, ve = 0.0;
+        if (a < n) {
+            const double ea = eps[c * nu + a];
+            const double f2t = 2.0 * fermi((ea - mu) / kT) * t[c * nu + a];
+            v = f2t;
+            ve = f2t * ea;
+        }
+        y[a] = v;
+        ye[a] = ve;
+    }
+    __syncthreads();
+    const int64_t kb = rp[J];
+    const int npat = 4 * (int)(rp[J + 1] - kb);
+    const double *Pc = P + p_off[c];
+    for (int r = threadIdx.x; r < npat; r += blockDim.x) {
+        double s = 0.0, se = 0.0;
+        const double *row = Pc + (int64_t)r * nu;
+        for (int a = 0; a < n; ++a) {
+            s = fma(row[a], y[a], s);
+            se = fma(row[a], ye[a], se);
+        }
+        const int64_t o = tmap[kb + (r >> 2)] * 16 + (r & 3) * 4 + b;
+        rho[o] = s;
+        rhoE[o] = se;
+    }
+}
+
+__global__ void __launch_bounds__(128) green_kernel(
+    int nu, const int64_t *__restrict__ cols, const int *__restrict__ nu_eff,
+    const double *__restrict__ eps, const double *__restrict__ t, const double *__restrict__ P,
+    const int64_t *__restrict__ p_off, const int64_t *__restrict__ rp,
+    const int64_t *__restrict__ tmap, double zr, double zi, double *__restrict__ G)
+{
+    extern __shared__ double ys[];
+    double *yr = ys, *yi = ys + nu;
+    const int64_t c = blockIdx.x;
+    const int64_t j = cols[c], J = j >> 2;
+    const int b = (int)(j & 3), n = nu_eff[c];
+    for (int a = threadIdx.x; a < nu; a += blockDim.x) {
+        double vr = 0.0, vi = 0.0;
+        if (a < n) {  // t / (z - eps) = t (conj(z) - eps) / |z - eps|^2
+            const double dr = zr - eps[c * nu + a];
+            const double den = dr * dr + zi * zi;
+            const double ta = t[c * nu + a];
+            vr = ta * dr / den;
+            vi = -ta * zi / den;
+        }
+        yr[a] = vr;
+        yi[a] = vi;
+    }
+    __syncthreads();
+    const int64_t kb = rp[J];
+    const int npat = 4 * (int)(rp[J + 1] - kb);
+    const double *Pc = P + p_off[c];
+    for (int r = threadIdx.x; r < npat; r += blockDim.x) {
+        double sr = 0.0, sim = 0.0;
+        const double *row = Pc + (int64_t)r * nu;
+        for (int a = 0; a < n; ++a) {
+            sr = fma(row[a], yr[a], sr);
+            sim = fma(row[a], yi[a], sim);
+        }
+        const int64_t o = tmap[kb + (r >> 2)] * 16 + (r & 3) * 4 + b;
+        G[2 * o] = sr;
+        G[2 * o + 1] = sim;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_minmax(const ColumnState &st, double *partial, unsigned *ticket, double *out,
+                          cudaStream_t s)
+{
+    minmax_kernel<<<kReduceBlocks, 256, 0, s>>>(st.ncols * st.nu, st.nu, st.nu_eff, st.eps,
+                                                 partial, ticket, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_count(const ColumnState &st, double mu, double kT, double *partial,
+                         unsigned *ticket, double *out, cudaStream_t s)
+{
+    count_kernel<<<kReduceBlocks, 256, 0, s>>>(st.ncols * st.nu, st.nu, st.nu_eff, st.eps, st.w,
+                                                mu, kT, partial, ticket, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_density(const DeviceMatrix &A, const ColumnState &st, double mu, double kT,
+                           double *rho, double *rhoE, cudaStream_t s)
+{
+    if (st.ncols == 0) return cudaSuccess;
+    density_kernel<<<(unsigned)st.ncols, 128, 2 * st.nu * sizeof(double), s>>>(
+        st.nu, st.cols, st.nu_eff, st.eps, st.t, st.P, st.p_off, A.rp, A.tmap, mu, kT, rho, rhoE);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_green(const DeviceMatrix &A, const ColumnState &st, double zr, double zi,
+                         double *G, cudaStream_t s)
+{
+    if (st.ncols == 0) return cudaSuccess;
+    green_kernel<<<(unsigned)st.ncols, 128, 2 * st.nu * sizeof(double), s>>>(
+        st.nu, st.cols, st.nu_eff, st.eps, st.t, st.P, st.p_off, A.rp, A.tmap, zr, zi, G);
+    return cudaGetLastError();
+}
+
+}  // namespace marnoldi
