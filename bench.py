@@ -39,6 +39,11 @@ METRIC = "mArnoldi columns/s"
 UNIT = "columns/s"
 L2_FLUSH_BYTES = 256 << 20
 FP64_PEAK_NOTE = "152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz (nominal 1.25 TFLOP/s FP64)"
+# (dram__bytes_read + dram__bytes_write) / algorithmic bytes of one captured MGS
+# launch (ncu --set full, mixed precision, 608 columns, step n = 20):
+# (3.507104e9 + 0.034488e9) / (89 x 16,384 x 4 B x 608 = 3.546e9).
+# Must be re-measured (or removed) whenever the MGS kernel changes.
+MGS_DRAM_PER_ALGORITHMIC = {"mixed": 0.9988}
 
 
 def parse():
@@ -54,6 +59,8 @@ def parse():
     p.add_argument("--no-fp64", action="store_true", help="skip the FP64 side measurement")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-extra", action="store_true",
+                   help="skip the nu=100 and regional side measurements")
     p.add_argument("--cpu-seconds", type=float, default=15.0)
     p.add_argument("--region", type=int, default=0,
                    help="regional mode with this many atoms per region (0 = global mode)")
@@ -151,6 +158,8 @@ def mgs_algorithmic(nu: int, m: int, vbytes: int, ncols: int):
     update per entry and stored vector; the last step beta and one dot.
     """
     vals = sum(4 * (n + 1) + 2 + (2 if n >= 1 else 0) for n in range(nu - 1)) + (nu + 1 + 2)
+    if vbytes == 4:
+        vals += nu   # mixed precision also reads the lo word of u = H w_n once per step
     fmas = sum(5 * (n + 1) + (1 if n >= 1 else 0) for n in range(nu - 1)) + nu + 1
     return vals * m * vbytes * ncols, 2.0 * fmas * m * ncols
 
@@ -317,8 +326,17 @@ def main():
         bound = ach = peak = unit = peak_src = None
     roof = None
     if ach is not None:
+        # DRAM bytes per average launch: the ncu capture's DRAM/algorithmic ratio for
+        # this kernel (a smaller case of the same kernel; bytes scale with columns and
+        # stored vectors) times the algorithmic bytes per launch
+        ratio = MGS_DRAM_PER_ALGORITHMIC.get(args.precision) if dom == "mgs" and not args.region else None
+        launches_per_step = nlaunch / steps
+        traffic = round(ratio * by / launches_per_step) if ratio and by else None
         roof = {"kernel": dom, "bound": bound, "achieved": round(ach, 3), "peak": round(peak, 3),
-                "unit": unit, "frac": round(ach / peak, 4), "traffic": None,
+                "unit": unit, "frac": round(ach / peak, 4), "traffic": traffic,
+                "traffic_note": ("dram bytes per average launch = DRAM/algorithmic "
+                                 f"{ratio} (ncu, mgs_kernel<float,16,1024>, step n=20, 608 columns) "
+                                 "x algorithmic bytes per launch") if traffic else None,
                 "peak_source": peak_src, "launches": nlaunch, "avg_launch_ms": round(dom_ms / nlaunch, 4),
                 "algorithmic_per_step": {"bytes": by, "flops": fl}}
 
@@ -356,6 +374,21 @@ def main():
                                          "unit": "TFLOP/s", "frac": round(ach64 / pk64, 4)},
                         "result": {"E_band_eV": r64["E"], "mu_eV": r64["mu"], "N": r64["N"]}}
         m.marnoldi_destroy(r64["ctx"])
+
+    if not args.no_extra and not args.region and args.nu == 30:
+        # the metric's second subspace dimension, and regional (order-N) mode,
+        # on the same structure and precision
+        import copy
+        for label, nu_x, reg_x in (("nu100", 100, 0), ("regional_256", 30, 256)):
+            a2 = copy.copy(args)
+            a2.nu, a2.region = nu_x, reg_x
+            rx = time_gpu(m, t, cols, a2, prec, 3, 3, dev)
+            sx = statistics.mean(rx["times"]) / 1e3
+            line[label] = {"value": round(world * ncols / sx, 2), "unit": UNIT, "nu": nu_x,
+                           "mode": mode_name(a2), "ms_per_step": round(sx * 1e3, 3),
+                           "kernel_ms_per_step": {k: round(v[1] / 3, 3) for k, v in rx["stats"].items() if v[0]},
+                           "result": {"E_band_eV": rx["E"], "mu_eV": rx["mu"], "N": rx["N"]}}
+            m.marnoldi_destroy(rx["ctx"])
 
     if not args.no_e2e:
         e2e_s, h2d, d2h = time_e2e(m, t, cols, args, prec, max(3, args.steps // 2), 1)

@@ -342,6 +342,77 @@ __global__ void __launch_bounds__(256) spmm_f32_accurate_kernel(
     store4(Ylo + (int64_t)c * ldy + 4 * I, yl);
 }
 
+// Mixed precision over row tiles.  Rows adjacent in the (spatially sorted)
+// atom order share most of their neighbours, so a CTA stages the x entries of
+// its tile's neighbour union for its 32 columns in shared memory once (each
+// 16-byte entry gathered once instead of once per block that uses it: about
+// 3x fewer gathers on amorphous carbon), then every warp computes its rows
+// from shared memory.  Lanes are columns, as above, so the staged entries are
+// read without bank conflicts and the matrix block stays a broadcast load.
+// MODE 0: plain FP32 with the hi values (S); MODE 1: exact products and
+// two-sums over hi + lo with a (hi, lo) output (H).
+template <int MODE>
+__global__ void __launch_bounds__(256) spmm_tile_kernel(
+    const int *__restrict__ tile_row0, const int *__restrict__ tile_uptr,
+    const int *__restrict__ tile_u, const uint8_t *__restrict__ blk_u,
+    const int64_t *__restrict__ rp, const float *__restrict__ vals, const float *__restrict__ X,
+    int64_t ldx, float *__restrict__ Y, float *__restrict__ Ylo, int64_t ldy, int ncols)
+{
+    extern __shared__ __align__(16) float4 xs[];   // [kTileCap][32]
+    const int tile = blockIdx.x, lane = threadIdx.x, warp = threadIdx.y;
+    const int c = blockIdx.y * 32 + lane;
+    const bool live = c < ncols;
+    const int u0 = tile_uptr[tile], nt = tile_uptr[tile + 1] - u0;
+    const float *x = X + (int64_t)(live ? c : 0) * ldx;
+    for (int u = warp; u < nt; u += 8) {
+        const int J = tile_u[u0 + u];
+        xs[u * 32 + lane] = live ? __ldg(reinterpret_cast<const float4 *>(x + 4 * (int64_t)J))
+                                 : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    __syncthreads();
+    const int I1 = tile_row0[tile + 1];
+    for (int I = tile_row0[tile] + warp; I < I1; I += 8) {
+        float hi[4] = {0.f, 0.f, 0.f, 0.f}, lo[4] = {0.f, 0.f, 0.f, 0.f};
+        const int64_t k1 = rp[I + 1];
+        for (int64_t k = rp[I]; k < k1; ++k) {
+            const float4 x4 = xs[(int)blk_u[k] * 32 + lane];
+            const float xv[4] = {x4.x, x4.y, x4.z, x4.w};
+            const float *B = vals + 32 * k;
+#pragma unroll
+            for (int a = 0; a < 4; ++a) {
+                float h[4];
+                load4(B + 4 * a, h);
+                if constexpr (MODE == 1) {
+                    float l[4];
+                    load4(B + 16 + 4 * a, l);
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const float p = __fmul_rn(h[q], xv[q]);
+                        const float e = __fmaf_rn(h[q], xv[q], -p);
+                        df_add(hi[a], lo[a], p, __fmaf_rn(l[q], xv[q], e));
+                    }
+                } else {
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) hi[a] = fmaf(h[q], xv[q], hi[a]);
+                }
+            }
+        }
+        if (!live) continue;
+        if constexpr (MODE == 1) {
+            float yh[4], yl[4];
+#pragma unroll
+            for (int a = 0; a < 4; ++a) {
+                yh[a] = __fadd_rn(hi[a], lo[a]);
+                yl[a] = __fsub_rn(lo[a], __fsub_rn(yh[a], hi[a]));
+            }
+            store4(Y + (int64_t)c * ldy + 4 * I, yh);
+            store4(Ylo + (int64_t)c * ldy + 4 * I, yl);
+        } else {
+            store4(Y + (int64_t)c * ldy + 4 * I, hi);
+        }
+    }
+}
+
 // ------------------------------------------------------------------ MGS
 // One CTA of T threads per column; thread t owns entries r = t + v T
 // (v < VPT) of the column's vectors.  T is a compile-time constant, so the
@@ -600,6 +671,32 @@ cudaError_t launch_spmm(const DeviceMatrix &A, int which, const KrylovBatch &b, 
                         int64_t ldx, void *Y, int64_t ldy, cudaStream_t s)
 {
     const dim3 block(32, 8);
+    // The staged tile form pays off for the gather-bound plain S product; the
+    // accurate H product is bound by its exact-arithmetic FP32 work and runs
+    // faster in the direct form below.
+    if (b.prec == 1 && A.ntiles > 0 && which == 1) {
+        const size_t smem = (size_t)kTileCap * 32 * sizeof(float4);
+        static bool configured = false;
+        if (!configured) {
+            cudaError_t e = cudaFuncSetAttribute(spmm_tile_kernel<0>,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e == cudaSuccess)
+                e = cudaFuncSetAttribute(spmm_tile_kernel<1>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+            configured = true;
+        }
+        const dim3 tgrid((unsigned)A.ntiles, (unsigned)((b.nb + 31) / 32));
+        if (which == 0)
+            spmm_tile_kernel<1><<<tgrid, block, smem, s>>>(A.tile_row0, A.tile_uptr, A.tile_u, A.blk_u,
+                                                           A.rp, A.Hf, (const float *)X, ldx, (float *)Y,
+                                                           (float *)b.Ulo, ldy, b.nb);
+        else
+            spmm_tile_kernel<0><<<tgrid, block, smem, s>>>(A.tile_row0, A.tile_uptr, A.tile_u, A.blk_u,
+                                                           A.rp, A.Sf, (const float *)X, ldx, (float *)Y,
+                                                           nullptr, ldy, b.nb);
+        return cudaGetLastError();
+    }
     const dim3 grid((unsigned)((A.nbr + 7) / 8), (unsigned)((b.nb + 31) / 32));
     if (b.prec == 0)
         spmm_kernel<double><<<grid, block, 0, s>>>(A.nbr, A.rp, A.ci, which ? A.Sd : A.Hd,

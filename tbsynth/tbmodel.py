@@ -263,3 +263,17 @@ def tiny_system(n_atoms: int, seed: int = 0, radius: float | None = None,
     t = build_tb(s)
     t.meta.update(name=f"cluster-{n_atoms}", seed=seed)
     return t
+
+
+def tiny_hydrocarbon(n_atoms: int, n_hydrogen: int, seed: int = 0, box: float = 12.0) -> TBSystem:
+    """A small cluster in which n_hydrogen of the atoms are hydrogen (one s
+    orbital padded to a 4x4 block with three masked dummy orbitals)."""
+    from .structures import HYDROGEN
+    base = tiny_system(n_atoms, seed=seed, box=box)
+    s = base.structure
+    species = s.species.copy()
+    rng = np.random.default_rng(seed + 1000)
+    species[rng.choice(n_atoms, size=n_hydrogen, replace=False)] = HYDROGEN
+    t = build_tb(Structure(s.positions.copy(), species, s.box.copy()))
+    t.meta.update(name=f"hydrocarbon-{n_atoms}-{n_hydrogen}", seed=seed)
+    return t

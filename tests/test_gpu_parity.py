@@ -325,3 +325,42 @@ def test_c2_regional_sampled(m, c2, prec):
     else:
         assert drho <= 1e-5
         assert drhoE <= 1e-4
+
+
+# ----------------------------------------------------------------- padding orbitals
+
+@pytest.mark.parametrize("seed", [4, 1])
+def test_hydrocarbon_padding(m, seed):
+    from tbsynth import tiny_hydrocarbon
+    t = tiny_hydrocarbon(10, 4, seed=seed)
+    g = gpu_solve(m, t, 12)
+    ref = oracle.solve(t, nu=12, kT=KT)
+    assert_close_fp64(g, ref, t)
+    gm = gpu_solve(m, t, 12, prec=1)
+    refm = oracle.solve(t, nu=12, kT=KT, mu_fixed=gm["mu"])
+    e = mixed_errors(gm, refm, t)
+    assert e["drho"] <= 1e-5 and e["dE_per_atom"] <= 1e-6
+    ctx = m.setup_system(t, 0)
+    pad = int(np.nonzero(t.orbital_mask == 0)[0][0])
+    with pytest.raises(m.MarnoldiError) as ei:
+        m.marnoldi_solve(ctx, [pad], 4, 0, 1.0, KT)
+    assert ei.value.code == m.marnoldi.MARNOLDI_EINVAL
+
+
+def test_regional_beyond_global_limit(m):
+    """8,192 atoms (M = 32,768 > the global-mode limit): regional mode only; every column
+    on the GPU, a seeded sample recomputed by the regional oracle at the GPU's mu."""
+    t = amorphous_system(8192, seed=3)
+    ctx = m.setup_system(t, 0)
+    with pytest.raises(m.MarnoldiError) as ei:
+        m.marnoldi_solve(ctx, None, 30, 0, t.n_electrons, KT)
+    assert ei.value.code == m.marnoldi.MARNOLDI_EINVAL
+    for prec in (0, 1):
+        g = gpu_solve_regional(m, t, 30, 256, prec=prec)
+        assert g["N"] == pytest.approx(t.n_electrons, rel=1e-12 if prec == 0 else 1e-8)
+        sample = np.sort(np.random.default_rng(9).choice(t.M, size=8, replace=False))
+        ref = oracle.solve(t, nu=30, kT=KT, mu_fixed=g["mu"], cols=sample, region_atoms=256)
+        mask = ~np.isnan(ref.rho)
+        drho = np.abs(g["rho"][mask] - ref.rho[mask]).max()
+        print(f"8192-atom regional prec={prec}: drho={drho:.3e}")
+        assert drho <= (FP64_REL * np.abs(ref.rho[mask]).max() if prec == 0 else 1e-5)

@@ -395,3 +395,26 @@ def test_region_definition_and_convergence(c1):
         r = oracle.solve(c1, nu=16, kT=KT, region_atoms=nr, mu_fixed=ref.mu)
         errs.append(np.nanmax(np.abs(r.rho - ref.rho)))
     assert errs[-1] == 0.0 and errs[1] < errs[0]
+
+
+@pytest.mark.parametrize("seed", [4, 1])
+def test_padding_orbitals_dense_limit(seed):
+    """Hydrogen atoms padded to 4x4 blocks: the masked dummy orbitals never enter, and
+    nu = (real orbitals) reproduces the dense eigensolve on the real orbitals."""
+    from tbsynth import tiny_hydrocarbon
+    t = tiny_hydrocarbon(10, 4, seed=seed)
+    r = t.orbital_mask.astype(bool)
+    nr = int(r.sum())
+    sol = oracle.solve(t, nu=nr, kT=KT)
+    assert sol.N == pytest.approx(t.n_electrons, rel=1e-12)
+    H, S = t.dense()
+    ev, Phi = sl.eigh(H[np.ix_(r, r)], S[np.ix_(r, r)])
+    P = np.zeros((t.M, ev.size))
+    P[r] = Phi
+    rho = (P * fermi2((ev - sol.mu) / KT)) @ P.T
+    for (I, J), v in bsr_to_dense_blocks(t, sol.rho).items():
+        if not np.all(np.isnan(v)):
+            vv = np.where(np.isnan(v), 0.0, v)
+            np.testing.assert_allclose(vv, rho[4 * I:4 * I + 4, 4 * J:4 * J + 4], atol=1e-12)
+    # padding columns are never solved
+    assert set(sol.cols.cols.tolist()) == set(np.nonzero(r)[0].tolist())
