@@ -106,9 +106,16 @@ int marnoldi_setup(marnoldi_ctx **out, int64_t n_block_rows, const int64_t *row_
  *   columns, ncols  orbital indices to solve (host int64); columns == NULL and
  *                   ncols < 0 select every real orbital.  Duplicates and
  *                   padding orbitals are rejected (MARNOLDI_EINVAL).
- *   nu              subspace dimension, 1 <= nu <= min(M_real, 110).
+ *   nu              subspace dimension, 1 <= nu <= min(M_real, 110); in regional
+ *                   mode also nu <= 4 * region_atoms.
  *   region_atoms    0 = global mode (Krylov vectors over all M orbitals, M <= 16384).
- *                   > 0 = regional mode (not available in this build: MARNOLDI_EINVAL).
+ *                   N_reg > 0 = regional mode: column j of atom J is solved on the
+ *                   principal sub-pair of (H, S) over the N_reg atoms nearest J
+ *                   (squared minimum-image distance, ties to the lower atom index,
+ *                   J always included), so M may exceed 16384.  Needs positions
+ *                   and box at setup; 1 <= N_reg <= min(n_block_rows, 1024), else
+ *                   MARNOLDI_EINVAL.  N_reg = n_block_rows reproduces global mode
+ *                   bit for bit.
  *   electron_count  target N_e of the bisection (ignored when mu_fixed != NULL).
  *   kT              > 0.
  *   mu_fixed        NULL = find mu by bisection on N(mu) = sum_j sum_a 2 f w_a over
