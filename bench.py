@@ -40,10 +40,8 @@ UNIT = "columns/s"
 L2_FLUSH_BYTES = 256 << 20
 FP64_PEAK_NOTE = "152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz (nominal 1.25 TFLOP/s FP64)"
 # (dram__bytes_read + dram__bytes_write) / algorithmic bytes of one captured MGS
-# launch (ncu --set full, mixed precision, 608 columns, step n = 20):
-# (3.507104e9 + 0.034488e9) / (89 x 16,384 x 4 B x 608 = 3.546e9).
-# Must be re-measured (or removed) whenever the MGS kernel changes.
-MGS_DRAM_PER_ALGORITHMIC = {"mixed": 0.9988}
+# launch, by precision; empty until the current kernel has been captured.
+MGS_DRAM_PER_ALGORITHMIC: dict = {}
 
 
 def parse():
@@ -162,6 +160,64 @@ def mgs_algorithmic(nu: int, m: int, vbytes: int, ncols: int):
         vals += nu   # mixed precision also reads the lo word of u = H w_n once per step
     fmas = sum(5 * (n + 1) + (1 if n >= 1 else 0) for n in range(nu - 1)) + nu + 1
     return vals * m * vbytes * ncols, 2.0 * fmas * m * ncols
+
+
+def column_m_pad(m: int) -> int:
+    """Padded vector length of the column-per-CTA kernels (256 or 1024 threads x a power of two <= 16)."""
+    T = 256 if m <= 4096 else 1024
+    v = 1
+    while v < 16 and v * T < m:
+        v *= 2
+    return v * T
+
+
+def support_counts(t, cols, nu: int, m_pad: int):
+    """tcnt[c][L]: tiles of 8 atoms (32 vector entries) within L pattern hops of column c's atom.
+
+    Basis vector w_i of column c vanishes outside the tiles with L <= i, S w_i and
+    H w_i outside L <= i + 1 (breadth-first hop counts over the block pattern).
+    """
+    import scipy.sparse as sp
+    from scipy.sparse.csgraph import shortest_path
+    nbr = t.n_block_rows
+    G = sp.csr_matrix((np.ones(len(t.col_idx)), t.col_idx, t.row_ptr), shape=(nbr, nbr))
+    atoms, inv = np.unique(np.asarray(cols) // 4, return_inverse=True)
+    ntile = m_pad // 32
+    out = np.zeros((len(atoms), nu + 2), dtype=np.int64)
+    for a0 in range(0, len(atoms), 512):
+        D = shortest_path(G, unweighted=True, indices=atoms[a0:a0 + 512])
+        D = np.where(np.isfinite(D), D, 1e9)
+        if ntile * 8 > nbr:
+            D = np.concatenate([D, np.full((D.shape[0], ntile * 8 - nbr), 1e9)], axis=1)
+        th = D.reshape(D.shape[0], ntile, 8).min(axis=2)
+        for L in range(nu + 2):
+            out[a0:a0 + 512, L] = (th <= L).sum(axis=1)
+    return out[inv]
+
+
+def mgs_algorithmic_support(nu: int, tcnt, vbytes: int):
+    """Bytes and FP64 flops of the Gram-Schmidt steps over the basis vectors' supports.
+
+    As mgs_algorithmic, but every vector counts only the entries of its support
+    tiles (32 entries per tile): w_n and S w_n for beta_n over the tiles within
+    n hops, u (and its lo word in mixed precision) and the new w within n + 1,
+    the pair w_i, S w_i of each pass within i + 1.
+    """
+    E = 32.0 * np.asarray(tcnt).sum(axis=0)   # entries within L hops, summed over columns
+    vals = fmas = 0.0
+    for n in range(nu):
+        need_w = n + 1 < nu
+        s = sum(E[i + 1] for i in range(n + 1))
+        if n >= 1:
+            vals += 2 * E[n]
+            fmas += E[n]
+        vals += (2 if vbytes == 4 else 1) * E[n + 1]
+        vals += (2 if need_w else 1) * s
+        fmas += (3 if need_w else 1) * s
+        if need_w:
+            vals += 2 * s + E[n + 1]
+            fmas += 2 * s
+    return vals * vbytes, 2.0 * fmas
 
 
 def spmm_algorithmic(nu: int, m: int, nnzb: int, nbr: int, vbytes: int, ncols: int):
@@ -309,11 +365,14 @@ def main():
     dom = max(stats, key=lambda k: stats[k][1])
     nlaunch, dom_ms = stats[dom]
     steps = args.steps
+    tcnt = None if args.region else support_counts(t, cols, args.nu, column_m_pad(m_vec))
     if dom == "mgs":
-        by, fl = mgs_algorithmic(args.nu, m_vec, vb, ncols)
-    elif dom in ("spmm_H", "spmm_S"):
+        by, fl = (mgs_algorithmic_support(args.nu, tcnt, vb) if tcnt is not None
+                  else mgs_algorithmic(args.nu, m_vec, vb, ncols))
+    elif dom in ("spmm_H", "spmm_S", "spmm_HS"):
         by, fl = spmm_algorithmic(args.nu, m_vec, t.nnzb, t.n_block_rows, vb, ncols)
-        by, fl = by / 2, fl / 2
+        if dom != "spmm_HS":
+            by, fl = by / 2, fl / 2
     else:
         by, fl = None, None
     if prec == 1 and by is not None:
@@ -364,7 +423,8 @@ def main():
         s64 = statistics.mean(r64["times"]) / 1e3
         st64 = r64["stats"]
         ms64 = st64["mgs"][1]
-        by64, fl64 = mgs_algorithmic(args.nu, m_vec, 8, ncols)
+        by64, fl64 = (mgs_algorithmic_support(args.nu, tcnt, 8) if tcnt is not None
+                      else mgs_algorithmic(args.nu, m_vec, 8, ncols))
         ach64 = fl64 * max(3, args.steps // 2) / (ms64 / 1e3) / 1e12
         pk64 = 152 * 2 * 2 * 2.07e9 / 1e12
         line["fp64"] = {"value": round(world * ncols / s64, 2), "ms_per_step": round(s64 * 1e3, 3),

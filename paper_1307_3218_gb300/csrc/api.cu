@@ -780,7 +780,8 @@ int marnoldi_solve(marnoldi_ctx *c, const int64_t *columns, int64_t ncols, int n
     const size_t vs = c->prec == 0 ? 8 : 4;
     const size_t reg_per_col = regional ? (size_t)region_atoms * (12 + 8 * (size_t)c->rm.maxrow) : 0;
     const size_t per_col = al((size_t)2 * nu * shape.m_pad * vs) + (size_t)2 * shape.m_pad * vs +
-                           (size_t)nu * nu * 8 + (size_t)nu * 8 + 64 + reg_per_col;
+                           (size_t)nu * nu * 8 + (size_t)nu * 8 + 64 + reg_per_col +
+                           (size_t)(shape.m_pad / 32) * 3 + (size_t)(nu + 2) * 4;
     int64_t B = c->batch_override;
     if (B <= 0) {
         size_t freeb = 0, totb = 0;
@@ -802,7 +803,10 @@ int marnoldi_solve(marnoldi_ctx *c, const int64_t *columns, int64_t ncols, int n
                  oRi = oRc + (regional ? al((size_t)B * region_atoms * 4) : 0),
                  oRk = oRi + (regional ? al((size_t)B * region_atoms * c->rm.maxrow * 4) : 0),
                  oRs = oRk + (regional ? al((size_t)B * region_atoms * c->rm.maxrow * 4) : 0),
-                 oEg = oRs + (regional ? al((size_t)B * 4) : 0);
+                 oTh = oRs + (regional ? al((size_t)B * 4) : 0),
+                 oTo = oTh + al((size_t)B * (shape.m_pad / 32)),
+                 oTc = oTo + al((size_t)B * (shape.m_pad / 32) * 2),
+                 oEg = oTc + al((size_t)B * (nu + 2) * 4);
     // eigensolve scratch, for chunks of at most ceig subspaces
     EigScratch es;
     es.nr_max = 4 * c->maxrow + 2;
@@ -843,6 +847,10 @@ int marnoldi_solve(marnoldi_ctx *c, const int64_t *columns, int64_t ncols, int n
     kb.status = (int *)(wb + oS);
     kb.nu_eff = (int *)(wb + oN);
     kb.m = m_vec;
+    kb.ntile = (int)(shape.m_pad / 32);
+    kb.thop = (uint8_t *)(wb + oTh);
+    kb.tinv = (uint16_t *)(wb + oTo);
+    kb.tcnt = (int *)(wb + oTc);
     es.D = (double *)(wb + oED);
     es.E = (double *)(wb + oEE);
     es.RQ = (double *)(wb + oERQ);
@@ -868,32 +876,39 @@ int marnoldi_solve(marnoldi_ctx *c, const int64_t *columns, int64_t ncols, int n
             if ((rc = find_regions(c, kb))) return rc;
             if ((rc = launch(c, KK_REGION, [&] { return launch_local_bsr(c->A, c->rm, kb, c->stream); })))
                 return rc;
-            if ((rc = launch(c, KK_INIT, [&] { return launch_init_regional(c->A, c->rm, kb, c->stream); })))
-                return rc;
-        } else if ((rc = launch(c, KK_INIT, [&] { return launch_init(c->A, kb, c->stream); }))) {
-            return rc;
         }
+        // the vectors are stored in the tile order that the support search sets
+        if ((rc = launch(c, KK_SUPPORT, [&] { return launch_support(c->A, rmp, kb, c->stream); })))
+            return rc;
+        if ((rc = launch(c, KK_INIT, [&] {
+                 return regional ? launch_init_regional(c->A, c->rm, kb, c->stream)
+                                 : launch_init(c->A, kb, c->stream);
+             })))
+            return rc;
         for (int n = 0; n < nu; ++n) {
-            // slot n holds w_n (unnormalised); the MGS of step n scales it
+            // slot n holds w_n (unnormalised); H w_n goes to U and, for n >= 1,
+            // S w_n to its slot (S w_0 comes from the initialisation); the MGS
+            // of step n scales them and writes w_{n+1}
             const char *Kn = (const char *)kb.K + (size_t)n * mp * vs;
-            if ((rc = launch(c, KK_SPMM_H, [&] {
-                     return regional ? launch_spmm_regional(c->A, c->rm, 0, kb, Kn, (int64_t)nu * mp,
-                                                            kb.U, mp, c->stream)
-                                     : launch_spmm(c->A, 0, kb, Kn, (int64_t)nu * mp, kb.U, mp, c->stream);
-                 })))
+            char *SKn = n > 0 ? (char *)kb.SK + (size_t)n * mp * vs : nullptr;
+            if (regional) {
+                if ((rc = launch(c, KK_SPMM_H, [&] {
+                         return launch_spmm_regional(c->A, c->rm, 0, kb, Kn, (int64_t)nu * mp, kb.U, mp,
+                                                     n + 1, c->stream);
+                     })))
+                    return rc;
+                if (SKn && (rc = launch(c, KK_SPMM_S, [&] {
+                                return launch_spmm_regional(c->A, c->rm, 1, kb, Kn, (int64_t)nu * mp, SKn,
+                                                            (int64_t)nu * mp, n + 1, c->stream);
+                            })))
+                    return rc;
+            } else if ((rc = launch(c, KK_SPMM_HS, [&] {
+                            return launch_spmm_hs(c->A, kb, Kn, (int64_t)nu * mp, SKn, (int64_t)nu * mp,
+                                                  n + 1, c->stream);
+                        }))) {
                 return rc;
-            const int need_w = n + 1 < nu;
-            if ((rc = launch(c, KK_MGS, [&] { return launch_mgs(kb, n, need_w, tau, c->stream); })))
-                return rc;
-            if (!need_w) break;
-            char *Kn1 = (char *)kb.K + (size_t)(n + 1) * mp * vs;
-            char *SKn1 = (char *)kb.SK + (size_t)(n + 1) * mp * vs;
-            if ((rc = launch(c, KK_SPMM_S, [&] {
-                     return regional ? launch_spmm_regional(c->A, c->rm, 1, kb, Kn1, (int64_t)nu * mp,
-                                                            SKn1, (int64_t)nu * mp, c->stream)
-                                     : launch_spmm(c->A, 1, kb, Kn1, (int64_t)nu * mp, SKn1,
-                                                   (int64_t)nu * mp, c->stream);
-                 })))
+            }
+            if ((rc = launch(c, KK_MGS, [&] { return launch_mgs(kb, n, n + 1 < nu, tau, c->stream); })))
                 return rc;
         }
         if ((rc = launch(c, KK_EIG, [&] { return launch_eig(c->A, kb, c->st, start, rmp, es, c->stream); })))

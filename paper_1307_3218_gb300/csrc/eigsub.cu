@@ -60,7 +60,8 @@ __device__ __forceinline__ int find_sorted(const int *__restrict__ R, int n, int
 template <typename VT>
 __global__ void __launch_bounds__(kTriThreads) eig_tridiag_kernel(
     const double *__restrict__ Hsub, const int *__restrict__ bnu_eff,
-    const double *__restrict__ bscale, const VT *__restrict__ K, int64_t m_pad, int nu,
+    const double *__restrict__ bscale, const VT *__restrict__ K, int64_t m_pad,
+    const uint16_t *__restrict__ tinv, int nb, int nu,
     const int64_t *__restrict__ bcols, const int64_t *__restrict__ rp,
     const int32_t *__restrict__ ci, const int *__restrict__ reg, int n_reg, int cofs,
     double *__restrict__ D, double *__restrict__ E, double *__restrict__ RQ, int nr_max)
@@ -100,11 +101,12 @@ __global__ void __launch_bounds__(kTriThreads) eig_tridiag_kernel(
         if (r == 0) {
             val = i == 0 ? 1.0 : 0.0;
         } else if (r == 1) {
-            val = si * (double)Kc[(int64_t)i * m_pad + jl];
+            val = si * (double)Kc[(int64_t)i * m_pad + vpos(tinv, nb, c, jl)];
         } else {
             const int atom = ci[kb + ((r - 2) >> 2)];
             const int64_t lr = Rg ? find_sorted(Rg, n_reg, atom) : atom;
-            val = lr >= 0 ? si * (double)Kc[(int64_t)i * m_pad + 4 * lr + ((r - 2) & 3)] : 0.0;
+            val = lr >= 0 ? si * (double)Kc[(int64_t)i * m_pad + vpos(tinv, nb, c, 4 * lr + ((r - 2) & 3))]
+                          : 0.0;
         }
         R[r * lda + i] = val;
     }
@@ -365,7 +367,7 @@ cudaError_t tridiag_dispatch(const DeviceMatrix &A, const KrylovBatch &b, const 
         configured = smem;
     }
     eig_tridiag_kernel<VT><<<nb2, kTriThreads, smem, s>>>(
-        b.Hsub, b.nu_eff, b.scale, (const VT *)b.K, b.shape.m_pad, nu, b.cols, A.rp, A.ci,
+        b.Hsub, b.nu_eff, b.scale, (const VT *)b.K, b.shape.m_pad, b.tinv, b.nb, nu, b.cols, A.rp, A.ci,
         rm ? rm->reg : nullptr, rm ? rm->n_reg : 0, cofs, es.D, es.E, es.RQ, es.nr_max);
     return cudaGetLastError();
 }

@@ -20,6 +20,8 @@ enum KernelKind {
     KK_DENSITY,
     KK_GREEN,
     KK_REGION,
+    KK_SUPPORT,
+    KK_SPMM_HS,
     KK_NKINDS
 };
 
@@ -64,7 +66,28 @@ struct KrylovBatch {
     int *status;
     int *nu_eff;
     const int64_t *cols;  // global orbital column of each batch column
+    // Structural support of the basis, over tiles of 8 atoms (32 vector
+    // entries; t < ntile = m_pad / 32):
+    //   thop[t * nb + c]          fewest pattern hops from the column's atom to
+    //                             an atom of tile t (255: more than nu + 1)
+    //   tinv[t * nb + c]          position of tile t in column c's tile order,
+    //                             (thop, t) ascending
+    //   tcnt[c * (nu + 2) + L]    number of tiles with thop <= L (L <= nu + 1)
+    // Column c's vectors (K, SK, U, Ulo) are stored in its tile order: entry r
+    // at position vpos(r) = 32 tinv[r / 32] + r % 32.  w_i vanishes outside
+    // the first tcnt[i] tiles, S w_i and H w_i outside the first tcnt[i + 1].
+    int ntile = 0;
+    uint8_t *thop = nullptr;
+    uint16_t *tinv = nullptr;
+    int *tcnt = nullptr;
 };
+
+// Storage position of vector entry r of batch column c (see KrylovBatch).
+__device__ __forceinline__ int64_t vpos(const uint16_t *__restrict__ tinv, int nb, int c, int64_t r)
+{
+    return 32 * (int64_t)tinv[(r >> 5) * nb + c] + (r & 31);
+}
+constexpr int kMaxTiles = (int)(kMaxGlobalM / 32);
 
 struct DeviceMatrix {
     int64_t nbr, nnzb;
@@ -111,11 +134,29 @@ cudaError_t launch_init_regional(const DeviceMatrix &A, const RegionMaps &rm, co
                                  cudaStream_t s);
 cudaError_t launch_spmm_regional(const DeviceMatrix &A, const RegionMaps &rm, int which,
                                  const KrylovBatch &b, const void *X, int64_t ldx, void *Y,
-                                 int64_t ldy, cudaStream_t s);
+                                 int64_t ldy, int lim, cudaStream_t s);
+
+// Position of atom a in the ascending list R[0..n), or -1.
+__device__ __forceinline__ int find_sorted(const int *__restrict__ R, int n, int a)
+{
+    int lo = 0, hi = n;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (R[mid] < a) lo = mid + 1; else hi = mid;
+    }
+    return (lo < n && R[lo] == a) ? lo : -1;
+}
 
 cudaError_t launch_init(const DeviceMatrix &A, const KrylovBatch &b, cudaStream_t s);
-cudaError_t launch_spmm(const DeviceMatrix &A, int which /*0 H, 1 S*/, const KrylovBatch &b,
-                        const void *X, int64_t ldx, void *Y, int64_t ldy, cudaStream_t s);
+// Fills thop / tinv / tcnt of the batch (rm = null in global mode).
+cudaError_t launch_support(const DeviceMatrix &A, const RegionMaps *rm, const KrylovBatch &b,
+                           cudaStream_t s);
+// U (and Ulo) = H X and, when SY is not null, SY = S X for the batch (X and
+// SY with column strides ldx, ldsy; U with m_pad); rows of tiles with
+// thop > lim are written as zeros without being computed (X must vanish
+// outside thop <= lim - 1).
+cudaError_t launch_spmm_hs(const DeviceMatrix &A, const KrylovBatch &b, const void *X, int64_t ldx,
+                           void *SY, int64_t ldsy, int lim, cudaStream_t s);
 cudaError_t launch_mgs(const KrylovBatch &b, int n, int need_w, double tau, cudaStream_t s);
 
 // ---------------------------------------------------------------- subspace eigensolve

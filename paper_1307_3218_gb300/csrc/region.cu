@@ -146,16 +146,6 @@ __global__ void __launch_bounds__(1024) region_kernel(
     if (threadIdx.x == 0) rstat[c] = 0;
 }
 
-__device__ __forceinline__ int find_sorted(const int *__restrict__ R, int n, int a)
-{
-    int lo = 0, hi = n;
-    while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        if (R[mid] < a) lo = mid + 1; else hi = mid;
-    }
-    return (lo < n && R[lo] == a) ? lo : -1;
-}
-
 __global__ void __launch_bounds__(256) local_bsr_kernel(
     const int64_t *__restrict__ rp, const int32_t *__restrict__ ci, const int *__restrict__ reg,
     int n_reg, int maxrow, int *__restrict__ lcnt, int *__restrict__ lci, int *__restrict__ lgk)
@@ -186,7 +176,8 @@ __global__ void init_regional_kernel(const double *__restrict__ Sv, const double
                                      const int *__restrict__ lci, const int *__restrict__ lgk,
                                      VT *__restrict__ K, VT *__restrict__ SK,
                                      double *__restrict__ scale, int *__restrict__ status,
-                                     int *__restrict__ nu_eff, int nu, int64_t m_pad)
+                                     int *__restrict__ nu_eff, int nu, int64_t m_pad,
+                                     const uint16_t *__restrict__ tinv, int nb)
 {
     const int c = blockIdx.x;
     const int64_t j = cols[c];
@@ -210,7 +201,7 @@ __global__ void init_regional_kernel(const double *__restrict__ Sv, const double
     }
     const double inv = 1.0 / sqrt(sdiag[j]);
     if (threadIdx.x == 0) {
-        k0[4 * pJ + b] = (VT)inv;
+        k0[vpos(tinv, nb, c, 4 * pJ + b)] = (VT)inv;
         scale[(int64_t)c * nu] = 1.0;
         status[c] = 0;
         nu_eff[c] = nu;
@@ -221,7 +212,7 @@ __global__ void init_regional_kernel(const double *__restrict__ Sv, const double
         const int q = lci[base + (int64_t)s * n_reg + pJ];
         const int64_t k = lgk[base + (int64_t)s * n_reg + pJ];
 #pragma unroll
-        for (int a = 0; a < 4; ++a) sk0[4 * q + a] = (VT)(Sv[16 * k + 4 * b + a] * inv);
+        for (int a = 0; a < 4; ++a) sk0[vpos(tinv, nb, c, 4 * q + a)] = (VT)(Sv[16 * k + 4 * b + a] * inv);
     }
 }
 
@@ -238,26 +229,31 @@ __device__ __forceinline__ void df_add(float &hi, float &lo, float h2, float l2)
 // local-structure reads coalesce and the x gathers stay inside the column's
 // short local vector.  MODE 0: FP64.  MODE 1: FP32 with hi values (S).
 // MODE 2: FP32, exact products and two-sums over hi + lo, output as a
-// (hi, lo) pair (H; the subspace matrix entries use it).
+// (hi, lo) pair (H; the subspace matrix entries use it).  Rows whose support
+// tile lies more than `lim` hops from the column's atom are exact zeros and
+// are written without being computed.
 template <typename VT, int MODE>
 __global__ void __launch_bounds__(256) spmm_regional_kernel(
     int n_reg, int maxrow, const int *__restrict__ lcnt, const int *__restrict__ lci,
     const int *__restrict__ lgk, const VT *__restrict__ vals, const VT *__restrict__ X,
-    int64_t ldx, VT *__restrict__ Y, VT *__restrict__ Ylo, int64_t ldy, int ncols)
+    int64_t ldx, VT *__restrict__ Y, VT *__restrict__ Ylo, int64_t ldy, int ncols,
+    const uint8_t *__restrict__ thop, const uint16_t *__restrict__ tinv, int lim)
 {
     const int p = blockIdx.x * 32 + threadIdx.x;
     const int c = blockIdx.y * 8 + threadIdx.y;
     if (p >= n_reg || c >= ncols) return;
     const VT *x = X + (int64_t)c * ldx;
     const int64_t base = (int64_t)c * maxrow * n_reg;
-    const int cnt = lcnt[(int64_t)c * n_reg + p];
+    const bool act = (int)thop[(int64_t)(p >> 3) * ncols + c] <= lim;
+    const int cnt = act ? lcnt[(int64_t)c * n_reg + p] : 0;
     VT acc[4] = {VT(0), VT(0), VT(0), VT(0)}, acl[4] = {VT(0), VT(0), VT(0), VT(0)};
     for (int s = 0; s < cnt; ++s) {
         const int q = lci[base + (int64_t)s * n_reg + p];
         const int64_t k = lgk[base + (int64_t)s * n_reg + p];
         VT xv[4];
+        const VT *xq = x + 32 * (int64_t)tinv[(int64_t)(q >> 3) * ncols + c] + 4 * (q & 7);
 #pragma unroll
-        for (int e = 0; e < 4; ++e) xv[e] = x[4 * q + e];
+        for (int e = 0; e < 4; ++e) xv[e] = xq[e];
         constexpr int stride = MODE == 0 ? 16 : 32;
         const VT *B = vals + stride * k;
 #pragma unroll
@@ -275,9 +271,10 @@ __global__ void __launch_bounds__(256) spmm_regional_kernel(
             }
         }
     }
-    VT *y = Y + (int64_t)c * ldy + 4 * p;
+    const int64_t yp = 32 * (int64_t)tinv[(int64_t)(p >> 3) * ncols + c] + 4 * (p & 7);
+    VT *y = Y + (int64_t)c * ldy + yp;
     if constexpr (MODE == 2) {
-        VT *yl = Ylo + (int64_t)c * ldy + 4 * p;
+        VT *yl = Ylo + (int64_t)c * ldy + yp;
 #pragma unroll
         for (int a = 0; a < 4; ++a) {
             const float h = __fadd_rn(acc[a], acl[a]);
@@ -328,32 +325,35 @@ cudaError_t launch_init_regional(const DeviceMatrix &A, const RegionMaps &rm, co
     if (b.prec == 0)
         init_regional_kernel<double><<<b.nb, 256, 0, s>>>(
             A.Sd, A.sdiag, b.cols, rm.reg, rm.n_reg, rm.maxrow, rm.lcnt, rm.lci, rm.lgk,
-            (double *)b.K, (double *)b.SK, b.scale, b.status, b.nu_eff, b.nu, b.shape.m_pad);
+            (double *)b.K, (double *)b.SK, b.scale, b.status, b.nu_eff, b.nu, b.shape.m_pad,
+            b.tinv, b.nb);
     else
         init_regional_kernel<float><<<b.nb, 256, 0, s>>>(
             A.Sd, A.sdiag, b.cols, rm.reg, rm.n_reg, rm.maxrow, rm.lcnt, rm.lci, rm.lgk,
-            (float *)b.K, (float *)b.SK, b.scale, b.status, b.nu_eff, b.nu, b.shape.m_pad);
+            (float *)b.K, (float *)b.SK, b.scale, b.status, b.nu_eff, b.nu, b.shape.m_pad,
+            b.tinv, b.nb);
     return cudaGetLastError();
 }
 
 cudaError_t launch_spmm_regional(const DeviceMatrix &A, const RegionMaps &rm, int which,
                                  const KrylovBatch &b, const void *X, int64_t ldx, void *Y,
-                                 int64_t ldy, cudaStream_t s)
+                                 int64_t ldy, int lim, cudaStream_t s)
 {
+    if (!b.thop || !b.tinv || b.ntile * 8 < rm.n_reg) return cudaErrorInvalidValue;
     const dim3 block(32, 8);
     const dim3 grid((unsigned)((rm.n_reg + 31) / 32), (unsigned)((b.nb + 7) / 8));
     if (b.prec == 0)
         spmm_regional_kernel<double, 0><<<grid, block, 0, s>>>(
             rm.n_reg, rm.maxrow, rm.lcnt, rm.lci, rm.lgk, which ? A.Sd : A.Hd, (const double *)X,
-            ldx, (double *)Y, nullptr, ldy, b.nb);
+            ldx, (double *)Y, nullptr, ldy, b.nb, b.thop, b.tinv, lim);
     else if (which == 0)
         spmm_regional_kernel<float, 2><<<grid, block, 0, s>>>(
             rm.n_reg, rm.maxrow, rm.lcnt, rm.lci, rm.lgk, A.Hf, (const float *)X, ldx, (float *)Y,
-            (float *)b.Ulo, ldy, b.nb);
+            (float *)b.Ulo, ldy, b.nb, b.thop, b.tinv, lim);
     else
         spmm_regional_kernel<float, 1><<<grid, block, 0, s>>>(
             rm.n_reg, rm.maxrow, rm.lcnt, rm.lci, rm.lgk, A.Sf, (const float *)X, ldx, (float *)Y,
-            nullptr, ldy, b.nb);
+            nullptr, ldy, b.nb, b.thop, b.tinv, lim);
     return cudaGetLastError();
 }
 

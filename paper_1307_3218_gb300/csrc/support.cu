@@ -1,0 +1,112 @@
+// Structural support of the Krylov vectors of the multiple Arnoldi method.
+//
+// The subspace of column j is span{e_j, H e_j, ..., H^(nu-1) e_j}
+// (arXiv:1307.3218, Section 2).  Its i-th basis vector is a combination of
+// H^l e_j (l <= i), so it vanishes on every atom more than i hops from the
+// column's atom J in the block pattern of H and S; S and H applied to it
+// vanish beyond i + 1 hops.  The values there are exact zeros (sums of
+// products with exact zeros), so a kernel that skips those entries computes
+// bit for bit what the dense sweep computes.  Early basis vectors of a large
+// cell cover a small part of it: on 4096-atom amorphous carbon at nu = 30 the
+// Gram-Schmidt sweeps touch about two thirds of the dense entries.
+//
+// support_kernel: one CTA per batch column runs a breadth-first search from
+// J over the block pattern (global mode) or the region's local pattern
+// (regional mode), capped at nu + 1 hops, and summarises it per tile of 8
+// atoms (32 vector entries): thop[t][c] (fewest hops into tile t), the
+// position of each tile in (thop, t) order, and the number of tiles within
+// each hop count.  The column's vectors are stored in that tile order, so
+// every basis vector's support is a prefix of its slot.
+#include "internal.h"
+
+namespace marnoldi {
+namespace {
+
+template <bool kRegional>
+__global__ void __launch_bounds__(256) support_kernel(
+    const int64_t *__restrict__ rp, const int32_t *__restrict__ ci, int nbr,
+    const int *__restrict__ reg, int n_reg, int maxrow, const int *__restrict__ lcnt,
+    const int *__restrict__ lci, const int64_t *__restrict__ cols, int nb, int ntile, int maxlev,
+    uint8_t *__restrict__ thop, uint16_t *__restrict__ tinv, int *__restrict__ tcnt)
+{
+    extern __shared__ uint8_t dist[];   // per atom (global or local index)
+    __shared__ uint8_t th[kMaxTiles];
+    __shared__ int start[kMaxNu + 3];
+    const int c = blockIdx.x, tid = threadIdx.x;
+    const int na = kRegional ? n_reg : nbr;
+    const int Jg = (int)(cols[c] >> 2);
+    const int J = kRegional ? find_sorted(reg + (int64_t)c * n_reg, n_reg, Jg) : Jg;
+    const int64_t lbase = (int64_t)c * maxrow * n_reg;
+    for (int a = tid; a < na; a += blockDim.x) dist[a] = a == J ? 0 : 255;
+    __syncthreads();
+    // level-synchronous search; every writer of dist[b] in a level writes the
+    // same value, and a reader of the level's frontier never sees it change
+    for (int lev = 0; lev < maxlev; ++lev) {
+        int grew = 0;
+        for (int a = tid; a < na; a += blockDim.x) {
+            if (dist[a] != lev) continue;
+            if constexpr (kRegional) {
+                const int cnt = lcnt[(int64_t)c * n_reg + a];
+                for (int s = 0; s < cnt; ++s) {
+                    const int b = lci[lbase + (int64_t)s * n_reg + a];
+                    if (dist[b] == 255) { dist[b] = (uint8_t)(lev + 1); grew = 1; }
+                }
+            } else {
+                for (int64_t k = rp[a]; k < rp[a + 1]; ++k) {
+                    const int b = ci[k];
+                    if (dist[b] == 255) { dist[b] = (uint8_t)(lev + 1); grew = 1; }
+                }
+            }
+        }
+        if (!__syncthreads_or(grew)) break;
+    }
+    for (int t = tid; t < ntile; t += blockDim.x) {
+        int h = 255;
+        const int a1 = min(8 * t + 8, na);
+        for (int a = 8 * t; a < a1; ++a) h = min(h, (int)dist[a]);
+        th[t] = (uint8_t)h;
+        thop[(int64_t)t * nb + c] = (uint8_t)h;
+    }
+    __syncthreads();
+    if (tid == 0) {   // stable counting sort of the tiles by hop count
+        for (int L = 0; L <= maxlev; ++L) start[L] = 0;
+        for (int t = 0; t < ntile; ++t)
+            if (th[t] <= maxlev) ++start[th[t]];
+        int run = 0;
+        for (int L = 0; L <= maxlev; ++L) {
+            const int n = start[L];
+            start[L] = run;
+            run += n;
+            tcnt[(int64_t)c * (maxlev + 1) + L] = run;
+        }
+        int tail = run;
+        for (int t = 0; t < ntile; ++t) {
+            const int h = th[t];
+            tinv[(int64_t)t * nb + c] = (uint16_t)(h <= maxlev ? start[h]++ : tail++);
+        }
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_support(const DeviceMatrix &A, const RegionMaps *rm, const KrylovBatch &b,
+                           cudaStream_t s)
+{
+    const int maxlev = b.nu + 1;
+    if (b.ntile > kMaxTiles || b.ntile * 32 != b.shape.m_pad || maxlev > 254)
+        return cudaErrorInvalidValue;
+    if (rm) {
+        if (rm->n_reg > kMaxRegion) return cudaErrorInvalidValue;
+        support_kernel<true><<<b.nb, 256, rm->n_reg, s>>>(
+            A.rp, A.ci, (int)A.nbr, rm->reg, rm->n_reg, rm->maxrow, rm->lcnt, rm->lci, b.cols, b.nb,
+            b.ntile, maxlev, b.thop, b.tinv, b.tcnt);
+    } else {
+        if (A.nbr > kMaxGlobalM / 4) return cudaErrorInvalidValue;
+        support_kernel<false><<<b.nb, 256, (size_t)A.nbr, s>>>(
+            A.rp, A.ci, (int)A.nbr, nullptr, 0, 0, nullptr, nullptr, b.cols, b.nb, b.ntile, maxlev,
+            b.thop, b.tinv, b.tcnt);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace marnoldi
