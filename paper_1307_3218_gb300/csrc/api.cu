@@ -563,54 +563,6 @@ int marnoldi_setup(marnoldi_ctx **out, int64_t n_block_rows, const int64_t *row_
         }
         c->A.Hf = dHf;
         c->A.Sf = dSf;
-        // row tiles for the FP32 SpMM: consecutive block rows while the union of
-        // their block columns stays within kTileCap (and at most kTileRows rows)
-        std::vector<int> row0, uptr, ucols;
-        std::vector<uint8_t> bu(nnzb);
-        std::vector<int32_t> un;
-        row0.push_back(0);
-        uptr.push_back(0);
-        for (int64_t I0 = 0; I0 < n_block_rows;) {
-            un.clear();
-            int64_t r = I0;
-            while (r < n_block_rows && r - I0 < kTileRows) {
-                std::vector<int32_t> merged;
-                std::set_union(un.begin(), un.end(), c->ci.begin() + c->rp[r], c->ci.begin() + c->rp[r + 1],
-                               std::back_inserter(merged));
-                if ((int)merged.size() > kTileCap && r > I0) break;
-                if ((int)merged.size() > kTileCap) { un.clear(); break; }   // one row alone overflows
-                un.swap(merged);
-                ++r;
-            }
-            if (un.empty()) {   // a row with more than kTileCap blocks: no tiles at all
-                row0.clear();
-                break;
-            }
-            for (int64_t I = I0; I < r; ++I)
-                for (int64_t k = c->rp[I]; k < c->rp[I + 1]; ++k)
-                    bu[k] = (uint8_t)(std::lower_bound(un.begin(), un.end(), c->ci[k]) - un.begin());
-            ucols.insert(ucols.end(), un.begin(), un.end());
-            row0.push_back((int)r);
-            uptr.push_back((int)ucols.size());
-            I0 = r;
-        }
-        if (!row0.empty()) {
-            int *dr0 = nullptr, *dup = nullptr, *duc = nullptr;
-            uint8_t *dbu = nullptr;
-            if ((rc = dupload(c, &dr0, row0.data(), row0.size(), "tile rows")) ||
-                (rc = dupload(c, &dup, uptr.data(), uptr.size(), "tile unions")) ||
-                (rc = dupload(c, &duc, ucols.data(), ucols.size(), "tile columns")) ||
-                (rc = dupload(c, &dbu, bu.data(), bu.size(), "block positions"))) {
-                g_setup_err = c->err;
-                marnoldi_destroy(c);
-                return rc;
-            }
-            c->A.ntiles = (int)row0.size() - 1;
-            c->A.tile_row0 = dr0;
-            c->A.tile_uptr = dup;
-            c->A.tile_u = duc;
-            c->A.blk_u = dbu;
-        }
     }
     // reduction scratch
     void *p = dalloc(c, (2 * kReduceBlocks + 2) * sizeof(double) + 16);

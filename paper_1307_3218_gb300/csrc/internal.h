@@ -99,16 +99,7 @@ struct DeviceMatrix {
     const float *Hf, *Sf;
     const double *sdiag;     // S_jj, length 4 nbr
     const int64_t *tmap;     // block (J, I) -> index of block (I, J)
-    // Row tiles (mixed precision, global mode): tile t holds block rows
-    // [tile_row0[t], tile_row0[t+1]) and the sorted union of their block
-    // columns tile_u[tile_uptr[t] .. tile_uptr[t+1]) (at most kTileCap);
-    // blk_u[k] is block k's column position in its tile's union.
-    int ntiles = 0;
-    const int *tile_row0 = nullptr, *tile_uptr = nullptr, *tile_u = nullptr;
-    const uint8_t *blk_u = nullptr;
 };
-constexpr int kTileCap = 128;    // union entries per row tile
-constexpr int kTileRows = 32;    // block rows per row tile
 
 // ---------------------------------------------------------------- regional mode
 // Per batch column c: reg[c][p] (region atoms, ascending), lcnt[c][p] local

@@ -301,67 +301,6 @@ __global__ void __launch_bounds__(256) spmm_hs_kernel(
     }
 }
 
-// Plain FP32 S product over row tiles.  Rows adjacent in the (spatially
-// sorted) atom order share most of their neighbours, so a CTA stages the x
-// entries of its tile's neighbour union for its 32 columns in shared memory
-// once (each 16-byte entry gathered once instead of once per block that uses
-// it: about 3x fewer gathers on amorphous carbon), then every warp computes
-// its rows from shared memory.  Lanes are columns, as above, so the staged
-// entries are read without bank conflicts and the matrix block stays a
-// broadcast load.  Entries outside a column's input support are staged as
-// zeros without a gather, and a CTA whose rows all lie outside the output
-// support only writes zeros.
-__global__ void __launch_bounds__(256) spmm_tile_kernel(
-    const int *__restrict__ tile_row0, const int *__restrict__ tile_uptr,
-    const int *__restrict__ tile_u, const uint8_t *__restrict__ blk_u,
-    const int64_t *__restrict__ rp, const float *__restrict__ vals, const float *__restrict__ X,
-    int64_t ldx, float *__restrict__ Y, int64_t ldy, int ncols, const uint8_t *__restrict__ thop,
-    const uint16_t *__restrict__ tinv, int lim)
-{
-    extern __shared__ __align__(16) float4 xs[];   // [kTileCap][32]
-    const int tile = blockIdx.x, lane = threadIdx.x, warp = threadIdx.y;
-    const int c = blockIdx.y * 32 + lane;
-    const bool live = c < ncols;
-    const int I0 = tile_row0[tile], I1 = tile_row0[tile + 1];
-    int any = 0;
-    for (int I = I0 + warp; I < I1; I += 8) any |= row_live(thop, I >> 3, ncols, c, lim).act;
-    if (!__syncthreads_or(any)) {
-        if (live)
-            for (int I = I0 + warp; I < I1; I += 8)
-                reinterpret_cast<float4 *>(Y + (int64_t)c * ldy)[apos(tinv, ncols, c, I)] =
-                    make_float4(0.f, 0.f, 0.f, 0.f);
-        return;
-    }
-    const int u0 = tile_uptr[tile], nt = tile_uptr[tile + 1] - u0;
-    const float *x = X + (int64_t)(live ? c : 0) * ldx;
-    for (int u = warp; u < nt; u += 8) {
-        const int J = tile_u[u0 + u];
-        xs[u * 32 + lane] = row_live(thop, J >> 3, ncols, c, lim - 1).act
-                                ? __ldg(reinterpret_cast<const float4 *>(x) + apos(tinv, ncols, c, J))
-                                : make_float4(0.f, 0.f, 0.f, 0.f);
-    }
-    __syncthreads();
-    for (int I = I0 + warp; I < I1; I += 8) {
-        float acc[4] = {0.f, 0.f, 0.f, 0.f};
-        if (__any_sync(kFull, row_live(thop, I >> 3, ncols, c, lim).act)) {
-            const int64_t k1 = rp[I + 1];
-            for (int64_t k = rp[I]; k < k1; ++k) {
-                const float4 x4 = xs[(int)blk_u[k] * 32 + lane];
-                const float xv[4] = {x4.x, x4.y, x4.z, x4.w};
-                const float *B = vals + 32 * k;
-#pragma unroll
-                for (int a = 0; a < 4; ++a) {
-                    float h[4];
-                    load4(B + 4 * a, h);
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) acc[a] = fmaf(h[q], xv[q], acc[a]);
-                }
-            }
-        }
-        if (live) store4(Y + (int64_t)c * ldy + 4 * apos(tinv, ncols, c, I), acc);
-    }
-}
-
 // ------------------------------------------------------------------ MGS
 // One CTA of T threads (NW = T / 32 warps) per column; thread t owns the
 // values at positions p = t + v T (v < VPT) of the column's vectors, which are
@@ -397,7 +336,7 @@ constexpr int kGsBlock = 4;
 template <typename VT, int VPT, int T>
 struct MgsCfg {
     static constexpr bool kLo = sizeof(VT) == 4;                    // u as (hi, lo) pair
-    static constexpr bool kWs = VPT >= (sizeof(VT) == 4 ? 8 : 16);   // w in smem
+    static constexpr bool kWs = VPT >= (sizeof(VT) == 4 ? 8 : 4);    // w in smem
     static constexpr bool kUs = kLo || !kWs || 2 * VPT * T * sizeof(VT) <= 160 * 1024;
     static constexpr int kChunkDot = sizeof(VT) == 8 ? 1 : 2;      // values per batch of loads
     static constexpr int kChunkUpd = sizeof(VT) == 8 ? 2 : 4;
