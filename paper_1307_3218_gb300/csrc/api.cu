@@ -728,7 +728,7 @@ int marnoldi_solve(marnoldi_ctx *c, const int64_t *columns, int64_t ncols, int n
 
     // batch workspace
     const int64_t m_vec = regional ? 4 * (int64_t)region_atoms : c->m;
-    const ColumnShape shape = column_shape(m_vec);
+    const ColumnShape shape = column_shape(m_vec, c->prec);
     const size_t vs = c->prec == 0 ? 8 : 4;
     const size_t reg_per_col = regional ? (size_t)region_atoms * (12 + 8 * (size_t)c->rm.maxrow) : 0;
     const size_t per_col = al((size_t)2 * nu * shape.m_pad * vs) + (size_t)2 * shape.m_pad * vs +

@@ -35,14 +35,14 @@ constexpr int kMaxNu = 110;
 // Largest Krylov-vector length of global mode (one CTA holds a column's vector).
 constexpr int64_t kMaxGlobalM = 16384;
 
-// Threads per CTA and values per thread for a column-per-CTA kernel on vectors
-// of length m: T * VPT = m_pad >= m, T a multiple of 32, T <= 1024.
+// Threads per CTA and values per thread of the column-per-CTA kernels on
+// vectors of length m: m_pad = vpt * threads >= m, a multiple of 32.
 struct ColumnShape {
     int vpt;
     int threads;
     int64_t m_pad;
 };
-ColumnShape column_shape(int64_t m);
+ColumnShape column_shape(int64_t m, int prec);
 
 // ---------------------------------------------------------------- Krylov build
 // All pointers are device pointers.  Batch layout (c = batch column):

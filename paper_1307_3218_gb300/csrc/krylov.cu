@@ -36,10 +36,12 @@ const char *kernel_name(int kind)
 }
 
 // Vectors up to 4096 entries run 256-thread CTAs (several columns share an SM
-// and overlap each other's barriers); longer ones 1024-thread CTAs.  VPT is
-// the power of two that covers m.
-ColumnShape column_shape(int64_t m)
+// and overlap each other's reductions).  Longer FP32 vectors up to 8192
+// entries run 512-thread CTAs of 16 values per thread (two per SM); the rest
+// run 1024-thread CTAs.  VPT is the power of two that covers m.
+ColumnShape column_shape(int64_t m, int prec)
 {
+    if (prec == 1 && m > 4096 && m <= 8192) return ColumnShape{16, 512, 8192};
     const int T = m <= 4096 ? 256 : 1024;
     int v = 1;
     while (v < 16 && (int64_t)v * T < m) v *= 2;
@@ -83,6 +85,7 @@ template <> struct DotAcc<double> {
     }
     __device__ __forceinline__ double pack() const { return s; }
     __device__ __forceinline__ void unpack(double p) { s = p; }
+    __device__ __forceinline__ void set(double x) { s = x; }
 };
 template <> struct DotAcc<float> {
     float hi = 0.f, lo = 0.f;
@@ -115,6 +118,11 @@ template <> struct DotAcc<float> {
         u.d = p;
         hi = u.f.x;
         lo = u.f.y;
+    }
+    __device__ __forceinline__ void set(float x)
+    {
+        hi = x;
+        lo = 0.f;
     }
 };
 
@@ -325,6 +333,11 @@ __global__ void __launch_bounds__(256) spmm_hs_kernel(
 // FP64 scalar work; blocks cut the chains per step from 2 (n + 1) + 1 to
 // 2 ceil((n + 1) / kGsBlock) + 1.
 //
+// The first pass sums its projection coefficients S w_i . w per thread with
+// plain FMAs (the CTA reduction stays accurate): their rounding only leaves a
+// small component along w_i, which the second pass, whose sums are all
+// error-free, removes.  The h dots are error-free in both.
+//
 // w lives in registers for small VPT and in shared memory for large; u
 // (with its lo word in mixed precision) in shared memory when it fits, else
 // re-read from global memory (an L2 hit: the SpMM has just written it).  In
@@ -413,7 +426,7 @@ __device__ __forceinline__ void block_sum(DotAcc<VT> (&a)[N], double *part, int 
 }
 
 template <typename VT, int VPT, int T>
-__global__ void __launch_bounds__(T, T == 256 ? 4 : 1) mgs_kernel(
+__global__ void __launch_bounds__(T, T == 256 ? 4 : T == 512 ? 2 : 1) mgs_kernel(
     VT *__restrict__ K, VT *__restrict__ SK, const VT *__restrict__ U, const VT *__restrict__ Ulo,
     double *__restrict__ Hsub, double *__restrict__ scale, double *__restrict__ cn2,
     int *__restrict__ status, int *__restrict__ nu_eff, const int *__restrict__ tcnt, int n, int nu,
@@ -439,6 +452,7 @@ __global__ void __launch_bounds__(T, T == 256 ? 4 : 1) mgs_kernel(
     __shared__ int bc_stop;
     const int64_t base = (int64_t)c * nu * MP;
     int buf = 0;
+    auto live = [&](int cnt) { return live_values<T>(cnt, warp); };
 
     for (int i = tid; i < n; i += T) ssc[i] = scale[(int64_t)c * nu + i];
     for (int L = tid; L <= n + 1; L += T) cnt_s[L] = tcnt[(int64_t)c * (nu + 2) + L];
@@ -450,7 +464,7 @@ __global__ void __launch_bounds__(T, T == 256 ? 4 : 1) mgs_kernel(
         const VT *wn = K + base + (int64_t)n * MP + tid;
         const VT *swn = SK + base + (int64_t)n * MP + tid;
         DotAcc<VT> acc[1];
-        for_live<VPT, 2 * Cfg::kChunkDot>(live_values<T>(cnt_s[n], warp), [&](int v, bool a) {
+        for_live<VPT, 2 * Cfg::kChunkDot>(live(cnt_s[n]), [&](int v, bool a) {
             acc[0].add(a ? wn[v * T] : VT(0), a ? swn[v * T] : VT(0));
         });
         block_sum(acc, red, buf, [&](int, double beta2) {
@@ -476,7 +490,7 @@ __global__ void __launch_bounds__(T, T == 256 ? 4 : 1) mgs_kernel(
     const VT *ul = kLo ? Ulo + (int64_t)c * MP + tid : nullptr;
     VT wr[kWs ? 1 : VPT];
     {
-        const int nv = live_values<T>(cnt_s[n + 1], warp);
+        const int nv = live(cnt_s[n + 1]);
 #pragma unroll
         for (int v = 0; v < VPT; ++v) {
             const int p = tid + v * T;
@@ -512,15 +526,15 @@ __global__ void __launch_bounds__(T, T == 256 ? 4 : 1) mgs_kernel(
         int nvmax = 0;
 #pragma unroll
         for (int l = 0; l < kB; ++l) {
-            nvl[l] = l < nbk ? live_values<T>(cnt_s[i0 + l + 1], warp) : 0;
+            nvl[l] = l < nbk ? live(cnt_s[i0 + l + 1]) : 0;
             nvmax = max(nvmax, nvl[l]);
         }
         const VT *kb = K + base + (int64_t)i0 * MP + tid;
         const VT *skb = SK + base + (int64_t)i0 * MP + tid;
         DotAcc<VT> acc[2 * kB];   // [l]: c = S k . w, [kB + l]: h = k . u
-        VT hl[kB];
+        VT hl[kB], cp[kB];
 #pragma unroll
-        for (int l = 0; l < kB; ++l) hl[l] = VT(0);
+        for (int l = 0; l < kB; ++l) hl[l] = cp[l] = VT(0);
         for_live<VPT, Cfg::kChunkDot>(nvmax, [&](int v, bool a) {
             const int p = tid + v * T;
             VT uu;
@@ -532,12 +546,13 @@ __global__ void __launch_bounds__(T, T == 256 ? 4 : 1) mgs_kernel(
                 const VT kr = al ? kb[l * MP + v * T] : VT(0);
                 acc[kB + l].add(kr, uu);
                 if constexpr (kLo) hl[l] = fma(kr, uls[p], hl[l]);
-                if (need_w) acc[l].add(al ? skb[l * MP + v * T] : VT(0), wv);
+                if (need_w) cp[l] = fma(al ? skb[l * MP + v * T] : VT(0), wv, cp[l]);
             }
         });
-        if constexpr (kLo) {
 #pragma unroll
-            for (int l = 0; l < kB; ++l) acc[kB + l].add_lo(hl[l]);
+        for (int l = 0; l < kB; ++l) {
+            if constexpr (kLo) acc[kB + l].add_lo(hl[l]);
+            acc[l].set(cp[l]);
         }
         block_sum(acc, red, buf, [&](int q, double t) {
             const int l = q < kB ? q : q - kB, i = i0 + l;
@@ -571,7 +586,7 @@ __global__ void __launch_bounds__(T, T == 256 ? 4 : 1) mgs_kernel(
         int nvmax = 0;
 #pragma unroll
         for (int l = 0; l < kB; ++l) {
-            nvl[l] = l < nbk ? live_values<T>(cnt_s[i0 + l + 1], warp) : 0;
+            nvl[l] = l < nbk ? live(cnt_s[i0 + l + 1]) : 0;
             nvmax = max(nvmax, nvl[l]);
         }
         const VT *kb = K + base + (int64_t)i0 * MP + tid;
@@ -632,6 +647,11 @@ cudaError_t mgs_dispatch(const KrylovBatch &b, int n, int need_w, double tau, cu
 template <typename VT>
 cudaError_t mgs_shape(const KrylovBatch &b, int n, int need_w, double tau, cudaStream_t s)
 {
+    if (b.shape.threads == 512) {   // FP32, 16 values per thread
+        if constexpr (sizeof(VT) == 4)
+            if (b.shape.vpt == 16) return mgs_dispatch<VT, 16, 512>(b, n, need_w, tau, s);
+        return cudaErrorInvalidValue;
+    }
     if (b.shape.threads == 1024) {
         switch (b.shape.vpt) {
         case 1: return mgs_dispatch<VT, 1, 1024>(b, n, need_w, tau, s);
