@@ -25,6 +25,8 @@
 //                       P_j are written in ascending order of eps.
 #include "internal.h"
 
+#include <math_constants.h>
+
 #include <cfloat>
 
 namespace marnoldi {
@@ -321,11 +323,16 @@ __global__ void __launch_bounds__(kApplyThreads) eig_apply_kernel(
             }
         }
     }
-    // rank of every level (ties by index): ascending order
+    // rank of every level (ties by index): ascending order; a NaN level (from
+    // non-finite input) ranks as +inf, so the ranks always form a permutation
+    auto key = [&](int b) { const double x = d[b]; return x != x ? CUDART_INF : x; };
     for (int a = tid; a < n; a += T) {
-        const double da = d[a];
+        const double da = key(a);
         int rank = 0;
-        for (int b = 0; b < n; ++b) rank += (d[b] < da) || (d[b] == da && b < a);
+        for (int b = 0; b < n; ++b) {
+            const double db = key(b);
+            rank += (db < da) || (db == da && b < a);
+        }
         perm[rank] = a;
     }
     __syncthreads();

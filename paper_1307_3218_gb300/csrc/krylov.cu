@@ -351,8 +351,12 @@ struct MgsCfg {
     static constexpr bool kLo = sizeof(VT) == 4;                    // u as (hi, lo) pair
     static constexpr bool kWs = VPT >= (sizeof(VT) == 4 ? 8 : 4);    // w in smem
     static constexpr bool kUs = kLo || !kWs || 2 * VPT * T * sizeof(VT) <= 160 * 1024;
-    static constexpr int kChunkDot = sizeof(VT) == 8 ? 1 : 2;      // values per batch of loads
-    static constexpr int kChunkUpd = sizeof(VT) == 8 ? 2 : 4;
+    // values per batch of loads: pass-1 coefficients (8 streams), beta and
+    // pass-2 coefficients (2 or 4 streams), subtractions (4 streams); FP64
+    // is bound by its arithmetic and runs one value at a time
+    static constexpr int kChunkDot = sizeof(VT) == 8 ? 1 : 2;
+    static constexpr int kChunkSmall = sizeof(VT) == 8 ? 1 : 4;
+    static constexpr int kChunkUpd = sizeof(VT) == 8 ? 1 : 4;
     static constexpr int kSmemVectors = (kUs ? 1 : 0) + (kLo ? 1 : 0) + (kWs ? 1 : 0);
 };
 
@@ -464,7 +468,7 @@ __global__ void __launch_bounds__(T, T == 256 ? 4 : T == 512 ? 2 : 1) mgs_kernel
         const VT *wn = K + base + (int64_t)n * MP + tid;
         const VT *swn = SK + base + (int64_t)n * MP + tid;
         DotAcc<VT> acc[1];
-        for_live<VPT, 2 * Cfg::kChunkDot>(live(cnt_s[n]), [&](int v, bool a) {
+        for_live<VPT, Cfg::kChunkSmall>(live(cnt_s[n]), [&](int v, bool a) {
             acc[0].add(a ? wn[v * T] : VT(0), a ? swn[v * T] : VT(0));
         });
         block_sum(acc, red, buf, [&](int, double beta2) {
@@ -592,7 +596,7 @@ __global__ void __launch_bounds__(T, T == 256 ? 4 : T == 512 ? 2 : 1) mgs_kernel
         const VT *kb = K + base + (int64_t)i0 * MP + tid;
         const VT *skb = SK + base + (int64_t)i0 * MP + tid;
         DotAcc<VT> acc[kB];
-        for_live<VPT, 2 * Cfg::kChunkDot>(nvmax, [&](int v, bool a) {
+        for_live<VPT, Cfg::kChunkSmall>(nvmax, [&](int v, bool a) {
             const VT wv = wget(v);
 #pragma unroll
             for (int l = 0; l < kB; ++l)
