@@ -40,8 +40,10 @@ UNIT = "columns/s"
 L2_FLUSH_BYTES = 256 << 20
 FP64_PEAK_NOTE = "152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz (nominal 1.25 TFLOP/s FP64)"
 # (dram__bytes_read + dram__bytes_write) / algorithmic bytes of one captured MGS
-# launch, by precision; empty until the current kernel has been captured.
-MGS_DRAM_PER_ALGORITHMIC: dict = {}
+# launch (ncu --set full, mixed precision, 608 columns, step n = 20):
+# (2.624361e9 + 0.034059e9) / (2.572095e9 read + 0.039846e9 written over the supports).
+# Must be re-measured (or removed) whenever the MGS kernel changes.
+MGS_DRAM_PER_ALGORITHMIC = {"mixed": 1.0178}
 
 
 def parse():
