@@ -149,6 +149,24 @@ int marnoldi_density_device(marnoldi_ctx *ctx, double *rho_vals_device, double *
 int marnoldi_energy(marnoldi_ctx *ctx, double *band_energy, double *mu, double *electron_count_out);
 
 /*
+ * Fermi level of a column set shared by several contexts (arXiv:1307.3218,
+ * Section 2: the density is a sum over the columns of all atoms; columns split
+ * across contexts or GPUs share one mu).  After marnoldi_solve:
+ *   marnoldi_level_range  smallest and largest subspace level of the solved
+ *                         columns (host outputs), for the bisection bracket.
+ *   marnoldi_fermi_at     N(mu) = sum_j sum_a 2 f((eps_a - mu) / kT) w_a and
+ *                         E(mu) = sum_j sum_a 2 f eps_a w_a over this context's
+ *                         solved columns, computed on the GPU (outputs may be
+ *                         NULL), and makes mu, kT the context's Fermi level for
+ *                         marnoldi_density, marnoldi_energy and marnoldi_green.
+ * A caller that splits the columns sums N(mu) over the contexts at every
+ * bisection step.  Errors: MARNOLDI_EINVAL (null outputs of level_range,
+ * kT <= 0 or a non-finite mu), MARNOLDI_ESTATE (no successful solve).
+ */
+int marnoldi_level_range(marnoldi_ctx *ctx, double *eps_min, double *eps_max);
+int marnoldi_fermi_at(marnoldi_ctx *ctx, double mu, double kT, double *N, double *E);
+
+/*
  * Green's-function values G(z) e_j = K V diag(1 / (z - eps)) V^T q on H's
  * pattern (the solution x of (z S - H) x = e_j inside L_nu^(j); Eq. 1 of
  * arXiv:1307.3218) for nz complex shifts z = z_re_im[2i] + i z_re_im[2i+1].

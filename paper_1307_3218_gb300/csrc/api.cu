@@ -955,6 +955,38 @@ int marnoldi_energy(marnoldi_ctx *c, double *band_energy, double *mu, double *el
     return MARNOLDI_OK;
 }
 
+int marnoldi_level_range(marnoldi_ctx *c, double *eps_min, double *eps_max)
+{
+    if (!c || !eps_min || !eps_max) return MARNOLDI_EINVAL;
+    if (!c->solved) return fail(c, MARNOLDI_ESTATE, "level range requested before a successful solve");
+    int rc = launch(c, KK_MINMAX, [&] {
+        return launch_minmax(c->st, c->d_partial, c->d_ticket, c->d_out, c->stream);
+    });
+    if (rc) return rc;
+    cudaError_t e = cudaMemcpyAsync(c->h_out, c->d_out, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+    if (e != cudaSuccess) return fail_cuda(c, e, "minmax read-back");
+    if ((rc = sync(c, "minmax"))) return rc;
+    *eps_min = c->h_out[0];
+    *eps_max = c->h_out[1];
+    return MARNOLDI_OK;
+}
+
+int marnoldi_fermi_at(marnoldi_ctx *c, double mu, double kT, double *N, double *E)
+{
+    if (!c || !(kT > 0.0) || !std::isfinite(mu) || !std::isfinite(kT)) return MARNOLDI_EINVAL;
+    if (!c->solved) return fail(c, MARNOLDI_ESTATE, "Fermi level set before a successful solve");
+    double n = 0.0, en = 0.0;
+    const int rc = count_at(c, mu, kT, &n, &en);
+    if (rc) return rc;
+    c->mu = mu;
+    c->kT = kT;
+    c->N = n;
+    c->E = en;
+    if (N) *N = n;
+    if (E) *E = en;
+    return MARNOLDI_OK;
+}
+
 int marnoldi_green(marnoldi_ctx *c, const double *z, int nz, double *G)
 {
     if (!c || (nz > 0 && (!z || !G)) || nz < 0) return MARNOLDI_EINVAL;

@@ -333,11 +333,6 @@ __global__ void __launch_bounds__(256) spmm_hs_kernel(
 // FP64 scalar work; blocks cut the chains per step from 2 (n + 1) + 1 to
 // 2 ceil((n + 1) / kGsBlock) + 1.
 //
-// The first pass sums its projection coefficients S w_i . w per thread with
-// plain FMAs (the CTA reduction stays accurate): their rounding only leaves a
-// small component along w_i, which the second pass, whose sums are all
-// error-free, removes.  The h dots are error-free in both.
-//
 // w lives in registers for small VPT and in shared memory for large; u
 // (with its lo word in mixed precision) in shared memory when it fits, else
 // re-read from global memory (an L2 hit: the SpMM has just written it).  In
@@ -536,9 +531,9 @@ __global__ void __launch_bounds__(T, T == 256 ? 4 : T == 512 ? 2 : 1) mgs_kernel
         const VT *kb = K + base + (int64_t)i0 * MP + tid;
         const VT *skb = SK + base + (int64_t)i0 * MP + tid;
         DotAcc<VT> acc[2 * kB];   // [l]: c = S k . w, [kB + l]: h = k . u
-        VT hl[kB], cp[kB];
+        VT hl[kB];
 #pragma unroll
-        for (int l = 0; l < kB; ++l) hl[l] = cp[l] = VT(0);
+        for (int l = 0; l < kB; ++l) hl[l] = VT(0);
         for_live<VPT, Cfg::kChunkDot>(nvmax, [&](int v, bool a) {
             const int p = tid + v * T;
             VT uu;
@@ -550,13 +545,12 @@ __global__ void __launch_bounds__(T, T == 256 ? 4 : T == 512 ? 2 : 1) mgs_kernel
                 const VT kr = al ? kb[l * MP + v * T] : VT(0);
                 acc[kB + l].add(kr, uu);
                 if constexpr (kLo) hl[l] = fma(kr, uls[p], hl[l]);
-                if (need_w) cp[l] = fma(al ? skb[l * MP + v * T] : VT(0), wv, cp[l]);
+                if (need_w) acc[l].add(al ? skb[l * MP + v * T] : VT(0), wv);
             }
         });
 #pragma unroll
         for (int l = 0; l < kB; ++l) {
             if constexpr (kLo) acc[kB + l].add_lo(hl[l]);
-            acc[l].set(cp[l]);
         }
         block_sum(acc, red, buf, [&](int q, double t) {
             const int l = q < kB ? q : q - kB, i = i0 + l;

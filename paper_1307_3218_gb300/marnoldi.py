@@ -76,6 +76,8 @@ def load(path: str | None = None):
         "marnoldi_density": (i32, [P, P, P]),
         "marnoldi_density_device": (i32, [P, P, P]),
         "marnoldi_energy": (i32, [P, P, P, P]),
+        "marnoldi_level_range": (i32, [P, P, P]),
+        "marnoldi_fermi_at": (i32, [P, d, d, P, P]),
         "marnoldi_green": (i32, [P, P, i32, P]),
         "marnoldi_column_stats": (i32, [P, P, P, P]),
         "marnoldi_solved_shape": (i32, [P, P, P]),
@@ -273,6 +275,18 @@ def marnoldi_energy(ctx: Context) -> tuple[float, float, float]:
     E, mu, N = C.c_double(), C.c_double(), C.c_double()
     _check(load().marnoldi_energy(ctx.handle, C.byref(E), C.byref(mu), C.byref(N)), ctx)
     return E.value, mu.value, N.value
+
+
+def marnoldi_level_range(ctx: Context) -> tuple[float, float]:
+    lo, hi = C.c_double(), C.c_double()
+    _check(load().marnoldi_level_range(ctx.handle, C.byref(lo), C.byref(hi)), ctx)
+    return lo.value, hi.value
+
+
+def marnoldi_fermi_at(ctx: Context, mu: float, kT: float) -> tuple[float, float]:
+    N, E = C.c_double(), C.c_double()
+    _check(load().marnoldi_fermi_at(ctx.handle, float(mu), float(kT), C.byref(N), C.byref(E)), ctx)
+    return N.value, E.value
 
 
 def marnoldi_green(ctx: Context, zs) -> np.ndarray:
