@@ -106,7 +106,7 @@ int marnoldi_setup(marnoldi_ctx **out, int64_t n_block_rows, const int64_t *row_
  *   columns, ncols  orbital indices to solve (host int64); columns == NULL and
  *                   ncols < 0 select every real orbital.  Duplicates and
  *                   padding orbitals are rejected (MARNOLDI_EINVAL).
- *   nu              subspace dimension, 1 <= nu <= min(M_real, 110); in regional
+ *   nu              subspace dimension, 1 <= nu <= min(M_real, 320); in regional
  *                   mode also nu <= 4 * region_atoms.
  *   region_atoms    0 = global mode (Krylov vectors over all M orbitals, M <= 16384).
  *                   N_reg > 0 = regional mode: column j of atom J is solved on the

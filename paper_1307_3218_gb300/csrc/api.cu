@@ -764,16 +764,21 @@ int marnoldi_solve(marnoldi_ctx *c, const int64_t *columns, int64_t ncols, int n
     es.nr_max = 4 * c->maxrow + 2;
     es.rcap = (int64_t)8 * nu * nu;
     es.scap = (int64_t)40 * nu;
-    const size_t per_sub = al((size_t)(2 + es.nr_max) * nu * 8) + al((size_t)es.rcap * 16) +
-                           al((size_t)es.scap * 8) + 8;
-    es.chunk = (int)std::max<int64_t>(32, std::min<int64_t>(B, (int64_t)(((size_t)3 << 30) / per_sub)));
-    if (eig_smem_bytes(nu, es.nr_max) > (size_t)227 * 1024)
+    // H_sub in shared memory when it fits, else in a global scratch per subspace
+    const size_t kSmemCap = (size_t)227 * 1024;
+    const bool a_global = eig_smem_bytes(nu, es.nr_max, false) > kSmemCap;
+    if (eig_smem_bytes(nu, es.nr_max, a_global) > kSmemCap)
         return fail(c, MARNOLDI_EINVAL, "nu = %d with %d blocks per row exceeds the eigensolver's shared memory",
                     nu, c->maxrow);
+    const size_t a_per_sub = a_global ? (size_t)nu * (nu | 1) * 8 : 0;
+    const size_t per_sub = al((size_t)(2 + es.nr_max) * nu * 8) + al((size_t)es.rcap * 16) +
+                           al((size_t)es.scap * 8) + 8 + a_per_sub;
+    es.chunk = (int)std::max<int64_t>(32, std::min<int64_t>(B, (int64_t)(((size_t)3 << 30) / per_sub)));
     const size_t ceig = (size_t)es.chunk;
     const size_t oED = oEg, oEE = oED + al(ceig * nu * 8), oERQ = oEE + al(ceig * nu * 8),
                  oERot = oERQ + al(ceig * es.nr_max * nu * 8), oESw = oERot + al(ceig * es.rcap * 16),
-                 oENs = oESw + al(ceig * es.scap * 8), wtot = oENs + al(ceig * 4);
+                 oENs = oESw + al(ceig * es.scap * 8), oEA = oENs + al(ceig * 4),
+                 wtot = oEA + al(ceig * a_per_sub);
     if (c->ws_bytes < wtot) {
         if (c->ws) dfree(c, c->ws, c->ws_bytes);
         c->ws = dalloc(c, wtot);
@@ -809,6 +814,7 @@ int marnoldi_solve(marnoldi_ctx *c, const int64_t *columns, int64_t ncols, int n
     es.rot = (double2 *)(wb + oERot);
     es.sweep = (int2 *)(wb + oESw);
     es.nsweep = (int *)(wb + oENs);
+    es.Ag = a_global ? (double *)(wb + oEA) : nullptr;
     RegionMaps *rmp = nullptr;
     if (regional) {
         c->rm.reg = (int *)(wb + oRg);

@@ -27,6 +27,7 @@
 
 #include <math_constants.h>
 
+#include <algorithm>
 #include <cfloat>
 
 namespace marnoldi {
@@ -44,21 +45,14 @@ __device__ __forceinline__ double warp_sum(double s)
     return s;
 }
 
-// Position of a in the ascending list R[0..n), or -1.
-__device__ __forceinline__ int find_sorted(const int *__restrict__ R, int n, int a)
-{
-    int lo = 0, hi = n;
-    while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        if (R[mid] < a) lo = mid + 1; else hi = mid;
-    }
-    return (lo < n && R[lo] == a) ? lo : -1;
-}
 
 // ------------------------------------------------------------------ tridiagonalisation
 // A = Q T Q^T with Q = P_0 P_1 ... P_{n-3}; R <- R P_0 P_1 ... (R Q).
 // Shared memory: A [n][lda], R [nr_max][lda] (lda = nu | 1, odd, so that the
-// per-thread row walks of R spread over the banks), v, e, scalars.
+// per-thread row walks of R spread over the banks), v, e, scalars.  When A
+// does not fit (nu above about 110), it lives in a global scratch of
+// nu x lda doubles per subspace (Ag), which the CTA's sweeps keep in L2
+// (720 KB at nu = 300), and shared memory holds R and the vectors only.
 template <typename VT>
 __global__ void __launch_bounds__(kTriThreads) eig_tridiag_kernel(
     const double *__restrict__ Hsub, const int *__restrict__ bnu_eff,
@@ -66,7 +60,8 @@ __global__ void __launch_bounds__(kTriThreads) eig_tridiag_kernel(
     const uint16_t *__restrict__ tinv, int nb, int nu,
     const int64_t *__restrict__ bcols, const int64_t *__restrict__ rp,
     const int32_t *__restrict__ ci, const int *__restrict__ reg, int n_reg, int cofs,
-    double *__restrict__ D, double *__restrict__ E, double *__restrict__ RQ, int nr_max)
+    double *__restrict__ D, double *__restrict__ E, double *__restrict__ RQ, int nr_max,
+    double *__restrict__ Ag)
 {
     const int sc = blockIdx.x;
     const int c = cofs + sc;
@@ -74,8 +69,8 @@ __global__ void __launch_bounds__(kTriThreads) eig_tridiag_kernel(
     const int tid = threadIdx.x, T = blockDim.x;
     const int lda = nu | 1;
     extern __shared__ __align__(16) double sm[];
-    double *A = sm;
-    double *R = A + (size_t)nu * lda;
+    double *A = Ag ? Ag + (size_t)sc * nu * lda : sm;
+    double *R = Ag ? sm : A + (size_t)nu * lda;
     double *v = R + (size_t)nr_max * lda;
     double *ev = v + nu;
     __shared__ double sc4[4];
@@ -147,16 +142,19 @@ __global__ void __launch_bounds__(kTriThreads) eig_tridiag_kernel(
         const double tauh = sc4[0];
         for (int l = tid; l < L; l += T) v[l] = (l == 0) ? sc4[1] : A[(k + 1 + l) * lda + k];
         __syncthreads();
-        // p = tau A_sub v, one column per thread (A_sub symmetric; consecutive
-        // threads read consecutive addresses)
-        double pl = 0.0;
-        if (tid < L) {
-            for (int m = 0; m < L; ++m) pl = fma(A[(k + 1 + m) * lda + (k + 1 + tid)], v[m], pl);
+        // p = tau A_sub v, columns over the threads (A_sub symmetric; consecutive
+        // threads read consecutive addresses); p goes to the scratch after e
+        double *qv = ev + nu;
+        double vp = 0.0;
+        for (int col = tid; col < L; col += T) {
+            double pl = 0.0;
+            for (int m = 0; m < L; ++m) pl = fma(A[(k + 1 + m) * lda + (k + 1 + col)], v[m], pl);
             pl *= tauh;
+            qv[col] = pl;
+            vp = fma(v[col], pl, vp);
         }
         // K = (tau/2) v . p
         __shared__ double wpart[kTriThreads / 32];
-        double vp = tid < L ? v[tid] * pl : 0.0;
         vp = warp_sum(vp);
         if ((tid & 31) == 0) wpart[tid >> 5] = vp;
         __syncthreads();
@@ -166,8 +164,7 @@ __global__ void __launch_bounds__(kTriThreads) eig_tridiag_kernel(
             sc4[2] = 0.5 * tauh * s;
         }
         __syncthreads();
-        double *qv = ev + nu;   // q = p - K v, in the scratch after e
-        if (tid < L) qv[tid] = fma(-sc4[2], v[tid], pl);
+        for (int col = tid; col < L; col += T) qv[col] = fma(-sc4[2], v[col], qv[col]);   // q = p - K v
         __syncthreads();
         for (int idx = tid; idx < L * L; idx += T) {  // A_sub -= v q^T + q v^T
             const int a = idx / L, b = idx - (idx / L) * L;
@@ -364,8 +361,8 @@ template <typename VT>
 cudaError_t tridiag_dispatch(const DeviceMatrix &A, const KrylovBatch &b, const RegionMaps *rm,
                              const EigScratch &es, int cofs, int nb2, cudaStream_t s)
 {
-    const int nu = b.nu, lda = nu | 1;
-    const size_t smem = ((size_t)(nu + es.nr_max) * lda + 3 * (size_t)nu) * sizeof(double);
+    const int nu = b.nu;
+    const size_t smem = eig_tridiag_smem(nu, es.nr_max, es.Ag != nullptr);
     static size_t configured = 0;
     if (smem > configured) {
         cudaError_t e = cudaFuncSetAttribute(eig_tridiag_kernel<VT>,
@@ -375,18 +372,25 @@ cudaError_t tridiag_dispatch(const DeviceMatrix &A, const KrylovBatch &b, const 
     }
     eig_tridiag_kernel<VT><<<nb2, kTriThreads, smem, s>>>(
         b.Hsub, b.nu_eff, b.scale, (const VT *)b.K, b.shape.m_pad, b.tinv, b.nb, nu, b.cols, A.rp, A.ci,
-        rm ? rm->reg : nullptr, rm ? rm->n_reg : 0, cofs, es.D, es.E, es.RQ, es.nr_max);
+        rm ? rm->reg : nullptr, rm ? rm->n_reg : 0, cofs, es.D, es.E, es.RQ, es.nr_max, es.Ag);
     return cudaGetLastError();
 }
 
 }  // namespace
 
-size_t eig_smem_bytes(int nu, int nr_max)
+size_t eig_tridiag_smem(int nu, int nr_max, bool a_global)
 {
     const size_t lda = (size_t)(nu | 1);
-    const size_t tri = ((size_t)(nu + nr_max) * lda + 3 * (size_t)nu) * sizeof(double);
+    return ((size_t)((a_global ? 0 : nu) + nr_max) * lda + 3 * (size_t)nu) * sizeof(double);
+}
+
+size_t eig_smem_bytes(int nu, int nr_max, bool a_global)
+{
+    const size_t lda = (size_t)(nu | 1);
+    const size_t tri = eig_tridiag_smem(nu, nr_max, a_global);
     const size_t app = (size_t)nr_max * lda * sizeof(double) + (size_t)nu * (sizeof(double) + sizeof(int));
-    return tri > app ? tri : app;
+    const size_t ql = (size_t)2 * nu * 32 * sizeof(double);
+    return std::max(tri, std::max(app, ql));
 }
 
 cudaError_t launch_eig(const DeviceMatrix &A, const KrylovBatch &b, const ColumnState &st,

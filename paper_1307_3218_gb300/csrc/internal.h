@@ -30,8 +30,9 @@ const char *kernel_name(int kind);
 // Record the message that marnoldi_last_error(NULL) returns; returns `code`.
 int set_global_error(int code, const char *msg);
 
-// Largest subspace dimension of the shared-memory eigensolver.
-constexpr int kMaxNu = 110;
+// Largest subspace dimension.  Up to about 110 the subspace matrix of the
+// eigensolve sits in shared memory, above that in a global scratch.
+constexpr int kMaxNu = 320;
 // Largest Krylov-vector length of global mode (one CTA holds a column's vector).
 constexpr int64_t kMaxGlobalM = 16384;
 
@@ -174,9 +175,12 @@ struct EigScratch {
     double2 *rot = nullptr;
     int2 *sweep = nullptr;
     int *nsweep = nullptr;
+    double *Ag = nullptr;   // chunk x nu x (nu | 1) doubles when H_sub does not fit in shared memory
 };
-// Largest dynamic shared memory the eigensolve kernels need.
-size_t eig_smem_bytes(int nu, int nr_max);
+// Dynamic shared memory of the tridiagonalisation and the largest one of the
+// eigensolve kernels, with H_sub in shared (a_global = false) or global memory.
+size_t eig_tridiag_smem(int nu, int nr_max, bool a_global);
+size_t eig_smem_bytes(int nu, int nr_max, bool a_global);
 
 cudaError_t launch_eig(const DeviceMatrix &A, const KrylovBatch &b, const ColumnState &st,
                        int64_t col0, const RegionMaps *rm /* null in global mode */,

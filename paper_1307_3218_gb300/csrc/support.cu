@@ -27,11 +27,11 @@ __global__ void __launch_bounds__(256) support_kernel(
     const int64_t *__restrict__ rp, const int32_t *__restrict__ ci, int nbr,
     const int *__restrict__ reg, int n_reg, int maxrow, const int *__restrict__ lcnt,
     const int *__restrict__ lci, const int64_t *__restrict__ cols, int nb, int ntile, int maxlev,
-    uint8_t *__restrict__ thop, uint16_t *__restrict__ tinv, int *__restrict__ tcnt)
+    int nlev, uint8_t *__restrict__ thop, uint16_t *__restrict__ tinv, int *__restrict__ tcnt)
 {
     extern __shared__ uint8_t dist[];   // per atom (global or local index)
     __shared__ uint8_t th[kMaxTiles];
-    __shared__ int start[kMaxNu + 3];
+    __shared__ int start[256];
     const int c = blockIdx.x, tid = threadIdx.x;
     const int na = kRegional ? n_reg : nbr;
     const int Jg = (int)(cols[c] >> 2);
@@ -77,8 +77,10 @@ __global__ void __launch_bounds__(256) support_kernel(
             const int n = start[L];
             start[L] = run;
             run += n;
-            tcnt[(int64_t)c * (maxlev + 1) + L] = run;
+            tcnt[(int64_t)c * (nlev + 1) + L] = run;
         }
+        for (int L = maxlev + 1; L <= nlev; ++L)   // past the search depth: every tile
+            tcnt[(int64_t)c * (nlev + 1) + L] = ntile;
         int tail = run;
         for (int t = 0; t < ntile; ++t) {
             const int h = th[t];
@@ -92,19 +94,20 @@ __global__ void __launch_bounds__(256) support_kernel(
 cudaError_t launch_support(const DeviceMatrix &A, const RegionMaps *rm, const KrylovBatch &b,
                            cudaStream_t s)
 {
-    const int maxlev = b.nu + 1;
-    if (b.ntile > kMaxTiles || b.ntile * 32 != b.shape.m_pad || maxlev > 254)
-        return cudaErrorInvalidValue;
+    // hop counts up to nu + 1 matter; a uint8 holds up to 254 of them (255 =
+    // farther), and a tile beyond 254 hops is live for every level from 255 on
+    const int nlev = b.nu + 1, maxlev = nlev < 254 ? nlev : 254;
+    if (b.ntile > kMaxTiles || b.ntile * 32 != b.shape.m_pad) return cudaErrorInvalidValue;
     if (rm) {
         if (rm->n_reg > kMaxRegion) return cudaErrorInvalidValue;
         support_kernel<true><<<b.nb, 256, rm->n_reg, s>>>(
             A.rp, A.ci, (int)A.nbr, rm->reg, rm->n_reg, rm->maxrow, rm->lcnt, rm->lci, b.cols, b.nb,
-            b.ntile, maxlev, b.thop, b.tinv, b.tcnt);
+            b.ntile, maxlev, nlev, b.thop, b.tinv, b.tcnt);
     } else {
         if (A.nbr > kMaxGlobalM / 4) return cudaErrorInvalidValue;
         support_kernel<false><<<b.nb, 256, (size_t)A.nbr, s>>>(
             A.rp, A.ci, (int)A.nbr, nullptr, 0, 0, nullptr, nullptr, b.cols, b.nb, b.ntile, maxlev,
-            b.thop, b.tinv, b.tcnt);
+            nlev, b.thop, b.tinv, b.tcnt);
     }
     return cudaGetLastError();
 }

@@ -183,7 +183,7 @@ def test_errors(m, c1):
         m.marnoldi_density(ctx)
     assert ei.value.code == m.marnoldi.MARNOLDI_ESTATE
     with pytest.raises(m.MarnoldiError) as ei:
-        m.marnoldi_solve(ctx, None, 200, 0, c1.n_electrons, KT)
+        m.marnoldi_solve(ctx, None, 300, 0, c1.n_electrons, KT)      # nu > M_real
     assert ei.value.code == m.marnoldi.MARNOLDI_EINVAL
     with pytest.raises(m.MarnoldiError) as ei:
         m.marnoldi_solve(ctx, None, 30, 65, c1.n_electrons, KT)     # region larger than the system
@@ -200,6 +200,47 @@ def test_errors(m, c1):
     with pytest.raises(m.MarnoldiError) as ei:
         m.marnoldi_energy(ctx)
     assert ei.value.code == m.marnoldi.MARNOLDI_ESTATE
+
+
+# ----------------------------------------------------------------- large nu
+# Above nu of about 110 the subspace matrix no longer fits in shared memory and
+# the tridiagonalisation runs on a global copy; the observables are compared
+# (at large nu the Krylov vectors themselves are sensitive at rounding level).
+
+def assert_observables_fp64(g, ref):
+    assert g["N"] == pytest.approx(ref.N, rel=FP64_REL)
+    assert g["E"] == pytest.approx(ref.E_band, rel=FP64_REL)
+    mask = ~np.isnan(ref.rho)
+    assert np.abs(g["rho"][mask] - ref.rho[mask]).max() <= FP64_REL * np.abs(ref.rho[mask]).max()
+    assert np.abs(g["rhoE"][mask] - ref.rhoE[mask]).max() <= FP64_REL * np.abs(ref.rhoE[mask]).max()
+
+
+@pytest.mark.parametrize("nu", [128, 200, 256])
+def test_c1_large_nu_fp64(m, c1, nu):
+    g = gpu_solve(m, c1, nu)
+    ref = oracle.solve(c1, nu=nu, kT=KT, mu_fixed=g["mu"])
+    assert_observables_fp64(g, ref)
+
+
+def test_c1_large_nu_mixed(m, c1):
+    g = gpu_solve(m, c1, 200, prec=1)
+    ref = oracle.solve(c1, nu=200, kT=KT, mu_fixed=g["mu"])
+    e = mixed_errors(g, ref, c1)
+    print("C1 nu=200 mixed:", e)
+    assert e["drho"] <= 1e-5 and e["drhoE"] <= 1e-4 and e["dE_per_atom"] <= 1e-6
+
+
+def test_nu300_sampled(m):
+    from tbsynth import amorphous_system
+    t = amorphous_system(100, seed=3)
+    g = gpu_solve(m, t, 300)
+    rng = np.random.default_rng(5)
+    sample = np.sort(rng.choice(t.M, size=32, replace=False))
+    ref = oracle.solve(t, nu=300, kT=KT, mu_fixed=g["mu"], cols=sample)
+    mask = ~np.isnan(ref.rho)
+    assert np.abs(g["rho"][mask] - ref.rho[mask]).max() <= FP64_REL * np.abs(ref.rho[mask]).max()
+    assert np.abs(g["rhoE"][mask] - ref.rhoE[mask]).max() <= FP64_REL * np.abs(ref.rhoE[mask]).max()
+    assert g["N"] == pytest.approx(t.n_electrons, rel=1e-12)
 
 
 # ----------------------------------------------------------------- mixed precision
