@@ -39,11 +39,9 @@ METRIC = "mArnoldi columns/s"
 UNIT = "columns/s"
 L2_FLUSH_BYTES = 256 << 20
 FP64_PEAK_NOTE = "152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz (nominal 1.25 TFLOP/s FP64)"
-# (dram__bytes_read + dram__bytes_write) / algorithmic bytes of one captured MGS
-# launch (ncu --set full, mixed precision, 608 columns, step n = 20):
-# (2.624361e9 + 0.034059e9) / (2.572095e9 read + 0.039846e9 written over the supports).
-# Must be re-measured (or removed) whenever the MGS kernel changes.
-MGS_DRAM_PER_ALGORITHMIC: dict = {}
+# (dram__bytes_read + dram__bytes_write) / algorithmic bytes of one captured
+# Gram-Schmidt launch, by precision; empty until the current kernel is captured.
+GS_DRAM_PER_ALGORITHMIC: dict = {}
 
 
 def parse():
@@ -147,20 +145,20 @@ class Clocks:
                 "power_w_max": max(r[2] for r in rows), "samples": len(rows), "reasons": reasons}
 
 
-def mgs_algorithmic(nu: int, m: int, vbytes: int, ncols: int):
-    """Bytes the Gram-Schmidt step must stream and FP64 flops it must do.
+def gs_algorithmic(nu: int, m: int, vbytes: int, ncols: int):
+    """Bytes the Gram-Schmidt step must stream and FP64 flops it must do (dense vectors).
 
-    Step n (0-based) reads w_n and S w_n for beta_n = ||w_n||_S (n >= 1) and u;
-    for n < nu-1 it reads, in each of the two passes, the n+1 stored vectors
-    w_i and S w_i, and writes the new w: (4 (n+1) + 2 + 2 [n >= 1]) m values.
-    The last step forms h_{i,nu-1} = k_i . u only: (nu + 1 + 2) m values.
-    Flops: beta one dot; pass 1 two dots and one update, pass 2 one dot and one
-    update per entry and stored vector; the last step beta and one dot.
+    Step n (0-based) loads u (and its lo word in mixed precision) and w_n, reads
+    w_i and S w_i of every stored vector i <= n once for the coefficients
+    (a_i = w_i . u, b_i = S w_i . u, g_i = S w_i . w_n) and, for n < nu-1, w_i once
+    more for the subtraction, and writes the new w.  Flops: three dots per entry
+    and stored vector and one update (the last step: two dots).
     """
-    vals = sum(4 * (n + 1) + 2 + (2 if n >= 1 else 0) for n in range(nu - 1)) + (nu + 1 + 2)
-    if vbytes == 4:
-        vals += nu   # mixed precision also reads the lo word of u = H w_n once per step
-    fmas = sum(5 * (n + 1) + (1 if n >= 1 else 0) for n in range(nu - 1)) + nu + 1
+    vals = fmas = 0
+    for n in range(nu):
+        need_w = n + 1 < nu
+        vals += (2 if vbytes == 4 else 1) + 1 + 2 * (n + 1) + ((n + 1) + 1 if need_w else 0)
+        fmas += (4 if need_w else 2) * (n + 1)
     return vals * m * vbytes * ncols, 2.0 * fmas * m * ncols
 
 
@@ -197,27 +195,23 @@ def support_counts(t, cols, nu: int, m_pad: int):
     return out[inv]
 
 
-def mgs_algorithmic_support(nu: int, tcnt, vbytes: int):
+def gs_algorithmic_support(nu: int, tcnt, vbytes: int):
     """Bytes and FP64 flops of the Gram-Schmidt steps over the basis vectors' supports.
 
-    As mgs_algorithmic, but every vector counts only the entries of its support
-    tiles (32 entries per tile): w_n and S w_n for beta_n over the tiles within
-    n hops, u (and its lo word in mixed precision) and the new w within n + 1,
-    the pair w_i, S w_i of each pass within i + 1.
+    As gs_algorithmic, but every vector counts only the entries of its support
+    tiles (32 entries per tile): u (and its lo word) and the new w within n + 1
+    hops, w_n within n, the pair w_i, S w_i and the subtraction's w_i within
+    i + 1.
     """
     E = 32.0 * np.asarray(tcnt).sum(axis=0)   # entries within L hops, summed over columns
     vals = fmas = 0.0
     for n in range(nu):
         need_w = n + 1 < nu
         s = sum(E[i + 1] for i in range(n + 1))
-        if n >= 1:
-            vals += 2 * E[n]
-            fmas += E[n]
-        vals += (2 if vbytes == 4 else 1) * E[n + 1]
-        vals += (2 if need_w else 1) * s
-        fmas += (3 if need_w else 1) * s
+        vals += (2 if vbytes == 4 else 1) * E[n + 1] + E[n] + 2 * s
+        fmas += 2 * s
         if need_w:
-            vals += 2 * s + E[n + 1]
+            vals += s + E[n + 1]
             fmas += 2 * s
     return vals * vbytes, 2.0 * fmas
 
@@ -406,9 +400,9 @@ def main():
     nlaunch, dom_ms = stats[dom]
     steps = args.steps
     tcnt = None if args.region else support_counts(t, cols, args.nu, column_m_pad(m_vec))
-    if dom == "mgs":
-        by, fl = (mgs_algorithmic_support(args.nu, tcnt, vb) if tcnt is not None
-                  else mgs_algorithmic(args.nu, m_vec, vb, ncols))
+    if dom == "gs":
+        by, fl = (gs_algorithmic_support(args.nu, tcnt, vb) if tcnt is not None
+                  else gs_algorithmic(args.nu, m_vec, vb, ncols))
     elif dom in ("spmm_H", "spmm_S", "spmm_HS"):
         by, fl = spmm_algorithmic(args.nu, m_vec, t.nnzb, t.n_block_rows, vb, ncols)
         if dom != "spmm_HS":
@@ -428,13 +422,13 @@ def main():
         # DRAM bytes per average launch: the ncu capture's DRAM/algorithmic ratio for
         # this kernel (a smaller case of the same kernel; bytes scale with columns and
         # stored vectors) times the algorithmic bytes per launch
-        ratio = MGS_DRAM_PER_ALGORITHMIC.get(args.precision) if dom == "mgs" and not args.region else None
+        ratio = GS_DRAM_PER_ALGORITHMIC.get(args.precision) if dom == "gs" and not args.region else None
         launches_per_step = nlaunch / steps
         traffic = round(ratio * by / launches_per_step) if ratio and by else None
         roof = {"kernel": dom, "bound": bound, "achieved": round(ach, 3), "peak": round(peak, 3),
                 "unit": unit, "frac": round(ach / peak, 4), "traffic": traffic,
                 "traffic_note": ("dram bytes per average launch = DRAM/algorithmic "
-                                 f"{ratio} (ncu, mgs_kernel<float,16,1024>, step n=20, 608 columns) "
+                                 f"{ratio} (ncu, gs_kernel<float,16,1024>, step n=20, 608 columns) "
                                  "x algorithmic bytes per launch") if traffic else None,
                 "peak_source": peak_src, "launches": nlaunch, "avg_launch_ms": round(dom_ms / nlaunch, 4),
                 "algorithmic_per_step": {"bytes": by, "flops": fl}}
@@ -463,15 +457,15 @@ def main():
         r64 = time_gpu(m, t, cols, args, 0, max(3, args.steps // 2), 3, dev)
         s64 = statistics.mean(r64["times"]) / 1e3
         st64 = r64["stats"]
-        ms64 = st64["mgs"][1]
-        by64, fl64 = (mgs_algorithmic_support(args.nu, tcnt, 8) if tcnt is not None
-                      else mgs_algorithmic(args.nu, m_vec, 8, ncols))
+        ms64 = st64["gs"][1]
+        by64, fl64 = (gs_algorithmic_support(args.nu, tcnt, 8) if tcnt is not None
+                      else gs_algorithmic(args.nu, m_vec, 8, ncols))
         ach64 = fl64 * max(3, args.steps // 2) / (ms64 / 1e3) / 1e12
         pk64 = 152 * 2 * 2 * 2.07e9 / 1e12
         line["fp64"] = {"value": round(world * ncols / s64, 2), "ms_per_step": round(s64 * 1e3, 3),
                         "kernel_ms_per_step": {k: round(v[1] / max(3, args.steps // 2), 3)
                                                for k, v in st64.items() if v[0]},
-                        "mgs_roofline": {"bound": "alu", "achieved": round(ach64, 3), "peak": round(pk64, 3),
+                        "gs_roofline": {"bound": "alu", "achieved": round(ach64, 3), "peak": round(pk64, 3),
                                          "unit": "TFLOP/s", "frac": round(ach64 / pk64, 4)},
                         "result": {"E_band_eV": r64["E"], "mu_eV": r64["mu"], "N": r64["N"]}}
         checks["fp64"] = gpu_outputs(m, r64["ctx"], cols, args.nu, 0)

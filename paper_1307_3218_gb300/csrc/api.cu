@@ -732,7 +732,7 @@ int marnoldi_solve(marnoldi_ctx *c, const int64_t *columns, int64_t ncols, int n
     const size_t vs = c->prec == 0 ? 8 : 4;
     const size_t reg_per_col = regional ? (size_t)region_atoms * (12 + 8 * (size_t)c->rm.maxrow) : 0;
     const size_t per_col = al((size_t)2 * nu * shape.m_pad * vs) + (size_t)2 * shape.m_pad * vs +
-                           (size_t)nu * nu * 8 + (size_t)nu * 8 + 64 + reg_per_col +
+                           (size_t)2 * nu * nu * 8 + (size_t)nu * 8 + 64 + reg_per_col +
                            (size_t)(shape.m_pad / 32) * 3 + (size_t)(nu + 2) * 4;
     int64_t B = c->batch_override;
     if (B <= 0) {
@@ -748,7 +748,8 @@ int marnoldi_solve(marnoldi_ctx *c, const int64_t *columns, int64_t ncols, int n
                  oU = oSK + al((size_t)B * nu * shape.m_pad * vs),
                  oUl = oU + al((size_t)B * shape.m_pad * vs),
                  oH = oUl + (c->prec == 1 ? al((size_t)B * shape.m_pad * vs) : 0),
-                 oSc = oH + al((size_t)B * nu * nu * 8),
+                 oL = oH + al((size_t)B * nu * nu * 8),
+                 oSc = oL + al((size_t)B * nu * nu * 8),
                  oC = oSc + al((size_t)B * nu * 8), oS = oC + al((size_t)B * 8),
                  oN = oS + al((size_t)B * 4), oRg = oN + al((size_t)B * 4),
                  oRc = oRg + (regional ? al((size_t)B * region_atoms * 4) : 0),
@@ -799,6 +800,7 @@ int marnoldi_solve(marnoldi_ctx *c, const int64_t *columns, int64_t ncols, int n
     kb.U = wb + oU;
     kb.Ulo = c->prec == 1 ? (void *)(wb + oUl) : nullptr;
     kb.Hsub = (double *)(wb + oH);
+    kb.Lsub = (double *)(wb + oL);
     kb.scale = (double *)(wb + oSc);
     kb.cn2 = (double *)(wb + oC);
     kb.status = (int *)(wb + oS);
@@ -866,7 +868,7 @@ int marnoldi_solve(marnoldi_ctx *c, const int64_t *columns, int64_t ncols, int n
                         }))) {
                 return rc;
             }
-            if ((rc = launch(c, KK_MGS, [&] { return launch_mgs(kb, n, n + 1 < nu, tau, c->stream); })))
+            if ((rc = launch(c, KK_GS, [&] { return launch_gs(kb, n, n + 1 < nu, tau, c->stream); })))
                 return rc;
         }
         if ((rc = launch(c, KK_EIG, [&] { return launch_eig(c->A, kb, c->st, start, rmp, es, c->stream); })))

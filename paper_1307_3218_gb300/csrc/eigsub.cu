@@ -61,7 +61,7 @@ __global__ void __launch_bounds__(kTriThreads) eig_tridiag_kernel(
     const int64_t *__restrict__ bcols, const int64_t *__restrict__ rp,
     const int32_t *__restrict__ ci, const int *__restrict__ reg, int n_reg, int cofs,
     double *__restrict__ D, double *__restrict__ E, double *__restrict__ RQ, int nr_max,
-    double *__restrict__ Ag)
+    double *__restrict__ Ag, const double *__restrict__ Lsub)
 {
     const int sc = blockIdx.x;
     const int c = cofs + sc;
@@ -106,6 +106,67 @@ __global__ void __launch_bounds__(kTriThreads) eig_tridiag_kernel(
                           : 0.0;
         }
         R[r * lda + i] = val;
+    }
+    __syncthreads();
+    // The stored basis K~ has unit S-norms and S-Gram matrix G = L L^T, so the
+    // S-orthonormal basis K = K~ L^-T carries the subspace problem
+    // A = L^-1 H~ L^-T and the rows q^T = q~^T L^-T and K_pat = K~_pat L^-T
+    // (row 0, e_1^T, is unchanged: K^T S e_j = sqrt(S_jj) e_1).  Lsub holds
+    // L^-1 (lower triangular); the products run in place from the last row
+    // (column) down, which only reads rows (columns) not yet replaced.
+    const double *Lc = Lsub + (int64_t)c * nu * nu;
+    constexpr int kPer = (kMaxNu + kTriThreads - 1) / kTriThreads;   // entries per thread
+    for (int i = n - 1; i >= 0; --i) {   // A <- L^-1 A, row i at a time
+        const double *Li = Lc + (int64_t)i * nu;
+        double x[kPer];
+#pragma unroll
+        for (int q = 0; q < kPer; ++q) {
+            const int col = tid + q * T;
+            double s = 0.0;
+            if (col < n)
+                for (int m = 0; m <= i; ++m) s = fma(Li[m], A[m * lda + col], s);
+            x[q] = s;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < kPer; ++q)
+            if (tid + q * T < n) A[i * lda + tid + q * T] = x[q];
+        __syncthreads();
+    }
+    for (int i = n - 1; i >= 0; --i) {   // A <- A L^-T, column i at a time
+        const double *Li = Lc + (int64_t)i * nu;
+        double x[kPer];
+#pragma unroll
+        for (int q = 0; q < kPer; ++q) {
+            const int row = tid + q * T;
+            double s = 0.0;
+            if (row < n)
+                for (int m = 0; m <= i; ++m) s = fma(A[row * lda + m], Li[m], s);
+            x[q] = s;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < kPer; ++q)
+            if (tid + q * T < n) A[(tid + q * T) * lda + i] = x[q];
+        __syncthreads();
+    }
+    for (int r = 1 + tid; r < nr; r += T) {   // R's rows 1..: R <- R L^-T, one row per thread
+        double *x = R + r * lda;
+        for (int i = n - 1; i >= 0; --i) {
+            const double *Li = Lc + (int64_t)i * nu;
+            double s = 0.0;
+            for (int m = 0; m <= i; ++m) s = fma(x[m], Li[m], s);
+            x[i] = s;
+        }
+    }
+    __syncthreads();
+    for (int idx = tid; idx < n * n; idx += T) {   // symmetrise what rounding left
+        const int i = idx / n, l = idx - (idx / n) * n;
+        if (i > l) {
+            const double a = 0.5 * (A[i * lda + l] + A[l * lda + i]);
+            A[i * lda + l] = a;
+            A[l * lda + i] = a;
+        }
     }
     __syncthreads();
 
@@ -372,7 +433,7 @@ cudaError_t tridiag_dispatch(const DeviceMatrix &A, const KrylovBatch &b, const 
     }
     eig_tridiag_kernel<VT><<<nb2, kTriThreads, smem, s>>>(
         b.Hsub, b.nu_eff, b.scale, (const VT *)b.K, b.shape.m_pad, b.tinv, b.nb, nu, b.cols, A.rp, A.ci,
-        rm ? rm->reg : nullptr, rm ? rm->n_reg : 0, cofs, es.D, es.E, es.RQ, es.nr_max, es.Ag);
+        rm ? rm->reg : nullptr, rm ? rm->n_reg : 0, cofs, es.D, es.E, es.RQ, es.nr_max, es.Ag, b.Lsub);
     return cudaGetLastError();
 }
 

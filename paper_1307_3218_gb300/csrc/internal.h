@@ -12,7 +12,7 @@ namespace marnoldi {
 enum KernelKind {
     KK_INIT = 0,
     KK_SPMM_H,
-    KK_MGS,
+    KK_GS,
     KK_SPMM_S,
     KK_EIG,
     KK_MINMAX,
@@ -61,9 +61,10 @@ struct KrylovBatch {
     ColumnShape shape;
     void *K, *SK, *U;
     void *Ulo;            // mixed precision: lo word of H w_n (u = U + Ulo to ~2^-48)
-    double *Hsub;
+    double *Hsub;         // [c][nu][nu]: k_i . H k_l of the stored basis (unit S-norm)
+    double *Lsub;         // [c][nu][nu]: L^-1, L the lower Cholesky factor of its S-Gram matrix
     double *scale;        // [c][nu]
-    double *cn2;          // per column: sum_i (c1_i + c2_i)^2 of the last MGS
+    double *cn2;          // per column: |S-projection of s_n H w_n on the basis|_S^2 of the last step
     int *status;
     int *nu_eff;
     const int64_t *cols;  // global orbital column of each batch column
@@ -149,7 +150,7 @@ cudaError_t launch_support(const DeviceMatrix &A, const RegionMaps *rm, const Kr
 // outside thop <= lim - 1).
 cudaError_t launch_spmm_hs(const DeviceMatrix &A, const KrylovBatch &b, const void *X, int64_t ldx,
                            void *SY, int64_t ldsy, int lim, cudaStream_t s);
-cudaError_t launch_mgs(const KrylovBatch &b, int n, int need_w, double tau, cudaStream_t s);
+cudaError_t launch_gs(const KrylovBatch &b, int n, int need_w, double tau, cudaStream_t s);
 
 // ---------------------------------------------------------------- subspace eigensolve
 // Per solved column c (global index col0 + batch column):

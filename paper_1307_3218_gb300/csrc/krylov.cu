@@ -30,7 +30,7 @@ namespace marnoldi {
 
 const char *kernel_name(int kind)
 {
-    static const char *names[KK_NKINDS] = {"init",   "spmm_H", "mgs",     "spmm_S", "eigsub",
+    static const char *names[KK_NKINDS] = {"init",   "spmm_H", "gs",      "spmm_S", "eigsub",
                                            "minmax", "count",  "density", "green", "region", "support", "spmm_HS"};
     return (kind >= 0 && kind < KK_NKINDS) ? names[kind] : "?";
 }
@@ -309,7 +309,7 @@ __global__ void __launch_bounds__(256) spmm_hs_kernel(
     }
 }
 
-// ------------------------------------------------------------------ MGS
+// ------------------------------------------------------------------ Gram-Schmidt
 // One CTA of T threads (NW = T / 32 warps) per column; thread t owns the
 // values at positions p = t + v T (v < VPT) of the column's vectors, which are
 // stored in the column's tile order (tiles of 32 entries by hop count from the
@@ -322,35 +322,43 @@ __global__ void __launch_bounds__(256) spmm_hs_kernel(
 // constants, so the offsets of the values and of the vector slots are load
 // immediates.
 //
-// Each Gram-Schmidt pass runs over the stored vectors in blocks of kGsBlock:
-// one sweep forms the block's coefficients against the same w, one CTA
-// reduction sums them, and one sweep subtracts them (block modified
-// Gram-Schmidt; the vectors of a block are S-orthonormal, so within a block
-// the coefficients equal those of the vector-by-vector order up to rounding,
-// and the second pass removes what rounding leaves).  The update sweep
-// re-reads the block's vectors, which the coefficient sweep has just brought
-// into L2.  A reduction is a latency chain of shuffles, two barriers and the
-// FP64 scalar work; blocks cut the chains per step from 2 (n + 1) + 1 to
-// 2 ceil((n + 1) / kGsBlock) + 1.
+// Orthogonalisation (one pass, with the exact S-Gram matrix).  The stored
+// vectors w_i, scaled to unit S-norm (k_i = s_i w_i), are S-orthonormal only
+// up to rounding; their Gram matrix G = K^T S K = L L^T is kept exactly
+// through L^-1 (its new row every step from G's new column), so that every
+// solve with G is a pair of matrix-vector products.  Step n
+// forms, in one sweep over the stored vectors i <= n (blocks of kGsBlock
+// vectors, one CTA reduction each),
+//   a_i = w_i . u          H_sub entries of the stored basis (u = H w_n)
+//   b_i = (S w_i) . u      right-hand side of the S-projection of u
+//   g_i = (S w_i) . w_n    G's column n (g_n = beta_n^2)
+// then, in FP64 over the CTA, the S-projection coefficients c = G^-1 p of
+// s_n u onto span(K) and subtracts them in a streaming sweep with no
+// reductions: w_{n+1} = s_n u - sum_i c_i k_i.  Whatever rounding leaves
+// along span(K) is carried by G, so the subspace problem, solved on
+// L^-1 H_sub L^-T, is the exact Rayleigh-Ritz projection on the stored
+// vectors.  The subspace is span{e_j, H e_j, ...} whatever the coefficients,
+// so in exact arithmetic this is the method's Arnoldi basis; per stored vector
+// and step it reads w_i and S w_i once for the coefficients and w_i once for
+// the subtraction (three vector reads, against four for two Gram-Schmidt
+// passes), and runs one reduction per block instead of two.
 //
-// w lives in registers for small VPT and in shared memory for large; u
-// (with its lo word in mixed precision) in shared memory when it fits, else
-// re-read from global memory (an L2 hit: the SpMM has just written it).  In
-// mixed precision the lo word of u only corrects h_{i,n} by about 2^-24
-// relative, so its products are summed with plain FMAs and folded into the lo
-// word of the accurate sum.
+// In mixed precision a_i and g_i are accumulated error-free (exact FP32
+// products, two-sums, (hi, lo) pairs; the lo word of u, which only corrects
+// a_i by about 2^-24, through plain FMAs).  b_i is summed per thread with
+// plain FMAs (the CTA reduction stays accurate): its rounding only leaves a
+// component of w_{n+1} along span(K) at the level the FP32 subtraction leaves
+// anyway, which G records.  The coefficients and G are FP64.
+// u (and its lo word) and w sit in shared memory (or registers for small
+// VPT); w holds w_n during the coefficient sweep and w_{n+1} afterwards.
 constexpr int kGsBlock = 4;
 
 template <typename VT, int VPT, int T>
-struct MgsCfg {
+struct GsCfg {
     static constexpr bool kLo = sizeof(VT) == 4;                    // u as (hi, lo) pair
     static constexpr bool kWs = VPT >= (sizeof(VT) == 4 ? 8 : 4);    // w in smem
     static constexpr bool kUs = kLo || !kWs || 2 * VPT * T * sizeof(VT) <= 160 * 1024;
-    // values per batch of loads: pass-1 coefficients (8 streams), beta and
-    // pass-2 coefficients (2 or 4 streams), subtractions (4 streams); FP64
-    // is bound by its arithmetic and runs one value at a time
-    static constexpr int kChunkDot = sizeof(VT) == 8 ? 1 : 2;
-    static constexpr int kChunkSmall = sizeof(VT) == 8 ? 1 : 4;
+    static constexpr int kChunkDot = sizeof(VT) == 8 ? 1 : 2;        // values per batch of loads
     static constexpr int kChunkUpd = sizeof(VT) == 8 ? 1 : 4;
     static constexpr int kSmemVectors = (kUs ? 1 : 0) + (kLo ? 1 : 0) + (kWs ? 1 : 0);
 };
@@ -383,23 +391,26 @@ __device__ __forceinline__ void for_live(int nv, F &&f)
     }
 }
 
-// Sum of N per-thread accumulators over the CTA in a fixed order.  In each
-// warp a reduce-scatter butterfly leaves value q = lane / (32 / N) on lanes
-// q (32 / N) .. (q + 1) (32 / N) - 1 (each lane sends half of its values per
-// round, so N values cost about as many shuffles as two), warp q then sums
-// value q over the warps, and its lane 0 runs epi(q, total): the scalar FP64
-// work of a reduction (scales, coefficients, the breakdown test) is done once
-// there and handed to the CTA through shared memory.  `buf` alternates the
-// partial slots so that two barriers per reduction suffice.
+// Sum of N <= 16 per-thread accumulators over the CTA in a fixed order.  In
+// each warp a reduce-scatter butterfly over NP = 2^ceil(log2 N) slots leaves
+// slot q on lanes q (32 / NP) .. (q + 1) (32 / NP) - 1 (each lane sends half of
+// its slots per round, so N values cost about as many shuffles as two); then
+// warp w sums values w, w + NW, ... over the warps and its lane 0 runs
+// epi(q, total).  `buf` alternates the partial slots (part holds
+// 2 x 16 x 32 doubles) so that two barriers per reduction suffice.
 template <typename VT, int N, typename Epi>
-__device__ __forceinline__ void block_sum(DotAcc<VT> (&a)[N], double *part, int &buf, Epi epi)
+__device__ __forceinline__ void block_sum(const DotAcc<VT> (&in)[N], double *part, int &buf, Epi epi)
 {
-    static_assert(N == 1 || N == 2 || N == 4 || N == 8, "N must be 1, 2, 4 or 8");
-    constexpr int LOGN = N == 8 ? 3 : N == 4 ? 2 : N == 2 ? 1 : 0;
+    static_assert(N >= 1 && N <= 16, "1 <= N <= 16");
+    constexpr int LOGN = N > 8 ? 4 : N > 4 ? 3 : N > 2 ? 2 : N > 1 ? 1 : 0;
+    constexpr int NP = 1 << LOGN;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    DotAcc<VT> a[NP];
+#pragma unroll
+    for (int q = 0; q < N; ++q) a[q] = in[q];
 #pragma unroll
     for (int r = 0; r < LOGN; ++r) {
-        const int o = 16 >> r, half = N >> (r + 1);
+        const int o = 16 >> r, half = NP >> (r + 1);
         const bool up = (lane & o) != 0;
 #pragma unroll
         for (int j = 0; j < half; ++j) {
@@ -411,45 +422,58 @@ __device__ __forceinline__ void block_sum(DotAcc<VT> (&a)[N], double *part, int 
     }
 #pragma unroll
     for (int o = 16 >> LOGN; o > 0; o >>= 1) a[0].merge(a[0].shfl_xor(o));
-    if ((lane & ((32 >> LOGN) - 1)) == 0) part[(buf * N + (lane >> (5 - LOGN))) * 32 + warp] = a[0].pack();
+    const int qm = lane >> (5 - LOGN);
+    if ((lane & ((32 >> LOGN) - 1)) == 0 && qm < N) part[(buf * 16 + qm) * 32 + warp] = a[0].pack();
     __syncthreads();
-    if (warp < N) {
+    for (int q = warp; q < N; q += nw) {
         DotAcc<VT> x;
-        if (lane < nw) x.unpack(part[(buf * N + warp) * 32 + lane]);
+        if (lane < nw) x.unpack(part[(buf * 16 + q) * 32 + lane]);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) x.merge(x.shfl_xor(o));
-        if (lane == 0) epi(warp, x.value());
+        if (lane == 0) epi(q, x.value());
     }
     __syncthreads();
     buf ^= 1;
 }
 
-template <typename VT, int VPT, int T>
-__global__ void __launch_bounds__(T, T == 256 ? 4 : T == 512 ? 2 : 1) mgs_kernel(
-    VT *__restrict__ K, VT *__restrict__ SK, const VT *__restrict__ U, const VT *__restrict__ Ulo,
-    double *__restrict__ Hsub, double *__restrict__ scale, double *__restrict__ cn2,
-    int *__restrict__ status, int *__restrict__ nu_eff, const int *__restrict__ tcnt, int n, int nu,
-    int need_w, double tau2)
+// sum over the warp of x (every lane holds the total)
+__device__ __forceinline__ double warp_total(double x)
 {
-    using Cfg = MgsCfg<VT, VPT, T>;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(kFull, x, o);
+    return x;
+}
+
+template <typename VT, int VPT, int T>
+__global__ void __launch_bounds__(T, T == 256 ? 4 : T == 512 ? 2 : 1) gs_kernel(
+    VT *__restrict__ K, VT *__restrict__ SK, const VT *__restrict__ U, const VT *__restrict__ Ulo,
+    double *__restrict__ Hsub, double *__restrict__ Lsub, double *__restrict__ scale,
+    double *__restrict__ cn2, int *__restrict__ status, int *__restrict__ nu_eff,
+    const int *__restrict__ tcnt, int n, int nu, int need_w, double tau2)
+{
+    using Cfg = GsCfg<VT, VPT, T>;
     constexpr bool kWs = Cfg::kWs, kUs = Cfg::kUs, kLo = Cfg::kLo;
     constexpr int kB = kGsBlock;
     constexpr int64_t MP = (int64_t)VPT * T;   // m_pad
     const int c = blockIdx.x;
     if (status[c] != 0) return;
-    const int tid = threadIdx.x, warp = tid >> 5;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     VT *us = reinterpret_cast<VT *>(smem_raw);             // u = H w_n, unscaled (if kUs)
     VT *uls = us + (kUs ? MP : 0);                          // its lo word (mixed precision)
-    VT *ws = uls + (kLo ? MP : 0);                          // w (if kWs)
-    __shared__ double red[2 * 2 * kGsBlock * 32];   // reduction partials, two slots
-    __shared__ double ctot[kMaxNu];
-    __shared__ double ssc[kMaxNu];
+    VT *ws = uls + (kLo ? MP : 0);                          // w_n, then w_{n+1} (if kWs)
+    __shared__ double red[2 * 16 * 32];   // reduction partials, two slots
+    __shared__ double ssc[kMaxNu];        // s_i, then s_n
+    __shared__ double ta[kMaxNu], tb[kMaxNu], tg[kMaxNu];   // the sweep's totals
+    __shared__ double lrow[kMaxNu];       // L^-1 G_{<n, n}
+    __shared__ double nrow[kMaxNu];       // the new row n of L^-1
+    __shared__ double zc[kMaxNu];         // L^-1 p
     __shared__ int cnt_s[kMaxNu + 2];
-    __shared__ VT coef[2][kGsBlock];   // FP32/FP64 update coefficients of the last reduction
-    __shared__ double bc_sn;
+    __shared__ VT coef[kMaxNu];           // subtraction coefficients c_i s_i
     __shared__ int bc_stop;
+    __shared__ double bc_dinv;
     const int64_t base = (int64_t)c * nu * MP;
+    double *Lc = Lsub + (int64_t)c * nu * nu;   // L^-1, row-major, lower triangle
     int buf = 0;
     auto live = [&](int cnt) { return live_values<T>(cnt, warp); };
 
@@ -457,216 +481,256 @@ __global__ void __launch_bounds__(T, T == 256 ? 4 : T == 512 ? 2 : 1) mgs_kernel
     for (int L = tid; L <= n + 1; L += T) cnt_s[L] = tcnt[(int64_t)c * (nu + 2) + L];
     __syncthreads();
 
-    // beta_n = ||w_n||_S and the breakdown test (slot 0 is stored normalised)
-    double sn = 1.0;
-    if (n > 0) {
-        const VT *wn = K + base + (int64_t)n * MP + tid;
-        const VT *swn = SK + base + (int64_t)n * MP + tid;
-        DotAcc<VT> acc[1];
-        for_live<VPT, Cfg::kChunkSmall>(live(cnt_s[n]), [&](int v, bool a) {
-            acc[0].add(a ? wn[v * T] : VT(0), a ? swn[v * T] : VT(0));
-        });
-        block_sum(acc, red, buf, [&](int, double beta2) {
-            if (!(beta2 > 0.0) || beta2 <= tau2 * (beta2 + cn2[c])) {
-                status[c] = (beta2 >= 0.0) ? 1 : 2;   // 2: negative or NaN S-norm
-                nu_eff[c] = n;
-                bc_stop = 1;
-            } else {
-                const double s = 1.0 / sqrt(beta2);
-                scale[(int64_t)c * nu + n] = s;
-                bc_sn = s;
-                bc_stop = 0;
-            }
-        });
-        if (bc_stop) return;   // uniform: read after the reduction's last barrier
-        sn = bc_sn;
-    }
-    // w starts as u = s_n H w_n; the h dots use H w_n unscaled (with its lo
-    // word in mixed precision) and apply s_i s_n in FP64 after the reduction.
-    // Positions past u's support hold zeros, which partly live chunks read.
-    const VT vsn = (VT)sn;
+    // u (hi, lo) and w_n on chip; zeros past their supports
     const VT *u = U + (int64_t)c * MP + tid;
     const VT *ul = kLo ? Ulo + (int64_t)c * MP + tid : nullptr;
+    const VT *wnp = K + base + (int64_t)n * MP + tid;
     VT wr[kWs ? 1 : VPT];
-    {
-        const int nv = live(cnt_s[n + 1]);
-#pragma unroll
-        for (int v = 0; v < VPT; ++v) {
-            const int p = tid + v * T;
-            const bool a = v < nv;
-            const VT x = a ? u[v * T] : VT(0);
-            if constexpr (kWs) ws[p] = x * vsn; else wr[v] = x * vsn;
-            if constexpr (kUs) us[p] = x;
-            if constexpr (kLo) uls[p] = a ? ul[v * T] : VT(0);
-        }
-    }
     auto wget = [&](int v) -> VT {
         if constexpr (kWs) return ws[tid + v * T]; else return wr[v];
     };
     auto wset = [&](int v, VT x) {
         if constexpr (kWs) ws[tid + v * T] = x; else wr[v] = x;
     };
-    // w -= sum_l coef_l k_{i0+l} over the block (vectors re-read from L2)
-    auto update = [&](const VT *kb, const int (&nvl)[kB], int nvmax, const VT (&co)[kB]) {
-        for_live<VPT, Cfg::kChunkUpd>(nvmax, [&](int v, bool a) {
-            VT x = wget(v);
+    {
+        const int nvu = live(cnt_s[n + 1]), nvn = live(cnt_s[n]);
 #pragma unroll
-            for (int l = 0; l < kB; ++l) {
-                const VT kr = (a && v < nvl[l]) ? kb[l * MP + v * T] : VT(0);
-                x = fma(-co[l], kr, x);
-            }
-            wset(v, x);
-        });
-    };
-    // pass 1: h_{i,n} = k_i . u and the first Gram-Schmidt sweep
-    for (int i0 = 0; i0 <= n; i0 += kB) {
-        const int nbk = min(kB, n + 1 - i0);
-        int nvl[kB];
-        int nvmax = 0;
+        for (int v = 0; v < VPT; ++v) {
+            const int p = tid + v * T;
+            const bool a = v < nvu;
+            if constexpr (kUs) us[p] = a ? u[v * T] : VT(0);
+            if constexpr (kLo) uls[p] = a ? ul[v * T] : VT(0);
+            wset(v, v < nvn ? wnp[v * T] : VT(0));
+        }
+    }
+    auto block_live = [&](int i0, int nbk, int (&nvl)[kB]) {
+        int m = 0;
 #pragma unroll
         for (int l = 0; l < kB; ++l) {
             nvl[l] = l < nbk ? live(cnt_s[i0 + l + 1]) : 0;
-            nvmax = max(nvmax, nvl[l]);
+            m = max(m, nvl[l]);
         }
+        return m;
+    };
+
+    // ---- coefficient sweep over the stored vectors i <= n
+    for (int i0 = 0; i0 <= n; i0 += kB) {
+        const int nbk = min(kB, n + 1 - i0);
+        int nvl[kB];
+        const int nvmax = block_live(i0, nbk, nvl);
         const VT *kb = K + base + (int64_t)i0 * MP + tid;
         const VT *skb = SK + base + (int64_t)i0 * MP + tid;
-        DotAcc<VT> acc[2 * kB];   // [l]: c = S k . w, [kB + l]: h = k . u
-        VT hl[kB];
+        DotAcc<VT> acc[3 * kB];   // [l] a, [kB + l] b, [2 kB + l] g
+        VT hl[kB], bp[kB];
 #pragma unroll
-        for (int l = 0; l < kB; ++l) hl[l] = VT(0);
+        for (int l = 0; l < kB; ++l) hl[l] = bp[l] = VT(0);
         for_live<VPT, Cfg::kChunkDot>(nvmax, [&](int v, bool a) {
             const int p = tid + v * T;
             VT uu;
             if constexpr (kUs) uu = us[p]; else uu = a ? u[v * T] : VT(0);
-            const VT wv = wget(v);
+            const VT wn = wget(v);
 #pragma unroll
             for (int l = 0; l < kB; ++l) {
                 const bool al = a && v < nvl[l];
                 const VT kr = al ? kb[l * MP + v * T] : VT(0);
-                acc[kB + l].add(kr, uu);
+                const VT sr = al ? skb[l * MP + v * T] : VT(0);
+                acc[l].add(kr, uu);
                 if constexpr (kLo) hl[l] = fma(kr, uls[p], hl[l]);
-                if (need_w) acc[l].add(al ? skb[l * MP + v * T] : VT(0), wv);
+                if (need_w) bp[l] = fma(sr, uu, bp[l]);
+                acc[2 * kB + l].add(sr, wn);
             }
         });
 #pragma unroll
         for (int l = 0; l < kB; ++l) {
-            if constexpr (kLo) acc[kB + l].add_lo(hl[l]);
+            if constexpr (kLo) acc[l].add_lo(hl[l]);
+            acc[kB + l].set(bp[l]);
         }
         block_sum(acc, red, buf, [&](int q, double t) {
-            const int l = q < kB ? q : q - kB, i = i0 + l;
-            if (l >= nbk) {
-                if (q < kB) coef[buf][q] = VT(0);
-                return;
-            }
-            const double si = i == n ? sn : ssc[i];
-            if (q < kB) {
-                const double ci = t * si;
-                ctot[i] = ci;
-                coef[buf][q] = (VT)(ci * si);
-            } else {
-                const double h = t * si * sn;
-                Hsub[((int64_t)c * nu + i) * nu + n] = h;
-                Hsub[((int64_t)c * nu + n) * nu + i] = h;
-            }
+            const int l = q % kB, i = i0 + l;
+            if (l >= nbk) return;
+            if (q < kB) ta[i] = t; else if (q < 2 * kB) tb[i] = t; else tg[i] = t;
         });
-        if (need_w) {
-            VT co[kB];
-#pragma unroll
-            for (int l = 0; l < kB; ++l) co[l] = coef[buf ^ 1][l];
-            update(kb, nvl, nvmax, co);
+    }
+
+    // ---- scalars, G's column, the new row of L^-1, the coefficients (FP64).
+    // Lc holds L^-1 (lower triangular), so every product below is a matrix-
+    // vector product, one warp per row or column, with no serial chain.
+    if (tid == 0) {
+        double sn = 1.0;   // slot 0 is stored normalised (G_00 = 1)
+        int stop = 0;
+        if (n > 0) {
+            const double beta2 = tg[n];
+            if (!(beta2 > 0.0) || beta2 <= tau2 * (beta2 + cn2[c])) {
+                stop = 1;
+                status[c] = (beta2 >= 0.0) ? 1 : 2;   // 2: negative or NaN S-norm
+                nu_eff[c] = n;
+            } else {
+                sn = 1.0 / sqrt(beta2);
+                scale[(int64_t)c * nu + n] = sn;
+            }
+        }
+        ssc[n] = sn;
+        bc_stop = stop;
+    }
+    __syncthreads();
+    if (bc_stop) return;
+    const double sn = ssc[n];
+    for (int m = tid; m <= n; m += T) {   // G_{mn}, p_m (of s_n u) and h_m of unit-norm vectors
+        const double f = ssc[m] * sn;
+        tg[m] *= f;
+        tb[m] *= f;
+        const double h = ta[m] * f;
+        Hsub[((int64_t)c * nu + m) * nu + n] = h;
+        Hsub[((int64_t)c * nu + n) * nu + m] = h;
+    }
+    __syncthreads();
+    constexpr int NW = T / 32;
+    // l = L^-1 G_{<n, n}
+    for (int r = warp; r < n; r += NW) {
+        double x = 0.0;
+        for (int m = lane; m <= r; m += 32) x = fma(Lc[(int64_t)r * nu + m], tg[m], x);
+        x = warp_total(x);
+        if (lane == 0) lrow[r] = x;
+    }
+    __syncthreads();
+    // d = sqrt(G_nn - |l|^2), G_nn = 1; the new row of L^-1 is (-l^T L^-1, 1) / d
+    if (warp == 0) {
+        double x = 0.0;
+        for (int r = lane; r < n; r += 32) x = fma(lrow[r], lrow[r], x);
+        x = warp_total(x);
+        if (lane == 0) {
+            const double dd = 1.0 - x;
+            if (!(dd > 0.0)) {   // the stored basis has lost its rank
+                bc_stop = 1;
+                status[c] = 1;
+                nu_eff[c] = n;
+            } else {
+                bc_dinv = 1.0 / sqrt(dd);
+            }
         }
     }
-    if (!need_w) return;
-    // pass 2: second Gram-Schmidt sweep
-    for (int i0 = 0; i0 <= n; i0 += kB) {
-        const int nbk = min(kB, n + 1 - i0);
-        int nvl[kB];
-        int nvmax = 0;
-#pragma unroll
-        for (int l = 0; l < kB; ++l) {
-            nvl[l] = l < nbk ? live(cnt_s[i0 + l + 1]) : 0;
-            nvmax = max(nvmax, nvl[l]);
+    __syncthreads();
+    if (bc_stop) return;
+    const double dinv = bc_dinv;
+    double *Ln = Lc + (int64_t)n * nu;
+    for (int m = warp; m < n; m += NW) {
+        double x = 0.0;
+        for (int r = m + lane; r < n; r += 32) x = fma(lrow[r], Lc[(int64_t)r * nu + m], x);
+        x = warp_total(x);
+        if (lane == 0) {
+            nrow[m] = -dinv * x;
+            Ln[m] = -dinv * x;
         }
+    }
+    if (tid == 0) {
+        nrow[n] = dinv;
+        Ln[n] = dinv;
+    }
+    __syncthreads();
+    if (!need_w) return;
+    // z = L^-1 p, |z|^2 = |projection of s_n u|_S^2, c = L^-T z
+    for (int r = warp; r <= n; r += NW) {
+        const double *Lr = r == n ? nrow : Lc + (int64_t)r * nu;
+        double x = 0.0;
+        for (int m = lane; m <= r; m += 32) x = fma(Lr[m], tb[m], x);
+        x = warp_total(x);
+        if (lane == 0) zc[r] = x;
+    }
+    __syncthreads();
+    for (int m = warp; m <= n; m += NW) {
+        double x = 0.0;
+        for (int r = m + lane; r <= n; r += 32) x = fma(r == n ? nrow[m] : Lc[(int64_t)r * nu + m], zc[r], x);
+        x = warp_total(x);
+        if (lane == 0) coef[m] = (VT)(x * ssc[m]);
+    }
+    if (warp == 0) {
+        double x = 0.0;
+        for (int r = lane; r <= n; r += 32) x = fma(zc[r], zc[r], x);
+        x = warp_total(x);
+        if (lane == 0) cn2[c] = x;
+    }
+    __syncthreads();
+
+    // ---- w_{n+1} = s_n u - sum_i coef_i w_i: streaming subtraction, last block
+    // first (its vectors are the ones the sweep read last; its support is u's)
+    const VT vsn = (VT)ssc[n];
+    const int nb1 = (n + kB) / kB;
+    for (int b = nb1 - 1; b >= 0; --b) {
+        const int i0 = b * kB, nbk = min(kB, n + 1 - i0);
+        int nvl[kB];
+        const int nvmax = block_live(i0, nbk, nvl);
+        const bool first = b == nb1 - 1;
+        const int nvs = first ? live(cnt_s[n + 1]) : nvmax;
         const VT *kb = K + base + (int64_t)i0 * MP + tid;
-        const VT *skb = SK + base + (int64_t)i0 * MP + tid;
-        DotAcc<VT> acc[kB];
-        for_live<VPT, Cfg::kChunkSmall>(nvmax, [&](int v, bool a) {
-            const VT wv = wget(v);
-#pragma unroll
-            for (int l = 0; l < kB; ++l)
-                acc[l].add((a && v < nvl[l]) ? skb[l * MP + v * T] : VT(0), wv);
-        });
-        block_sum(acc, red, buf, [&](int q, double t) {
-            if (q >= nbk) {
-                coef[buf][q] = VT(0);
-                return;
-            }
-            const int i = i0 + q;
-            const double si = i == n ? sn : ssc[i];
-            const double ci = t * si;
-            ctot[i] += ci;
-            coef[buf][q] = (VT)(ci * si);
-        });
         VT co[kB];
 #pragma unroll
-        for (int l = 0; l < kB; ++l) co[l] = coef[buf ^ 1][l];
-        update(kb, nvl, nvmax, co);
+        for (int l = 0; l < kB; ++l) co[l] = l < nbk ? coef[i0 + l] : VT(0);
+        for_live<VPT, Cfg::kChunkUpd>(nvs, [&](int v, bool a) {
+            VT x;
+            if (first) {
+                VT uu;
+                if constexpr (kUs) uu = us[tid + v * T]; else uu = a ? u[v * T] : VT(0);
+                x = uu * vsn;
+            } else {
+                x = wget(v);
+            }
+#pragma unroll
+            for (int l = 0; l < kB; ++l)
+                x = fma(-co[l], (a && v < nvl[l]) ? kb[l * MP + v * T] : VT(0), x);
+            wset(v, x);
+        });
     }
     VT *wo = K + base + (int64_t)(n + 1) * MP + tid;   // the next slot, unnormalised, zeros included
+    const int nvu = live(cnt_s[n + 1]);
 #pragma unroll
-    for (int v = 0; v < VPT; ++v) wo[v * T] = wget(v);
-    if (tid == 0) {
-        double q = 0.0;
-        for (int i = 0; i <= n; ++i) q += ctot[i] * ctot[i];
-        cn2[c] = q;
-    }
+    for (int v = 0; v < VPT; ++v) wo[v * T] = v < nvu ? wget(v) : VT(0);
 }
 
 template <typename VT, int VPT, int T>
-cudaError_t mgs_dispatch(const KrylovBatch &b, int n, int need_w, double tau, cudaStream_t s)
+cudaError_t gs_dispatch(const KrylovBatch &b, int n, int need_w, double tau, cudaStream_t s)
 {
-    using Cfg = MgsCfg<VT, VPT, T>;
-    if (b.shape.m_pad != (int64_t)VPT * T || b.ntile != VPT * T / 32 || !b.tcnt)
+    using Cfg = GsCfg<VT, VPT, T>;
+    if (b.shape.m_pad != (int64_t)VPT * T || b.ntile != VPT * T / 32 || !b.tcnt || !b.Lsub)
         return cudaErrorInvalidValue;
     const size_t smem = (size_t)VPT * T * sizeof(VT) * Cfg::kSmemVectors;
     static bool configured = false;
     if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(mgs_kernel<VT, VPT, T>,
+        cudaError_t e = cudaFuncSetAttribute(gs_kernel<VT, VPT, T>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         configured = true;
     }
-    mgs_kernel<VT, VPT, T><<<b.nb, T, smem, s>>>(
-        (VT *)b.K, (VT *)b.SK, (const VT *)b.U, (const VT *)b.Ulo, b.Hsub, b.scale, b.cn2,
+    gs_kernel<VT, VPT, T><<<b.nb, T, smem, s>>>(
+        (VT *)b.K, (VT *)b.SK, (const VT *)b.U, (const VT *)b.Ulo, b.Hsub, b.Lsub, b.scale, b.cn2,
         b.status, b.nu_eff, b.tcnt, n, b.nu, need_w, tau * tau);
     return cudaGetLastError();
 }
 
 template <typename VT>
-cudaError_t mgs_shape(const KrylovBatch &b, int n, int need_w, double tau, cudaStream_t s)
+cudaError_t gs_shape(const KrylovBatch &b, int n, int need_w, double tau, cudaStream_t s)
 {
     if (b.shape.threads == 512) {   // FP32, 16 values per thread
         if constexpr (sizeof(VT) == 4)
-            if (b.shape.vpt == 16) return mgs_dispatch<VT, 16, 512>(b, n, need_w, tau, s);
+            if (b.shape.vpt == 16) return gs_dispatch<VT, 16, 512>(b, n, need_w, tau, s);
         return cudaErrorInvalidValue;
     }
     if (b.shape.threads == 1024) {
         switch (b.shape.vpt) {
-        case 1: return mgs_dispatch<VT, 1, 1024>(b, n, need_w, tau, s);
-        case 2: return mgs_dispatch<VT, 2, 1024>(b, n, need_w, tau, s);
-        case 4: return mgs_dispatch<VT, 4, 1024>(b, n, need_w, tau, s);
-        case 8: return mgs_dispatch<VT, 8, 1024>(b, n, need_w, tau, s);
-        case 16: return mgs_dispatch<VT, 16, 1024>(b, n, need_w, tau, s);
+        case 1: return gs_dispatch<VT, 1, 1024>(b, n, need_w, tau, s);
+        case 2: return gs_dispatch<VT, 2, 1024>(b, n, need_w, tau, s);
+        case 4: return gs_dispatch<VT, 4, 1024>(b, n, need_w, tau, s);
+        case 8: return gs_dispatch<VT, 8, 1024>(b, n, need_w, tau, s);
+        case 16: return gs_dispatch<VT, 16, 1024>(b, n, need_w, tau, s);
         default: return cudaErrorInvalidValue;
         }
     }
     if (b.shape.threads != 256) return cudaErrorInvalidValue;
     switch (b.shape.vpt) {
-    case 1: return mgs_dispatch<VT, 1, 256>(b, n, need_w, tau, s);
-    case 2: return mgs_dispatch<VT, 2, 256>(b, n, need_w, tau, s);
-    case 4: return mgs_dispatch<VT, 4, 256>(b, n, need_w, tau, s);
-    case 8: return mgs_dispatch<VT, 8, 256>(b, n, need_w, tau, s);
-    case 16: return mgs_dispatch<VT, 16, 256>(b, n, need_w, tau, s);
+    case 1: return gs_dispatch<VT, 1, 256>(b, n, need_w, tau, s);
+    case 2: return gs_dispatch<VT, 2, 256>(b, n, need_w, tau, s);
+    case 4: return gs_dispatch<VT, 4, 256>(b, n, need_w, tau, s);
+    case 8: return gs_dispatch<VT, 8, 256>(b, n, need_w, tau, s);
+    case 16: return gs_dispatch<VT, 16, 256>(b, n, need_w, tau, s);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -715,9 +779,9 @@ cudaError_t launch_spmm_hs(const DeviceMatrix &A, const KrylovBatch &b, const vo
     return cudaGetLastError();
 }
 
-cudaError_t launch_mgs(const KrylovBatch &b, int n, int need_w, double tau, cudaStream_t s)
+cudaError_t launch_gs(const KrylovBatch &b, int n, int need_w, double tau, cudaStream_t s)
 {
-    return b.prec == 0 ? mgs_shape<double>(b, n, need_w, tau, s) : mgs_shape<float>(b, n, need_w, tau, s);
+    return b.prec == 0 ? gs_shape<double>(b, n, need_w, tau, s) : gs_shape<float>(b, n, need_w, tau, s);
 }
 
 }  // namespace marnoldi
