@@ -6,8 +6,9 @@
  * for every requested basis index j of a sparse real-symmetric LCAO pair (H, S),
  * S positive definite, it
  *   1. builds the nu-dimensional Krylov subspace L_nu^(j) that contains e_j
- *      (span{e_j, H e_j, ..., H^(nu-1) e_j}) with an S-orthonormal basis K,
- *      using two-pass modified Gram-Schmidt in the S inner product;
+ *      (span{e_j, H e_j, ..., H^(nu-1) e_j}) with an S-orthonormal basis K
+ *      (Gram-Schmidt in the S inner product against the exact S-Gram matrix
+ *      of the stored vectors);
  *   2. solves the nu x nu standard subspace eigenproblem H_sub = K^T H K
  *      (levels eps_a, vectors v_a);
  *   3. turns the subspace eigenpairs into the columns of the Green's function

@@ -1,27 +1,26 @@
 // Krylov-subspace build of the multiple Arnoldi method on sm_103a.
 //
-// For a batch of columns j, builds the S-orthonormal basis K of
+// For a batch of columns j, builds a basis of
 // span{e_j, H e_j, ..., H^(nu-1) e_j} (arXiv:1307.3218, Section 2: the subspace
 // L_nu^(j) containing e_j whose nu x nu *standard* eigenproblem replaces
-// H phi = eps S phi, Eq. 2) and the explicit subspace matrix H_sub = K^T H K.
+// H phi = eps S phi, Eq. 2), its S-Gram matrix and the explicit subspace
+// matrix of the stored vectors; the eigensolve turns them into the
+// S-orthonormal basis K and H_sub = K^T H K.
 //
 // The basis is stored unnormalised: slot i holds w_i and S w_i, and
 // k_i = s_i w_i with s_i = 1 / ||w_i||_S.  One Krylov step n, for every column:
-//   spmm(H):    H w_n                                    (BSR 4x4 x batch panel)
-//   mgs:        beta_n = sqrt(w_n . S w_n); stop the column when
-//               beta_n^2 <= tau^2 (beta_n^2 + sum_i c_i^2), i.e.
-//               ||w_n||_S <= tau ||u_{n-1}||_S (S-orthogonality of K splits
-//               ||u||_S^2 into beta^2 plus the squared projection coefficients);
-//               else s_n = 1 / beta_n, u = s_n H w_n, h_{i,n} = k_i . u (i <= n),
-//               and two passes of modified Gram-Schmidt in the S inner product
-//               using the stored S w_i: c_i = (S k_i) . w, w -= c_i k_i;
-//               w is written to slot n+1
-//   spmm(S):    S w into slot n+1
+//   spmm_hs:  H w_n into U (accurate (hi, lo) in mixed precision) and, for
+//             n >= 1, S w_n into slot n (one gather of w_n for both)
+//   gs:       beta_n^2 = w_n . S w_n; stop the column when
+//             beta_n^2 <= tau^2 (beta_n^2 + |projection of u_{n-1}|_S^2), i.e.
+//             ||w_n||_S <= tau ||u_{n-1}||_S; else s_n = 1 / beta_n, the
+//             entries k_i . H k_n, the Gram column k_i . S k_n, and
+//             w_{n+1} = s_n H w_n - (its S-projection on span(K)) into slot n+1
 //
-// Inner products are always accumulated to FP64 accuracy; in mixed precision
-// the vectors, the SpMM and the Gram-Schmidt updates are FP32.  Reductions use
-// a fixed order (warp butterfly, then warp 0 over the warps), so results do not
-// depend on scheduling.
+// Inner products are accumulated to FP64 accuracy where the result needs it;
+// in mixed precision the vectors, the SpMM and the Gram-Schmidt updates are
+// FP32.  Reductions use a fixed order (warp butterflies, then one warp over
+// the warps), so results do not depend on scheduling.
 #include "internal.h"
 
 #include <cstdio>
