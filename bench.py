@@ -62,6 +62,10 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-extra", action="store_true",
                    help="skip the nu=100 and regional side measurements")
+    p.add_argument("--no-serving", action="store_true", help="skip the request-server measurement")
+    p.add_argument("--serve-requests", type=int, default=60)
+    p.add_argument("--serve-workers", type=int, default=4)
+    p.add_argument("--serve-budget-gb", type=float, default=64.0)
     p.add_argument("--cpu-seconds", type=float, default=15.0)
     p.add_argument("--region", type=int, default=0,
                    help="regional mode with this many atoms per region (0 = global mode)")
@@ -496,6 +500,10 @@ def main():
                 checks[label] = gpu_outputs(m, rx["ctx"], cl, nu_x, pr)
             m.marnoldi_destroy(rx["ctx"])
 
+    if not args.no_serving and world == 1:
+        line["serving"] = serving(m, t, args.serve_requests, args.serve_workers,
+                                  int(args.serve_budget_gb * 2**30), prec)
+
     if not args.no_e2e:
         e2e_s, h2d, d2h = time_e2e(m, t, cols, args, prec, max(3, args.steps // 2), 1)
         line["e2e"] = {"value": round(world * ncols / e2e_s, 2), "unit": UNIT,
@@ -514,6 +522,80 @@ def main():
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+SERVE_SIZES = (256, 512, 1024, 2048, 4096)
+SERVE_SIZE_P = (0.3, 0.3, 0.2, 0.15, 0.05)
+
+
+def serving(m, t4096, requests: int, workers: int, budget: int, prec: int):
+    """Whole calculations through the request server on a seeded trace.
+
+    Structures of 256 to 4,096 atoms (amorphous carbon, the same recipe as
+    the headline), nu = 30, or nu = 100 for a quarter of the requests of
+    <= 1,024 atoms; the density matrices go back to the host.  Three passes:
+    the whole trace submitted at once with one worker (requests one after
+    another) and with `workers` (concurrent), then Poisson arrivals at 60 % of
+    the concurrent pass's request rate, whose submit-to-result latencies give
+    p50 / p99.
+    """
+    import torch
+    from tbsynth import amorphous_system
+
+    rng = np.random.default_rng(2024)
+    pool = {n: (t4096 if n == t4096.n_block_rows else amorphous_system(n, seed=100 + n))
+            for n in SERVE_SIZES}
+    trace = []
+    for _ in range(requests):
+        n = int(rng.choice(SERVE_SIZES, p=SERVE_SIZE_P))
+        nu = 100 if n <= 1024 and rng.random() < 0.25 else 30
+        trace.append((n, nu))
+    ncols_total = sum(pool[n].real_columns().size for n, _ in trace)
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+
+    def run(nworkers, gaps=None):
+        with m.Server(workers=nworkers, hbm_budget_bytes=budget) as srv:
+            # warm the pool and the kernels once
+            srv.wait(srv.submit_system(pool[512], prec, 30, 0, pool[512].n_electrons, 0.1))
+            ids, t0 = [], time.perf_counter()
+            for k, (n, nu) in enumerate(trace):
+                if gaps is not None:
+                    due = t0 + gaps[k]
+                    while time.perf_counter() < due:
+                        time.sleep(min(0.002, max(0.0, due - time.perf_counter())))
+                sysm = pool[n]
+                ids.append(srv.submit_system(sysm, prec, nu, 0, sysm.n_electrons, 0.1))
+            res = [srv.wait(i) for i in ids]
+            st = srv.stats()
+        first = min(r["t_submit"] for r in res)
+        wall = max(r["t_end"] for r in res) - first
+        lat = np.array([r["latency_s"] for r in res]) * 1e3
+        return dict(wall=wall, lat=lat, stats=st)
+
+    seq = run(1)
+    burst = run(workers)
+    rate = 0.6 * requests / burst["wall"]
+    gaps = np.cumsum(rng.exponential(1.0 / rate, size=requests))
+    gaps -= gaps[0]
+    pois = run(workers, gaps)
+    lat = pois["lat"]
+    return {
+        "trace": f"{requests} requests, atoms {list(SERVE_SIZES)} with p {list(SERVE_SIZE_P)}, "
+                 f"nu 30 (nu 100 for 1/4 of those <= 1024 atoms), {'mixed' if prec else 'fp64'}, "
+                 f"all real orbitals, density matrices returned to the host",
+        "columns": int(ncols_total), "workers": workers, "hbm_budget_gb": round(budget / 2**30, 1),
+        "sequential": {"wall_s": round(seq["wall"], 3), "columns_per_s": round(ncols_total / seq["wall"], 1)},
+        "concurrent": {"wall_s": round(burst["wall"], 3),
+                       "columns_per_s": round(ncols_total / burst["wall"], 1),
+                       "peak_running": burst["stats"]["peak_running"],
+                       "peak_footprint_gb": round(burst["stats"]["peak_bytes"] / 2**30, 2)},
+        "poisson": {"offered_requests_per_s": round(rate, 2),
+                    "p50_ms": round(float(np.percentile(lat, 50)), 2),
+                    "p99_ms": round(float(np.percentile(lat, 99)), 2),
+                    "mean_ms": round(float(lat.mean()), 2), "max_ms": round(float(lat.max()), 2),
+                    "columns_per_s": round(ncols_total / pois["wall"], 1)},
+    }
 
 
 def main_reference(args, world, rank):

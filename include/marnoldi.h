@@ -33,7 +33,8 @@
  *   - Host pointers unless a name ends in _device.  The caller owns every
  *     array it passes; the library copies what it keeps.
  *   - One context per structure.  A context's calls are issued on its CUDA
- *     stream and are not thread-safe; different contexts are independent.
+ *     stream and are not thread-safe; different contexts are independent and
+ *     may be used from different threads at the same time.
  */
 #ifndef MARNOLDI_H
 #define MARNOLDI_H
@@ -55,7 +56,8 @@ typedef enum {
     MARNOLDI_ECUDA = -4,     /* a CUDA call failed */
     MARNOLDI_ETIMEOUT = -5,  /* a bounded device loop ran out of iterations */
     MARNOLDI_ESTATE = -6,    /* call out of order (e.g. density before solve) */
-    MARNOLDI_ENOCONV = -7    /* the subspace eigensolver or the bisection did not converge */
+    MARNOLDI_ENOCONV = -7,   /* the subspace eigensolver or the bisection did not converge */
+    MARNOLDI_EPENDING = -8   /* a server request has not finished within the wait's timeout */
 } marnoldi_status;
 
 typedef enum {
@@ -226,6 +228,83 @@ int marnoldi_kernel_stats(marnoldi_ctx *ctx, int kind, const char **name, int64_
 int marnoldi_count_noalloc(const double *eps_device, const double *w_device,
                            const int32_t *nu_eff_device, int64_t ncols, int nu, double mu,
                            double kT, double *out_device, void *cuda_stream);
+
+/*
+ * Device memory.
+ *   marnoldi_device_bytes: bytes the context holds now and the most it has held
+ *     since setup (requested sizes; the allocator may round them up).
+ *   marnoldi_footprint: the peak of marnoldi_setup, one marnoldi_solve of every
+ *     real orbital (columns == NULL) and one marnoldi_density, computed on the
+ *     host from the block pattern alone: structure copies, column state, batch
+ *     workspace of batch_columns columns (>= 1; clamped to the column count and
+ *     the launch limits; the value used goes to *batch_used, which may be NULL)
+ *     and the density staging.  box is needed in regional mode (cell list).  It
+ *     equals the peak of marnoldi_device_bytes of such a run.  Errors
+ *     (MARNOLDI_EINVAL, through marnoldi_last_error(NULL)): arguments that
+ *     marnoldi_setup or marnoldi_solve would reject on size grounds.
+ */
+int marnoldi_device_bytes(const marnoldi_ctx *ctx, size_t *current, size_t *peak);
+int marnoldi_footprint(int64_t n_block_rows, const int64_t *row_ptr, const uint8_t *orbital_mask,
+                       const double *box, int precision, int nu, int region_atoms,
+                       int64_t batch_columns, size_t *bytes, int64_t *batch_used);
+
+/*
+ * Request server: whole calculations (setup, solve of every real orbital with
+ * the bisection on N_e, density and energy-density matrices, band energy) on
+ * structures of any size and nu, submitted at any time from any thread and run
+ * concurrently on the current CUDA device.
+ *
+ *   marnoldi_server_create(out, workers, hbm_budget_bytes)
+ *     `workers` threads (1..64), each with its own non-blocking stream, take
+ *     requests in submission order.  A request starts when a worker is free and
+ *     its footprint (marnoldi_footprint) fits under hbm_budget_bytes beside the
+ *     footprints of the running requests.  Device memory comes from a pool of
+ *     the server that keeps up to the budget mapped between requests.
+ *   marnoldi_server_submit(...)
+ *     Arguments as marnoldi_setup and marnoldi_solve (mu always by bisection).
+ *     batch_columns 0 = the largest batch whose footprint stays within
+ *     budget / workers (at least one column).  rho_vals, rhoE_vals: host arrays
+ *     of nnzb*16 doubles that receive the density and energy-density matrices
+ *     (both NULL = energy only).  Every array passed must stay valid and
+ *     unchanged until marnoldi_server_wait has returned this request's result.
+ *     Returns MARNOLDI_ENOMEM when the footprint exceeds the whole budget,
+ *     MARNOLDI_EINVAL for arguments the footprint check rejects and for
+ *     kT or electron_count not positive and finite; other input
+ *     errors come back as the request's status.  *request_id > 0 on success.
+ *   marnoldi_server_wait(srv, id, timeout_s, status, result, message, cap)
+ *     Waits up to timeout_s seconds (< 0 = no limit).  MARNOLDI_EPENDING if the
+ *     request is still queued or running (it stays waitable); MARNOLDI_EINVAL
+ *     for an unknown id; else MARNOLDI_OK, and the request's record is
+ *     released after writing (any output may be NULL):
+ *       *status    the request's marnoldi_status,
+ *       result[8]  band energy, mu, N(mu), then the submit, start and end
+ *                  times (seconds on the server's steady clock), the footprint
+ *                  in bytes and the batch size,
+ *       message    the request's error message (empty on success), truncated
+ *                  to cap - 1 characters.
+ *   marnoldi_server_stats(srv, stats[7])
+ *     queued, running, completed, footprint bytes in use, most footprint bytes
+ *     in use at once, most requests running at once, the pool's most reserved
+ *     bytes.
+ *   marnoldi_server_destroy(srv)
+ *     Waits for every submitted request to finish, then frees the workers,
+ *     streams and pool.  Records never waited for are dropped.
+ * Errors of create, submit, wait and stats: marnoldi_server_last_error()
+ * (per calling thread).
+ */
+typedef struct marnoldi_server marnoldi_server;
+int marnoldi_server_create(marnoldi_server **out, int workers, size_t hbm_budget_bytes);
+int marnoldi_server_submit(marnoldi_server *srv, int64_t n_block_rows, const int64_t *row_ptr,
+                           const int32_t *col_idx, const double *H_vals, const double *S_vals,
+                           const uint8_t *orbital_mask, const double *positions, const double *box,
+                           int precision, int nu, int region_atoms, double electron_count, double kT,
+                           int64_t batch_columns, double *rho_vals, double *rhoE_vals,
+                           int64_t *request_id);
+int marnoldi_server_wait(marnoldi_server *srv, int64_t request_id, double timeout_s, int *status,
+                         double *result, char *message, size_t message_cap);
+int marnoldi_server_stats(marnoldi_server *srv, int64_t *stats);
+const char *marnoldi_server_last_error(void);
+void marnoldi_server_destroy(marnoldi_server *srv);
 
 /* Message of the last failure on ctx (or of the last failed setup when ctx is NULL). */
 const char *marnoldi_last_error(const marnoldi_ctx *ctx);

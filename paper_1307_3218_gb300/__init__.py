@@ -4,12 +4,13 @@ The hot path of the mArnoldi method (Hoshi, Yamazaki, Akiyama, arXiv:1307.3218,
 Section 2) runs in libmarnoldi, hand-written CUDA for sm_103a behind the C ABI
 declared in ``include/marnoldi.h``.  This package holds the CUDA sources
 (``csrc/``), their build (``build.py``) and the ctypes binding
-(``marnoldi.py``), whose functions carry the C names, and the host logic that
-splits the columns over ranks with one shared Fermi level (``shard.py``).
+(``marnoldi.py``), whose functions carry the C names (``Server`` wraps the
+request server, ``marnoldi_server_*``), and the host logic that splits the
+columns over ranks with one shared Fermi level (``shard.py``).
 """
 
-from .marnoldi import (MARNOLDI_FP64, MARNOLDI_MIXED, Context, MarnoldiError, load,
-                       marnoldi_column_stats, marnoldi_count_noalloc, marnoldi_density, marnoldi_density_device,
+from .marnoldi import (MARNOLDI_FP64, MARNOLDI_MIXED, Context, MarnoldiError, Server, load,
+                       marnoldi_column_stats, marnoldi_device_bytes, marnoldi_footprint, marnoldi_count_noalloc, marnoldi_density, marnoldi_density_device,
                        marnoldi_destroy, marnoldi_energy, marnoldi_fermi_at, marnoldi_green,
                        marnoldi_kernel_kinds, marnoldi_level_range,
                        marnoldi_kernel_stats, marnoldi_last_error, marnoldi_set_allocator,
@@ -17,8 +18,8 @@ from .marnoldi import (MARNOLDI_FP64, MARNOLDI_MIXED, Context, MarnoldiError, lo
                        marnoldi_solve, marnoldi_solved_shape, setup_system, use_torch_allocator)
 
 __all__ = [
-    "MARNOLDI_FP64", "MARNOLDI_MIXED", "Context", "MarnoldiError", "load",
-    "marnoldi_column_stats", "marnoldi_count_noalloc", "marnoldi_density", "marnoldi_density_device", "marnoldi_destroy",
+    "MARNOLDI_FP64", "MARNOLDI_MIXED", "Context", "MarnoldiError", "Server", "load",
+    "marnoldi_column_stats", "marnoldi_device_bytes", "marnoldi_footprint", "marnoldi_count_noalloc", "marnoldi_density", "marnoldi_density_device", "marnoldi_destroy",
     "marnoldi_energy", "marnoldi_fermi_at", "marnoldi_green", "marnoldi_kernel_kinds",
     "marnoldi_kernel_stats", "marnoldi_level_range",
     "marnoldi_last_error", "marnoldi_set_allocator", "marnoldi_set_batch",

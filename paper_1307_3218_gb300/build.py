@@ -18,7 +18,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
-SOURCES = ["api.cu", "krylov.cu", "eigsub.cu", "outputs.cu", "region.cu", "support.cu", "noalloc.cu"]
+SOURCES = ["api.cu", "krylov.cu", "eigsub.cu", "outputs.cu", "region.cu", "support.cu", "noalloc.cu",
+           "server.cu"]
 HEADERS = [os.path.join(CSRC, "internal.h"), os.path.join(INCLUDE, "marnoldi.h")]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -10,7 +10,9 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
+#include <unordered_map>
 #include <utility>
 #include <vector>
 
@@ -36,6 +38,52 @@ int marnoldi::set_global_error(int code, const char *msg)
     return code;
 }
 
+cudaError_t marnoldi::allow_dynamic_smem(const void *kernel, size_t bytes)
+{
+    static std::mutex mu;
+    static std::unordered_map<const void *, size_t> allowed;
+    std::lock_guard<std::mutex> lock(mu);
+    size_t &cur = allowed[kernel];
+    if (bytes <= cur) return cudaSuccess;
+    const cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess) cur = bytes;
+    return e;
+}
+
+namespace {
+
+// Page-locked read-back slots of four doubles, carved from pages that stay
+// allocated until the process exits, so that creating and destroying a
+// context never calls cudaMallocHost or cudaFreeHost (either may wait for
+// work that other streams have in flight).
+std::mutex g_pin_mu;
+std::vector<double *> g_pin_free;
+
+double *pinned_slot()
+{
+    std::lock_guard<std::mutex> lock(g_pin_mu);
+    if (g_pin_free.empty()) {
+        void *page = nullptr;
+        if (cudaMallocHost(&page, 4096) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        for (int q = 0; q < 4096 / 32; ++q) g_pin_free.push_back((double *)page + 4 * q);
+    }
+    double *slot = g_pin_free.back();
+    g_pin_free.pop_back();
+    return slot;
+}
+
+void pinned_release(double *slot)
+{
+    if (!slot) return;
+    std::lock_guard<std::mutex> lock(g_pin_mu);
+    g_pin_free.push_back(slot);
+}
+
+}  // namespace
+
 struct marnoldi_ctx {
     cudaStream_t stream = nullptr;
     int prec = 0;
@@ -48,6 +96,9 @@ struct marnoldi_ctx {
     marnoldi_alloc_fn alloc = nullptr;
     marnoldi_free_fn free_fn = nullptr;
     void *user = nullptr;
+
+    // device memory: bytes held now and at most since setup
+    size_t dev_bytes = 0, dev_peak = 0;
 
     // device copies of the structure
     DeviceMatrix A{};
@@ -120,12 +171,18 @@ void *dalloc(marnoldi_ctx *c, size_t bytes)
         cudaGetLastError();
         p = nullptr;
     }
+    if (p) {
+        c->dev_bytes += bytes;
+        c->dev_peak = std::max(c->dev_peak, c->dev_bytes);
+    }
     return p;
 }
 
 void dfree(marnoldi_ctx *c, void *p, size_t bytes)
 {
     if (!p) return;
+    if (bytes == 0) bytes = 16;
+    c->dev_bytes -= bytes;
     if (c->free_fn) c->free_fn(p, bytes, (void *)c->stream, c->user);
     else cudaFreeAsync(p, c->stream);
 }
@@ -416,6 +473,125 @@ int find_regions(marnoldi_ctx *c, const KrylovBatch &kb)
     return fail(c, MARNOLDI_ENOCONV, "region search radius did not settle");
 }
 
+size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Device memory of one solve (every piece 256-byte aligned): the per-column
+// state, kept until the next solve, and the batch workspace, kept and only
+// grown across solves.
+struct SolvePlan {
+    size_t o_cols, o_poff, o_nue, o_est, o_eps, o_w, o_t, o_P, state_bytes;
+    int64_t B;
+    ColumnShape shape;
+    size_t vs;
+    bool a_global;
+    EigScratch es;   // sizes and chunk; the caller sets the pointers
+    size_t oK, oSK, oU, oUl, oH, oL, oSc, oC, oS, oN, oRg, oRc, oRi, oRk, oRs, oTh, oTo, oTc;
+    size_t oED, oEE, oERQ, oERot, oESw, oENs, oEA, ws_bytes;
+};
+
+// Workspace bytes per batch column, for the default batch size.
+size_t per_column_bytes(const ColumnShape &shape, size_t vs, int nu, int region_atoms, int maxrow)
+{
+    const size_t reg = region_atoms > 0 ? (size_t)region_atoms * (12 + 8 * (size_t)maxrow) : 0;
+    return al256((size_t)2 * nu * shape.m_pad * vs) + (size_t)2 * shape.m_pad * vs +
+           (size_t)2 * nu * nu * 8 + (size_t)nu * 8 + 64 + reg + (size_t)(shape.m_pad / 32) * 3 +
+           (size_t)(nu + 2) * 4;
+}
+
+// Batch size within [1, ncols] and the launch limits (one CTA per column, or
+// per column pair).
+int64_t clamp_batch(int64_t B, int64_t nc, bool regional)
+{
+    B = std::min<int64_t>(std::max<int64_t>(B, 1), nc);
+    return std::min<int64_t>(B, regional ? 65535 : 65535 * 32);
+}
+
+// Offsets and sizes of a solve of nc columns (prow = rows of the columns'
+// block patterns, 4 per block) in batches of B (already clamped).  Returns
+// false when nu with blocks rows of `maxrow` blocks does not fit the
+// eigensolver's shared memory.
+bool plan_solve(int64_t m_vec, int prec, int nu, int region_atoms, int maxrow, int64_t nc,
+                int64_t prow, int64_t B, SolvePlan &p)
+{
+    const bool regional = region_atoms > 0;
+    p.o_cols = 0;
+    p.o_poff = p.o_cols + al256(nc * 8);
+    p.o_nue = p.o_poff + al256(nc * 8);
+    p.o_est = p.o_nue + al256(nc * 4);
+    p.o_eps = p.o_est + al256(nc * 4);
+    p.o_w = p.o_eps + al256((size_t)nc * nu * 8);
+    p.o_t = p.o_w + al256((size_t)nc * nu * 8);
+    p.o_P = p.o_t + al256((size_t)nc * nu * 8);
+    p.state_bytes = p.o_P + al256((size_t)prow * nu * 8);
+
+    p.B = B;
+    p.shape = column_shape(m_vec, prec);
+    p.vs = prec == 0 ? 8 : 4;
+    const size_t mp = (size_t)p.shape.m_pad, vs = p.vs, nt = mp / 32;
+    const size_t rg = regional ? (size_t)region_atoms : 0;
+    p.oK = 0;
+    p.oSK = p.oK + al256((size_t)B * nu * mp * vs);
+    p.oU = p.oSK + al256((size_t)B * nu * mp * vs);
+    p.oUl = p.oU + al256((size_t)B * mp * vs);
+    p.oH = p.oUl + (prec == 1 ? al256((size_t)B * mp * vs) : 0);
+    p.oL = p.oH + al256((size_t)B * nu * nu * 8);
+    p.oSc = p.oL + al256((size_t)B * nu * nu * 8);
+    p.oC = p.oSc + al256((size_t)B * nu * 8);
+    p.oS = p.oC + al256((size_t)B * 8);
+    p.oN = p.oS + al256((size_t)B * 4);
+    p.oRg = p.oN + al256((size_t)B * 4);
+    p.oRc = p.oRg + (regional ? al256((size_t)B * rg * 4) : 0);
+    p.oRi = p.oRc + (regional ? al256((size_t)B * rg * 4) : 0);
+    p.oRk = p.oRi + (regional ? al256((size_t)B * rg * maxrow * 4) : 0);
+    p.oRs = p.oRk + (regional ? al256((size_t)B * rg * maxrow * 4) : 0);
+    p.oTh = p.oRs + (regional ? al256((size_t)B * 4) : 0);
+    p.oTo = p.oTh + al256((size_t)B * nt);
+    p.oTc = p.oTo + al256((size_t)B * nt * 2);
+    const size_t oEg = p.oTc + al256((size_t)B * (nu + 2) * 4);
+
+    // eigensolve scratch, for chunks of at most es.chunk subspaces; H_sub in
+    // shared memory when it fits, else in a global scratch per subspace
+    EigScratch &es = p.es;
+    es = EigScratch{};
+    es.nr_max = 4 * maxrow + 2;
+    es.rcap = (int64_t)8 * nu * nu;
+    es.scap = (int64_t)40 * nu;
+    const size_t kSmemCap = (size_t)227 * 1024;
+    p.a_global = eig_smem_bytes(nu, es.nr_max, false) > kSmemCap;
+    if (eig_smem_bytes(nu, es.nr_max, p.a_global) > kSmemCap) return false;
+    const size_t a_per_sub = p.a_global ? (size_t)nu * (nu | 1) * 8 : 0;
+    const size_t per_sub = al256((size_t)(2 + es.nr_max) * nu * 8) + al256((size_t)es.rcap * 16) +
+                           al256((size_t)es.scap * 8) + 8 + a_per_sub;
+    es.chunk = (int)std::max<int64_t>(32, std::min<int64_t>(B, (int64_t)(((size_t)3 << 30) / per_sub)));
+    const size_t ceig = (size_t)es.chunk;
+    p.oED = oEg;
+    p.oEE = p.oED + al256(ceig * nu * 8);
+    p.oERQ = p.oEE + al256(ceig * nu * 8);
+    p.oERot = p.oERQ + al256(ceig * es.nr_max * nu * 8);
+    p.oESw = p.oERot + al256(ceig * es.rcap * 16);
+    p.oENs = p.oESw + al256(ceig * es.scap * 8);
+    p.oEA = p.oENs + al256(ceig * 4);
+    p.ws_bytes = p.oEA + al256(ceig * a_per_sub);
+    return true;
+}
+
+// Device bytes that marnoldi_setup allocates for a structure, and that the
+// first regional solve adds (wrapped positions, box, cell list).
+size_t setup_bytes(int64_t nbr, int64_t nnzb, int prec)
+{
+    size_t b = 8 * (size_t)(nbr + 1) + 4 * (size_t)nnzb + 2 * 128 * (size_t)nnzb +
+               8 * 4 * (size_t)nbr + 8 * (size_t)nnzb;           // rp ci H S diag(S) transpose map
+    if (prec == MARNOLDI_MIXED) b += 2 * 128 * (size_t)nnzb;     // hi/lo FP32 copies of H and S
+    return b + (2 * kReduceBlocks + 2) * sizeof(double) + 16;    // reduction scratch
+}
+
+size_t cells_bytes(int64_t nbr, const double *box)
+{
+    int64_t ncells = 1;
+    for (int d = 0; d < 3; ++d) ncells *= (int64_t)std::max(1.0, std::min(256.0, std::floor(box[d] / 2.6)));
+    return 24 * (size_t)nbr + 24 + 4 * (size_t)(ncells + 1) + 4 * (size_t)nbr;
+}
+
 void free_state(marnoldi_ctx *c)
 {
     if (c->state) dfree(c, c->state, c->state_bytes);
@@ -453,7 +629,7 @@ void marnoldi_destroy(marnoldi_ctx *c)
     free_state(c);
     if (c->ws) dfree(c, c->ws, c->ws_bytes);
     for (auto &p : c->owned) dfree(c, p.first, p.second);
-    if (c->h_out) cudaFreeHost(c->h_out);
+    pinned_release(c->h_out);
     for (auto &p : c->pending) {
         c->events.push_back(p.second.first);
         c->events.push_back(p.second.second);
@@ -468,6 +644,71 @@ int marnoldi_setup(marnoldi_ctx **out, int64_t n_block_rows, const int64_t *row_
                    const int32_t *col_idx, const double *H_vals, const double *S_vals,
                    const uint8_t *orbital_mask, const double *positions, const double *box,
                    int precision, void *cuda_stream)
+{
+    return setup_with_allocator(out, n_block_rows, row_ptr, col_idx, H_vals, S_vals, orbital_mask,
+                                positions, box, precision, cuda_stream, g_alloc, g_free, g_user);
+}
+
+int marnoldi_device_bytes(const marnoldi_ctx *c, size_t *current, size_t *peak)
+{
+    if (!c) return MARNOLDI_EINVAL;
+    if (current) *current = c->dev_bytes;
+    if (peak) *peak = c->dev_peak;
+    return MARNOLDI_OK;
+}
+
+int marnoldi_footprint(int64_t n_block_rows, const int64_t *row_ptr, const uint8_t *orbital_mask,
+                       const double *box, int precision, int nu, int region_atoms,
+                       int64_t batch_columns, size_t *bytes, int64_t *batch_used)
+{
+    g_setup_err.clear();
+    if (!bytes) return fail(nullptr, MARNOLDI_EINVAL, "bytes is NULL");
+    if (n_block_rows < 1 || n_block_rows > (int64_t)1 << 30 || !row_ptr)
+        return fail(nullptr, MARNOLDI_EINVAL, "need n_block_rows >= 1 and row_ptr");
+    if (precision != MARNOLDI_FP64 && precision != MARNOLDI_MIXED)
+        return fail(nullptr, MARNOLDI_EINVAL, "unknown precision %d", precision);
+    if (batch_columns < 1) return fail(nullptr, MARNOLDI_EINVAL, "batch_columns must be >= 1");
+    const bool regional = region_atoms > 0;
+    if (region_atoms < 0 || region_atoms > kMaxRegion || region_atoms > n_block_rows || (regional && !box))
+        return fail(nullptr, MARNOLDI_EINVAL, "region_atoms = %d invalid (regional mode needs box)", region_atoms);
+    if (!regional && 4 * n_block_rows > kMaxGlobalM)
+        return fail(nullptr, MARNOLDI_EINVAL, "global mode supports M <= %lld", (long long)kMaxGlobalM);
+    if (nu < 1 || nu > kMaxNu || (regional && nu > 4 * region_atoms))
+        return fail(nullptr, MARNOLDI_EINVAL, "nu = %d out of range", nu);
+    const int64_t nnzb = row_ptr[n_block_rows];
+    int maxrow = 1;
+    int64_t nc = 0, prow = 0;
+    for (int64_t I = 0; I < n_block_rows; ++I) {
+        const int64_t len = row_ptr[I + 1] - row_ptr[I];
+        if (len < 1) return fail(nullptr, MARNOLDI_EINVAL, "block row %lld is empty", (long long)I);
+        maxrow = std::max<int>(maxrow, (int)len);
+        for (int a = 0; a < 4; ++a)
+            if (!orbital_mask || orbital_mask[4 * I + a]) {
+                ++nc;
+                prow += 4 * len;
+            }
+    }
+    if (nc < 1) return fail(nullptr, MARNOLDI_EINVAL, "no real orbitals");
+    const int64_t B = clamp_batch(batch_columns, nc, regional);
+    SolvePlan plan;
+    if (!plan_solve(regional ? 4 * (int64_t)region_atoms : 4 * n_block_rows, precision, nu, region_atoms,
+                    maxrow, nc, prow, B, plan))
+        return fail(nullptr, MARNOLDI_EINVAL, "nu = %d exceeds the eigensolver's shared memory", nu);
+    size_t total = setup_bytes(n_block_rows, nnzb, precision) + plan.state_bytes + plan.ws_bytes +
+                   (size_t)nnzb * 16 * sizeof(double) * 2;   // marnoldi_density's staging
+    if (regional) total += cells_bytes(n_block_rows, box);
+    *bytes = total;
+    if (batch_used) *batch_used = B;
+    return MARNOLDI_OK;
+}
+
+}  // extern "C"
+
+int marnoldi::setup_with_allocator(marnoldi_ctx **out, int64_t n_block_rows, const int64_t *row_ptr,
+                                   const int32_t *col_idx, const double *H_vals, const double *S_vals,
+                                   const uint8_t *orbital_mask, const double *positions, const double *box,
+                                   int precision, void *cuda_stream, marnoldi_alloc_fn alloc,
+                                   marnoldi_free_fn free_fn, void *user)
 {
     g_setup_err.clear();
     if (!out) return fail(nullptr, MARNOLDI_EINVAL, "out is NULL");
@@ -489,9 +730,9 @@ int marnoldi_setup(marnoldi_ctx **out, int64_t n_block_rows, const int64_t *row_
     c->nnzb = nnzb;
     c->m = 4 * n_block_rows;
     c->stream = (cudaStream_t)cuda_stream;
-    c->alloc = g_alloc;
-    c->free_fn = g_free;
-    c->user = g_user;
+    c->alloc = alloc;
+    c->free_fn = alloc ? free_fn : nullptr;
+    c->user = user;
     c->rp.assign(row_ptr, row_ptr + n_block_rows + 1);
     c->ci.assign(col_idx, col_idx + nnzb);
     if (orbital_mask) {
@@ -572,7 +813,7 @@ int marnoldi_setup(marnoldi_ctx **out, int64_t n_block_rows, const int64_t *row_
     c->d_out = c->d_partial + 2 * kReduceBlocks;
     c->d_ticket = (unsigned *)(c->d_out + 2);
     cudaError_t e = cudaMemsetAsync(p, 0, (2 * kReduceBlocks + 2) * sizeof(double) + 16, c->stream);
-    if (e == cudaSuccess) e = cudaMallocHost(&c->h_out, 4 * sizeof(double));
+    if (e == cudaSuccess && !(c->h_out = pinned_slot())) e = cudaErrorMemoryAllocation;
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) {
         fail_cuda(c, e, "setup");
@@ -583,6 +824,8 @@ int marnoldi_setup(marnoldi_ctx **out, int64_t n_block_rows, const int64_t *row_
     *out = c;
     return MARNOLDI_OK;
 }
+
+extern "C" {
 
 int marnoldi_set_batch(marnoldi_ctx *c, int64_t batch_columns)
 {
@@ -701,85 +944,47 @@ int marnoldi_solve(marnoldi_ctx *c, const int64_t *columns, int64_t ncols, int n
         const int64_t J = cols[q] >> 2;
         prow += 4 * (c->rp[J + 1] - c->rp[J]);
     }
-    auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
-    const size_t o_cols = 0, o_poff = o_cols + al(nc * 8), o_nue = o_poff + al(nc * 8),
-                 o_est = o_nue + al(nc * 4), o_eps = o_est + al(nc * 4),
-                 o_w = o_eps + al((size_t)nc * nu * 8), o_t = o_w + al((size_t)nc * nu * 8),
-                 o_P = o_t + al((size_t)nc * nu * 8), total = o_P + al((size_t)prow * nu * 8);
-    c->state = dalloc(c, total);
-    if (!c->state) return fail(c, MARNOLDI_ENOMEM, "device allocation of %zu bytes for column state failed", total);
-    c->state_bytes = total;
+    const int64_t m_vec = regional ? 4 * (int64_t)region_atoms : c->m;
+    int64_t B = c->batch_override;
+    if (B <= 0) {
+        const ColumnShape shape = column_shape(m_vec, c->prec);
+        const size_t per_col = per_column_bytes(shape, c->prec == 0 ? 8 : 4, nu, region_atoms, c->maxrow);
+        size_t freeb = 0, totb = 0;
+        if (cudaMemGetInfo(&freeb, &totb) != cudaSuccess) { cudaGetLastError(); freeb = (size_t)8 << 30; }
+        const size_t budget = std::min<size_t>(freeb / 2, (size_t)48 << 30);
+        B = std::max<int64_t>(1, (int64_t)(budget / per_col));
+    }
+    B = clamp_batch(B, nc, regional);
+    SolvePlan plan;
+    if (!plan_solve(m_vec, c->prec, nu, region_atoms, c->maxrow, nc, prow, B, plan))
+        return fail(c, MARNOLDI_EINVAL, "nu = %d with %d blocks per row exceeds the eigensolver's shared memory",
+                    nu, c->maxrow);
+    c->last_batch = B;
+    c->state = dalloc(c, plan.state_bytes);
+    if (!c->state)
+        return fail(c, MARNOLDI_ENOMEM, "device allocation of %zu bytes for column state failed", plan.state_bytes);
+    c->state_bytes = plan.state_bytes;
     char *sb = (char *)c->state;
-    c->d_cols = (int64_t *)(sb + o_cols);
+    c->d_cols = (int64_t *)(sb + plan.o_cols);
     c->st.ncols = nc;
     c->st.nu = nu;
     c->st.cols = c->d_cols;
-    c->st.p_off = (const int64_t *)(sb + o_poff);
-    c->st.nu_eff = (int *)(sb + o_nue);
-    c->st.eig_status = (int *)(sb + o_est);
-    c->st.eps = (double *)(sb + o_eps);
-    c->st.w = (double *)(sb + o_w);
-    c->st.t = (double *)(sb + o_t);
-    c->st.P = (double *)(sb + o_P);
+    c->st.p_off = (const int64_t *)(sb + plan.o_poff);
+    c->st.nu_eff = (int *)(sb + plan.o_nue);
+    c->st.eig_status = (int *)(sb + plan.o_est);
+    c->st.eps = (double *)(sb + plan.o_eps);
+    c->st.w = (double *)(sb + plan.o_w);
+    c->st.t = (double *)(sb + plan.o_t);
+    c->st.P = (double *)(sb + plan.o_P);
     cudaError_t e = cudaMemcpyAsync(c->d_cols, cols.data(), nc * 8, cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync((void *)c->st.p_off, p_off.data(), nc * 8, cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->st.eig_status, 0, nc * 4, c->stream);
     if (e != cudaSuccess) return fail_cuda(c, e, "column state upload");
 
     // batch workspace
-    const int64_t m_vec = regional ? 4 * (int64_t)region_atoms : c->m;
-    const ColumnShape shape = column_shape(m_vec, c->prec);
-    const size_t vs = c->prec == 0 ? 8 : 4;
-    const size_t reg_per_col = regional ? (size_t)region_atoms * (12 + 8 * (size_t)c->rm.maxrow) : 0;
-    const size_t per_col = al((size_t)2 * nu * shape.m_pad * vs) + (size_t)2 * shape.m_pad * vs +
-                           (size_t)2 * nu * nu * 8 + (size_t)nu * 8 + 64 + reg_per_col +
-                           (size_t)(shape.m_pad / 32) * 3 + (size_t)(nu + 2) * 4;
-    int64_t B = c->batch_override;
-    if (B <= 0) {
-        size_t freeb = 0, totb = 0;
-        if (cudaMemGetInfo(&freeb, &totb) != cudaSuccess) { cudaGetLastError(); freeb = (size_t)8 << 30; }
-        const size_t budget = std::min<size_t>(freeb / 2, (size_t)48 << 30);
-        B = std::max<int64_t>(1, (int64_t)(budget / per_col));
-    }
-    B = std::min<int64_t>(B, nc);
-    B = std::min<int64_t>(B, regional ? 65535 : 65535 * 32);
-    c->last_batch = B;
-    const size_t oK = 0, oSK = oK + al((size_t)B * nu * shape.m_pad * vs),
-                 oU = oSK + al((size_t)B * nu * shape.m_pad * vs),
-                 oUl = oU + al((size_t)B * shape.m_pad * vs),
-                 oH = oUl + (c->prec == 1 ? al((size_t)B * shape.m_pad * vs) : 0),
-                 oL = oH + al((size_t)B * nu * nu * 8),
-                 oSc = oL + al((size_t)B * nu * nu * 8),
-                 oC = oSc + al((size_t)B * nu * 8), oS = oC + al((size_t)B * 8),
-                 oN = oS + al((size_t)B * 4), oRg = oN + al((size_t)B * 4),
-                 oRc = oRg + (regional ? al((size_t)B * region_atoms * 4) : 0),
-                 oRi = oRc + (regional ? al((size_t)B * region_atoms * 4) : 0),
-                 oRk = oRi + (regional ? al((size_t)B * region_atoms * c->rm.maxrow * 4) : 0),
-                 oRs = oRk + (regional ? al((size_t)B * region_atoms * c->rm.maxrow * 4) : 0),
-                 oTh = oRs + (regional ? al((size_t)B * 4) : 0),
-                 oTo = oTh + al((size_t)B * (shape.m_pad / 32)),
-                 oTc = oTo + al((size_t)B * (shape.m_pad / 32) * 2),
-                 oEg = oTc + al((size_t)B * (nu + 2) * 4);
-    // eigensolve scratch, for chunks of at most ceig subspaces
-    EigScratch es;
-    es.nr_max = 4 * c->maxrow + 2;
-    es.rcap = (int64_t)8 * nu * nu;
-    es.scap = (int64_t)40 * nu;
-    // H_sub in shared memory when it fits, else in a global scratch per subspace
-    const size_t kSmemCap = (size_t)227 * 1024;
-    const bool a_global = eig_smem_bytes(nu, es.nr_max, false) > kSmemCap;
-    if (eig_smem_bytes(nu, es.nr_max, a_global) > kSmemCap)
-        return fail(c, MARNOLDI_EINVAL, "nu = %d with %d blocks per row exceeds the eigensolver's shared memory",
-                    nu, c->maxrow);
-    const size_t a_per_sub = a_global ? (size_t)nu * (nu | 1) * 8 : 0;
-    const size_t per_sub = al((size_t)(2 + es.nr_max) * nu * 8) + al((size_t)es.rcap * 16) +
-                           al((size_t)es.scap * 8) + 8 + a_per_sub;
-    es.chunk = (int)std::max<int64_t>(32, std::min<int64_t>(B, (int64_t)(((size_t)3 << 30) / per_sub)));
-    const size_t ceig = (size_t)es.chunk;
-    const size_t oED = oEg, oEE = oED + al(ceig * nu * 8), oERQ = oEE + al(ceig * nu * 8),
-                 oERot = oERQ + al(ceig * es.nr_max * nu * 8), oESw = oERot + al(ceig * es.rcap * 16),
-                 oENs = oESw + al(ceig * es.scap * 8), oEA = oENs + al(ceig * 4),
-                 wtot = oEA + al(ceig * a_per_sub);
+    const ColumnShape shape = plan.shape;
+    const size_t vs = plan.vs;
+    const size_t wtot = plan.ws_bytes;
     if (c->ws_bytes < wtot) {
         if (c->ws) dfree(c, c->ws, c->ws_bytes);
         c->ws = dalloc(c, wtot);
@@ -793,37 +998,37 @@ int marnoldi_solve(marnoldi_ctx *c, const int64_t *columns, int64_t ncols, int n
     KrylovBatch kb{};
     kb.prec = c->prec;
     kb.nu = nu;
-    kb.m = c->m;
     kb.shape = shape;
-    kb.K = wb + oK;
-    kb.SK = wb + oSK;
-    kb.U = wb + oU;
-    kb.Ulo = c->prec == 1 ? (void *)(wb + oUl) : nullptr;
-    kb.Hsub = (double *)(wb + oH);
-    kb.Lsub = (double *)(wb + oL);
-    kb.scale = (double *)(wb + oSc);
-    kb.cn2 = (double *)(wb + oC);
-    kb.status = (int *)(wb + oS);
-    kb.nu_eff = (int *)(wb + oN);
+    kb.K = wb + plan.oK;
+    kb.SK = wb + plan.oSK;
+    kb.U = wb + plan.oU;
+    kb.Ulo = c->prec == 1 ? (void *)(wb + plan.oUl) : nullptr;
+    kb.Hsub = (double *)(wb + plan.oH);
+    kb.Lsub = (double *)(wb + plan.oL);
+    kb.scale = (double *)(wb + plan.oSc);
+    kb.cn2 = (double *)(wb + plan.oC);
+    kb.status = (int *)(wb + plan.oS);
+    kb.nu_eff = (int *)(wb + plan.oN);
     kb.m = m_vec;
     kb.ntile = (int)(shape.m_pad / 32);
-    kb.thop = (uint8_t *)(wb + oTh);
-    kb.tinv = (uint16_t *)(wb + oTo);
-    kb.tcnt = (int *)(wb + oTc);
-    es.D = (double *)(wb + oED);
-    es.E = (double *)(wb + oEE);
-    es.RQ = (double *)(wb + oERQ);
-    es.rot = (double2 *)(wb + oERot);
-    es.sweep = (int2 *)(wb + oESw);
-    es.nsweep = (int *)(wb + oENs);
-    es.Ag = a_global ? (double *)(wb + oEA) : nullptr;
+    kb.thop = (uint8_t *)(wb + plan.oTh);
+    kb.tinv = (uint16_t *)(wb + plan.oTo);
+    kb.tcnt = (int *)(wb + plan.oTc);
+    EigScratch es = plan.es;
+    es.D = (double *)(wb + plan.oED);
+    es.E = (double *)(wb + plan.oEE);
+    es.RQ = (double *)(wb + plan.oERQ);
+    es.rot = (double2 *)(wb + plan.oERot);
+    es.sweep = (int2 *)(wb + plan.oESw);
+    es.nsweep = (int *)(wb + plan.oENs);
+    es.Ag = plan.a_global ? (double *)(wb + plan.oEA) : nullptr;
     RegionMaps *rmp = nullptr;
     if (regional) {
-        c->rm.reg = (int *)(wb + oRg);
-        c->rm.lcnt = (int *)(wb + oRc);
-        c->rm.lci = (int *)(wb + oRi);
-        c->rm.lgk = (int *)(wb + oRk);
-        c->rm.rstat = (int *)(wb + oRs);
+        c->rm.reg = (int *)(wb + plan.oRg);
+        c->rm.lcnt = (int *)(wb + plan.oRc);
+        c->rm.lci = (int *)(wb + plan.oRi);
+        c->rm.lgk = (int *)(wb + plan.oRk);
+        c->rm.rstat = (int *)(wb + plan.oRs);
         rmp = &c->rm;
     }
     const double tau = c->prec == 0 ? kTauFp64 : kTauMixed;
@@ -902,8 +1107,9 @@ int marnoldi_solve(marnoldi_ctx *c, const int64_t *columns, int64_t ncols, int n
     }
     if ((rc = sync(c, "solve"))) return rc;
     std::vector<int> est(nc);
-    e = cudaMemcpy(est.data(), c->st.eig_status, nc * 4, cudaMemcpyDeviceToHost);
+    e = cudaMemcpyAsync(est.data(), c->st.eig_status, nc * 4, cudaMemcpyDeviceToHost, c->stream);
     if (e != cudaSuccess) return fail_cuda(c, e, "status read-back");
+    if ((rc = sync(c, "status read-back"))) return rc;
     c->ncols = nc;
     c->nu = nu;
     c->cols = std::move(cols);
@@ -1030,11 +1236,11 @@ int marnoldi_column_stats(marnoldi_ctx *c, int32_t *nu_eff, double *eps, double 
     if (rc) return rc;
     cudaError_t e = cudaSuccess;
     const size_t n = (size_t)c->ncols * c->nu;
-    if (nu_eff) e = cudaMemcpy(nu_eff, c->st.nu_eff, c->ncols * 4, cudaMemcpyDeviceToHost);
-    if (e == cudaSuccess && eps) e = cudaMemcpy(eps, c->st.eps, n * 8, cudaMemcpyDeviceToHost);
-    if (e == cudaSuccess && w) e = cudaMemcpy(w, c->st.w, n * 8, cudaMemcpyDeviceToHost);
+    if (nu_eff) e = cudaMemcpyAsync(nu_eff, c->st.nu_eff, c->ncols * 4, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess && eps) e = cudaMemcpyAsync(eps, c->st.eps, n * 8, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess && w) e = cudaMemcpyAsync(w, c->st.w, n * 8, cudaMemcpyDeviceToHost, c->stream);
     if (e != cudaSuccess) return fail_cuda(c, e, "column stats read-back");
-    return MARNOLDI_OK;
+    return sync(c, "column stats read-back");
 }
 
 }  // extern "C"

@@ -424,13 +424,8 @@ cudaError_t tridiag_dispatch(const DeviceMatrix &A, const KrylovBatch &b, const 
 {
     const int nu = b.nu;
     const size_t smem = eig_tridiag_smem(nu, es.nr_max, es.Ag != nullptr);
-    static size_t configured = 0;
-    if (smem > configured) {
-        cudaError_t e = cudaFuncSetAttribute(eig_tridiag_kernel<VT>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        configured = smem;
-    }
+    cudaError_t e = allow_dynamic_smem((const void *)eig_tridiag_kernel<VT>, smem);
+    if (e != cudaSuccess) return e;
     eig_tridiag_kernel<VT><<<nb2, kTriThreads, smem, s>>>(
         b.Hsub, b.nu_eff, b.scale, (const VT *)b.K, b.shape.m_pad, b.tinv, b.nb, nu, b.cols, A.rp, A.ci,
         rm ? rm->reg : nullptr, rm ? rm->n_reg : 0, cofs, es.D, es.E, es.RQ, es.nr_max, es.Ag, b.Lsub);
@@ -460,20 +455,10 @@ cudaError_t launch_eig(const DeviceMatrix &A, const KrylovBatch &b, const Column
     const int nu = b.nu, ldr = nu | 1;
     const size_t qsmem = (size_t)2 * nu * 32 * sizeof(double);
     const size_t asmem = (size_t)es.nr_max * ldr * sizeof(double) + (size_t)nu * (sizeof(double) + sizeof(int));
-    static size_t qconf = 0, aconf = 0;
     cudaError_t e;
-    if (qsmem > qconf) {
-        if ((e = cudaFuncSetAttribute(eig_ql_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)qsmem)) != cudaSuccess)
-            return e;
-        qconf = qsmem;
-    }
-    if (asmem > aconf) {
-        if ((e = cudaFuncSetAttribute(eig_apply_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)asmem)) != cudaSuccess)
-            return e;
-        aconf = asmem;
-    }
+    if ((e = allow_dynamic_smem((const void *)eig_ql_kernel, qsmem)) != cudaSuccess ||
+        (e = allow_dynamic_smem((const void *)eig_apply_kernel, asmem)) != cudaSuccess)
+        return e;
     for (int cofs = 0; cofs < b.nb; cofs += es.chunk) {
         const int nb2 = b.nb - cofs < es.chunk ? b.nb - cofs : es.chunk;
         e = b.prec == 0 ? tridiag_dispatch<double>(A, b, rm, es, cofs, nb2, s)

@@ -6,6 +6,8 @@
 #include <cstddef>
 #include <cstdint>
 
+#include "marnoldi.h"
+
 namespace marnoldi {
 
 // Kernel kinds, for launch counting and optional event timing.
@@ -29,6 +31,19 @@ const char *kernel_name(int kind);
 
 // Record the message that marnoldi_last_error(NULL) returns; returns `code`.
 int set_global_error(int code, const char *msg);
+
+// marnoldi_setup with the context's own device allocator in place of the
+// process-wide hook (the request server draws each request's memory from its
+// own pool).  alloc == NULL selects cudaMallocAsync / cudaFreeAsync.
+int setup_with_allocator(marnoldi_ctx **out, int64_t n_block_rows, const int64_t *row_ptr,
+                         const int32_t *col_idx, const double *H_vals, const double *S_vals,
+                         const uint8_t *orbital_mask, const double *positions, const double *box,
+                         int precision, void *cuda_stream, marnoldi_alloc_fn alloc,
+                         marnoldi_free_fn free_fn, void *user);
+
+// Let `kernel` launch with up to `bytes` of dynamic shared memory.  The limit
+// only grows, and callers on several threads may race: one lock orders them.
+cudaError_t allow_dynamic_smem(const void *kernel, size_t bytes);
 
 // Largest subspace dimension.  Up to about 110 the subspace matrix of the
 // eigensolve sits in shared memory, above that in a global scratch.

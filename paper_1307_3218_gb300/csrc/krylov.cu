@@ -692,13 +692,8 @@ cudaError_t gs_dispatch(const KrylovBatch &b, int n, int need_w, double tau, cud
     if (b.shape.m_pad != (int64_t)VPT * T || b.ntile != VPT * T / 32 || !b.tcnt || !b.Lsub)
         return cudaErrorInvalidValue;
     const size_t smem = (size_t)VPT * T * sizeof(VT) * Cfg::kSmemVectors;
-    static bool configured = false;
-    if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(gs_kernel<VT, VPT, T>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        configured = true;
-    }
+    cudaError_t e = allow_dynamic_smem((const void *)gs_kernel<VT, VPT, T>, smem);
+    if (e != cudaSuccess) return e;
     gs_kernel<VT, VPT, T><<<b.nb, T, smem, s>>>(
         (VT *)b.K, (VT *)b.SK, (const VT *)b.U, (const VT *)b.Ulo, b.Hsub, b.Lsub, b.scale, b.cn2,
         b.status, b.nu_eff, b.tcnt, n, b.nu, need_w, tau * tau);

@@ -295,13 +295,8 @@ cudaError_t launch_region(const RegionMaps &rm, const KrylovBatch &b, double rs,
     const int hx = (int)ceil(rs / rm.cell_edge[0]), hy = (int)ceil(rs / rm.cell_edge[1]),
               hz = (int)ceil(rs / rm.cell_edge[2]);
     const size_t smem = (size_t)cap * (sizeof(double) + sizeof(int));
-    static bool configured = false;
-    if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(region_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)((size_t)kRegionCap * (sizeof(double) + sizeof(int))));
-        if (e != cudaSuccess) return e;
-        configured = true;
-    }
+    cudaError_t e = allow_dynamic_smem((const void *)region_kernel, smem);
+    if (e != cudaSuccess) return e;
     region_kernel<<<b.nb, 1024, smem, s>>>(rm.pos, rm.box, rm.cell_start, rm.cell_atoms,
                                            make_int3(rm.ncell[0], rm.ncell[1], rm.ncell[2]),
                                            rm.cell_edge[0], rm.cell_edge[1], rm.cell_edge[2],

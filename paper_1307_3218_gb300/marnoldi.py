@@ -29,11 +29,12 @@ MARNOLDI_ECUDA = -4
 MARNOLDI_ETIMEOUT = -5
 MARNOLDI_ESTATE = -6
 MARNOLDI_ENOCONV = -7
+MARNOLDI_EPENDING = -8
 MARNOLDI_FP64 = 0
 MARNOLDI_MIXED = 1
 
 STATUS_NAMES = {0: "OK", -1: "EINVAL", -2: "ENOTSPD", -3: "ENOMEM", -4: "ECUDA", -5: "ETIMEOUT",
-                -6: "ESTATE", -7: "ENOCONV"}
+                -6: "ESTATE", -7: "ENOCONV", -8: "EPENDING"}
 
 _LIB = None
 _ALLOC_CB = None     # keep the ctypes callbacks alive
@@ -87,6 +88,15 @@ def load(path: str | None = None):
         "marnoldi_kernel_stats": (i32, [P, i32, C.POINTER(C.c_char_p), C.POINTER(i64),
                                         C.POINTER(d), i32]),
         "marnoldi_count_noalloc": (i32, [P, P, P, i64, i32, d, d, P, P]),
+        "marnoldi_device_bytes": (i32, [P, P, P]),
+        "marnoldi_footprint": (i32, [i64, P, P, P, i32, i32, i32, i64, P, P]),
+        "marnoldi_server_create": (i32, [C.POINTER(P), i32, C.c_size_t]),
+        "marnoldi_server_submit": (i32, [P, i64, P, P, P, P, P, P, P, i32, i32, i32, d, d, i64, P, P,
+                                         P]),
+        "marnoldi_server_wait": (i32, [P, i64, d, P, P, P, C.c_size_t]),
+        "marnoldi_server_stats": (i32, [P, P]),
+        "marnoldi_server_last_error": (C.c_char_p, []),
+        "marnoldi_server_destroy": (None, [P]),
         "marnoldi_last_error": (C.c_char_p, [P]),
         "marnoldi_destroy": (None, [P]),
     }
@@ -357,3 +367,137 @@ def marnoldi_destroy(ctx: Context) -> None:
     if ctx is not None and ctx.handle is not None and ctx.handle.value:
         load().marnoldi_destroy(ctx.handle)
         ctx.handle = C.c_void_p(None)
+
+
+def marnoldi_device_bytes(ctx: Context) -> tuple[int, int]:
+    """(bytes held now, most bytes held since setup) of a context's device memory."""
+    cur, peak = C.c_size_t(), C.c_size_t()
+    _check(load().marnoldi_device_bytes(ctx.handle, C.byref(cur), C.byref(peak)), ctx)
+    return cur.value, peak.value
+
+
+def marnoldi_footprint(n_block_rows: int, row_ptr, orbital_mask=None, box=None,
+                       precision: int = MARNOLDI_FP64, nu: int = 30, region_atoms: int = 0,
+                       batch_columns: int = 1 << 40) -> tuple[int, int]:
+    """(peak device bytes, batch used) of setup + solve of every real orbital + density."""
+    rp = np.ascontiguousarray(row_ptr, dtype=np.int64)
+    if rp.size != n_block_rows + 1:
+        raise MarnoldiError(MARNOLDI_EINVAL, "row_ptr must have n_block_rows + 1 entries")
+    mask = None if orbital_mask is None else np.ascontiguousarray(orbital_mask, dtype=np.uint8)
+    bx = None if box is None else np.ascontiguousarray(box, dtype=np.float64)
+    nbytes, used = C.c_size_t(), C.c_int64()
+    _check(load().marnoldi_footprint(int(n_block_rows), _ptr(rp), _ptr(mask), _ptr(bx), int(precision),
+                                     int(nu), int(region_atoms), int(batch_columns), C.byref(nbytes),
+                                     C.byref(used)))
+    return nbytes.value, used.value
+
+
+class ServerError(MarnoldiError):
+    pass
+
+
+def _server_check(rc: int):
+    if rc != MARNOLDI_OK:
+        msg = load().marnoldi_server_last_error()
+        raise ServerError(rc, msg.decode() if msg else "")
+
+
+class Server:
+    """``marnoldi_server``: whole calculations queued and run concurrently on the current GPU.
+
+    ``submit`` returns a request id at once; ``wait`` returns its result.  The
+    arrays of a request are kept referenced here until it has been waited for,
+    as the C API requires.
+    """
+
+    def __init__(self, workers: int = 4, hbm_budget_bytes: int = 32 << 30):
+        L = load()
+        out = C.c_void_p()
+        _server_check(L.marnoldi_server_create(C.byref(out), int(workers), int(hbm_budget_bytes)))
+        self.handle = out
+        self._held: dict[int, tuple] = {}
+
+    def submit(self, n_block_rows: int, row_ptr, col_idx, H_vals, S_vals, orbital_mask=None,
+               positions=None, box=None, precision: int = MARNOLDI_FP64, nu: int = 30,
+               region_atoms: int = 0, electron_count: float = 0.0, kT: float = 0.1,
+               batch_columns: int = 0, density: bool = True) -> int:
+        rp = np.ascontiguousarray(row_ptr, dtype=np.int64)
+        ci = np.ascontiguousarray(col_idx, dtype=np.int32)
+        H = np.ascontiguousarray(H_vals, dtype=np.float64)
+        S = np.ascontiguousarray(S_vals, dtype=np.float64)
+        mask = None if orbital_mask is None else np.ascontiguousarray(orbital_mask, dtype=np.uint8)
+        pos = None if positions is None else np.ascontiguousarray(positions, dtype=np.float64)
+        bx = None if box is None else np.ascontiguousarray(box, dtype=np.float64)
+        if rp.size != n_block_rows + 1:
+            raise ServerError(MARNOLDI_EINVAL, "row_ptr must have n_block_rows + 1 entries")
+        nnzb = int(rp[-1])
+        if ci.size != nnzb or H.size != 16 * nnzb or S.size != 16 * nnzb:
+            raise ServerError(MARNOLDI_EINVAL, "col_idx / H_vals / S_vals sizes do not match row_ptr")
+        if mask is not None and mask.size != 4 * n_block_rows:
+            raise ServerError(MARNOLDI_EINVAL, "orbital_mask must have 4 n_block_rows entries")
+        rho = np.empty((nnzb, 4, 4)) if density else None
+        rhoE = np.empty((nnzb, 4, 4)) if density else None
+        rid = C.c_int64()
+        _server_check(load().marnoldi_server_submit(
+            self.handle, int(n_block_rows), _ptr(rp), _ptr(ci), _ptr(H), _ptr(S), _ptr(mask), _ptr(pos),
+            _ptr(bx), int(precision), int(nu), int(region_atoms), float(electron_count), float(kT),
+            int(batch_columns), _ptr(rho), _ptr(rhoE), C.byref(rid)))
+        self._held[rid.value] = (rp, ci, H, S, mask, pos, bx, rho, rhoE)
+        return rid.value
+
+    def submit_system(self, sysm, precision: int = MARNOLDI_FP64, nu: int = 30, region_atoms: int = 0,
+                      electron_count: float | None = None, kT: float = 0.1, batch_columns: int = 0,
+                      density: bool = True) -> int:
+        """submit for a tbsynth.TBSystem-like object (N_e defaults to its n_electrons)."""
+        s = getattr(sysm, "structure", None)
+        if electron_count is None:
+            electron_count = sysm.n_electrons
+        return self.submit(sysm.n_block_rows, sysm.row_ptr, sysm.col_idx, sysm.H, sysm.S,
+                           sysm.orbital_mask, None if s is None else s.positions,
+                           None if s is None else s.box, precision, nu, region_atoms,
+                           electron_count, kT, batch_columns, density)
+
+    def wait(self, request_id: int, timeout_s: float = -1.0) -> dict | None:
+        """The request's result, or None while it is still pending after timeout_s.
+
+        Raises MarnoldiError with the request's own status if it failed.
+        """
+        st = C.c_int()
+        res = np.zeros(8)
+        msg = C.create_string_buffer(512)
+        rc = load().marnoldi_server_wait(self.handle, int(request_id), float(timeout_s), C.byref(st),
+                                         _ptr(res), msg, 512)
+        if rc == MARNOLDI_EPENDING:
+            return None
+        _server_check(rc)
+        held = self._held.pop(int(request_id))
+        if st.value != MARNOLDI_OK:
+            raise MarnoldiError(st.value, msg.value.decode())
+        return {"band_energy": res[0], "mu": res[1], "N": res[2], "t_submit": res[3],
+                "t_start": res[4], "t_end": res[5], "latency_s": res[5] - res[3],
+                "footprint_bytes": int(res[6]), "batch": int(res[7]), "rho": held[7], "rhoE": held[8]}
+
+    def stats(self) -> dict:
+        v = np.zeros(7, np.int64)
+        _server_check(load().marnoldi_server_stats(self.handle, _ptr(v)))
+        keys = ("queued", "running", "completed", "bytes_in_use", "peak_bytes", "peak_running",
+                "pool_reserved_high")
+        return {k: int(x) for k, x in zip(keys, v)}
+
+    def close(self) -> None:
+        if self.handle is not None and self.handle.value:
+            load().marnoldi_server_destroy(self.handle)
+            self.handle = C.c_void_p(None)
+            self._held.clear()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
