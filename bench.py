@@ -63,6 +63,8 @@ def parse():
     p.add_argument("--no-extra", action="store_true",
                    help="skip the nu=100 and regional side measurements")
     p.add_argument("--no-serving", action="store_true", help="skip the request-server measurement")
+    p.add_argument("--fixed-shapes", action="store_true",
+                   help="fixed Gram-Schmidt launch-shape rule instead of the autotuner")
     p.add_argument("--serve-requests", type=int, default=60)
     p.add_argument("--serve-workers", type=int, default=4)
     p.add_argument("--serve-budget-gb", type=float, default=64.0)
@@ -386,6 +388,7 @@ def main():
     if world > 1:
         torch.distributed.init_process_group("nccl", device_id=dev)
     m.load()
+    m.marnoldi_set_autotune(0 if args.fixed_shapes else 1)
     t, cols = workload(args)
     ncols = len(cols)
     prec = 1 if args.precision == "mixed" else 0
@@ -448,6 +451,7 @@ def main():
         "config": {"workload": workload_name(args, t, ncols), "precision": args.precision,
                    "nu": args.nu, "columns": ncols, "atoms": t.n_block_rows, "M": t.M,
                    "nnzb": t.nnzb, "mode": mode_name(args),
+                   "gs_shape_rule": "fixed" if args.fixed_shapes else "autotuned",
                    "l2": f"flushed between timed steps ({L2_FLUSH_BYTES >> 20} MB write)",
                    "parallelism": f"{world} independent replica(s)" if world > 1 else "1 GPU"},
         "roofline": roof,
@@ -553,10 +557,21 @@ def serving(m, t4096, requests: int, workers: int, budget: int, prec: int):
     ncols_total = sum(pool[n].real_columns().size for n, _ in trace)
     torch.cuda.synchronize()
     torch.cuda.empty_cache()
+    # every (size, nu) once before the timed passes: kernel loading and, with
+    # the autotuner on, the one-time shape tuning of each key
+    shapes = {}
+    with m.Server(workers=1, hbm_budget_bytes=budget) as srv:
+        for n, nu in sorted(set(trace)):
+            srv.wait(srv.submit_system(pool[n], prec, nu, 0, pool[n].n_electrons, 0.1))
+    for n, nu in sorted(set(trace)):
+        ctx = m.setup_system(pool[n], prec)
+        m.marnoldi_solve(ctx, pool[n].real_columns()[:1], nu, 0, 0.0, 0.1, mu_fixed=0.0)
+        shapes[f"{n}_atoms_nu{nu}"] = "x".join(map(str, m.marnoldi_gs_shape(ctx)))
+        m.marnoldi_destroy(ctx)
 
     def run(nworkers, gaps=None):
         with m.Server(workers=nworkers, hbm_budget_bytes=budget) as srv:
-            # warm the pool and the kernels once
+            # warm the server's memory pool once
             srv.wait(srv.submit_system(pool[512], prec, 30, 0, pool[512].n_electrons, 0.1))
             ids, t0 = [], time.perf_counter()
             for k, (n, nu) in enumerate(trace):
@@ -585,6 +600,7 @@ def serving(m, t4096, requests: int, workers: int, budget: int, prec: int):
                  f"nu 30 (nu 100 for 1/4 of those <= 1024 atoms), {'mixed' if prec else 'fp64'}, "
                  f"all real orbitals, density matrices returned to the host",
         "columns": int(ncols_total), "workers": workers, "hbm_budget_gb": round(budget / 2**30, 1),
+        "gs_shapes": shapes,
         "sequential": {"wall_s": round(seq["wall"], 3), "columns_per_s": round(ncols_total / seq["wall"], 1)},
         "concurrent": {"wall_s": round(burst["wall"], 3),
                        "columns_per_s": round(ncols_total / burst["wall"], 1),

@@ -205,6 +205,25 @@ int marnoldi_kernel_stats(marnoldi_ctx *ctx, int kind, const char **name, int64_
                           double *ms, int reset);
 
 /*
+ * Launch-shape autotuner of the Gram-Schmidt kernel (process-wide).
+ *   marnoldi_set_autotune: mode 0 (default, also when MARNOLDI_AUTOTUNE is
+ *     unset or not "1") uses a fixed rule: 256 threads per CTA up to m = 4096,
+ *     512 for FP32 vectors up to 8192, else 1024, values per thread covering m.
+ *     Mode 1: the first solve of each (precision, nu, global/regional, padded
+ *     vector length) times every shape with the same padded length (threads
+ *     256, 512 or 1024) on its first 1,216 columns, keeps the fastest for the
+ *     rest of the process and, when MARNOLDI_TUNE_CACHE names a file, appends
+ *     it there and reads earlier choices from it.  Shapes change the order of
+ *     the kernel's partial sums, so results may differ by rounding between
+ *     shapes (within the solve's accuracy); a shape once chosen stays fixed.
+ *     MARNOLDI_EINVAL for other modes.
+ *   marnoldi_gs_shape: values per thread and threads per CTA of the last solve
+ *     (0, 0 before the first).
+ */
+int marnoldi_set_autotune(int mode);
+int marnoldi_gs_shape(const marnoldi_ctx *ctx, int *values_per_thread, int *threads);
+
+/*
  * Electron count and band energy at a given mu over subspace levels already in
  * device memory, without allocating any device memory.  The paper has no
  * counterpart: this is a variant of the bisection's reduction for callers that

@@ -10,7 +10,8 @@ columns over ranks with one shared Fermi level (``shard.py``).
 """
 
 from .marnoldi import (MARNOLDI_FP64, MARNOLDI_MIXED, Context, MarnoldiError, Server, load,
-                       marnoldi_column_stats, marnoldi_device_bytes, marnoldi_footprint, marnoldi_count_noalloc, marnoldi_density, marnoldi_density_device,
+                       marnoldi_column_stats, marnoldi_device_bytes, marnoldi_footprint, marnoldi_gs_shape,
+                       marnoldi_set_autotune, marnoldi_count_noalloc, marnoldi_density, marnoldi_density_device,
                        marnoldi_destroy, marnoldi_energy, marnoldi_fermi_at, marnoldi_green,
                        marnoldi_kernel_kinds, marnoldi_level_range,
                        marnoldi_kernel_stats, marnoldi_last_error, marnoldi_set_allocator,
@@ -19,7 +20,8 @@ from .marnoldi import (MARNOLDI_FP64, MARNOLDI_MIXED, Context, MarnoldiError, Se
 
 __all__ = [
     "MARNOLDI_FP64", "MARNOLDI_MIXED", "Context", "MarnoldiError", "Server", "load",
-    "marnoldi_column_stats", "marnoldi_device_bytes", "marnoldi_footprint", "marnoldi_count_noalloc", "marnoldi_density", "marnoldi_density_device", "marnoldi_destroy",
+    "marnoldi_column_stats", "marnoldi_device_bytes", "marnoldi_footprint", "marnoldi_gs_shape",
+    "marnoldi_set_autotune", "marnoldi_count_noalloc", "marnoldi_density", "marnoldi_density_device", "marnoldi_destroy",
     "marnoldi_energy", "marnoldi_fermi_at", "marnoldi_green", "marnoldi_kernel_kinds",
     "marnoldi_kernel_stats", "marnoldi_level_range",
     "marnoldi_last_error", "marnoldi_set_allocator", "marnoldi_set_batch",

@@ -10,8 +10,10 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <string>
+#include <tuple>
 #include <unordered_map>
 #include <utility>
 #include <vector>
@@ -27,8 +29,14 @@ thread_local std::string g_setup_err;
 
 constexpr double kTauFp64 = 1e-10;
 constexpr double kTauMixed = 1e-5;
-constexpr double kBisectRtol = 1e-12;
-constexpr int kBisectMaxit = 200;
+
+// Reduction scratch of a context: partial sums, the reduction output, the
+// level range, the bisection state and the reductions' ticket.
+constexpr size_t kOffOut = 2 * kReduceBlocks * sizeof(double);
+constexpr size_t kOffRange = kOffOut + 2 * sizeof(double);
+constexpr size_t kOffBisect = kOffRange + 2 * sizeof(double);
+constexpr size_t kOffTicket = kOffBisect + ((sizeof(BisectState) + 15) & ~(size_t)15);
+constexpr size_t kScratchBytes = kOffTicket + 16;
 
 }  // namespace
 
@@ -52,7 +60,7 @@ cudaError_t marnoldi::allow_dynamic_smem(const void *kernel, size_t bytes)
 
 namespace {
 
-// Page-locked read-back slots of four doubles, carved from pages that stay
+// Page-locked read-back slots of 128 bytes, carved from pages that stay
 // allocated until the process exits, so that creating and destroying a
 // context never calls cudaMallocHost or cudaFreeHost (either may wait for
 // work that other streams have in flight).
@@ -68,7 +76,7 @@ double *pinned_slot()
             cudaGetLastError();
             return nullptr;
         }
-        for (int q = 0; q < 4096 / 32; ++q) g_pin_free.push_back((double *)page + 4 * q);
+        for (int q = 0; q < 4096 / 128; ++q) g_pin_free.push_back((double *)page + 16 * q);
     }
     double *slot = g_pin_free.back();
     g_pin_free.pop_back();
@@ -80,6 +88,75 @@ void pinned_release(double *slot)
     if (!slot) return;
     std::lock_guard<std::mutex> lock(g_pin_mu);
     g_pin_free.push_back(slot);
+}
+
+}  // namespace
+
+namespace {
+
+// ---- autotuner of the Gram-Schmidt launch shape.  Shapes with the same
+// m_pad differ in threads per CTA and values per thread; the choice changes
+// the order of the kernel's partial sums (so results by rounding) and its
+// speed.  Mode 0 (default): the fixed rule of column_shape.  Mode 1: the first
+// solve of a (precision, nu, mode, m_pad) key times every candidate on its
+// first kTuneColumns columns and keeps the fastest for the process; with
+// MARNOLDI_TUNE_CACHE=<file> the choices are read from and appended to that
+// file, so later processes reuse them.
+constexpr int64_t kTuneColumns = 1216;   // 8 CTAs per SM on 152 SMs
+
+struct TuneKey {
+    int prec, nu, regional;
+    int64_t m_pad;
+    bool operator<(const TuneKey &o) const
+    {
+        return std::tie(prec, nu, regional, m_pad) < std::tie(o.prec, o.nu, o.regional, o.m_pad);
+    }
+};
+
+std::mutex g_tune_mu;
+std::map<TuneKey, ColumnShape> g_tuned;
+int g_autotune = -1;   // -1: not read from MARNOLDI_AUTOTUNE yet
+bool g_tune_cache_loaded = false;
+
+int autotune_mode()
+{
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    if (g_autotune < 0) {
+        const char *v = getenv("MARNOLDI_AUTOTUNE");
+        g_autotune = (v && v[0] == '1') ? 1 : 0;
+    }
+    return g_autotune;
+}
+
+void load_tune_cache_locked()
+{
+    if (g_tune_cache_loaded) return;
+    g_tune_cache_loaded = true;
+    const char *path = getenv("MARNOLDI_TUNE_CACHE");
+    if (!path || !*path) return;
+    FILE *f = fopen(path, "r");
+    if (!f) return;
+    TuneKey k;
+    long long mp;
+    int v, t;
+    while (fscanf(f, "%d %d %d %lld %d %d", &k.prec, &k.nu, &k.regional, &mp, &v, &t) == 6) {
+        k.m_pad = mp;
+        ColumnShape cand[3];
+        const int n = column_shape_candidates(k.m_pad, cand);
+        for (int q = 0; q < n; ++q)   // only shapes this build has
+            if (cand[q].vpt == v && cand[q].threads == t) g_tuned[k] = cand[q];
+    }
+    fclose(f);
+}
+
+void save_tune_entry_locked(const TuneKey &k, const ColumnShape &s)
+{
+    const char *path = getenv("MARNOLDI_TUNE_CACHE");
+    if (!path || !*path) return;
+    FILE *f = fopen(path, "a");
+    if (!f) return;
+    fprintf(f, "%d %d %d %lld %d %d\n", k.prec, k.nu, k.regional, (long long)k.m_pad, s.vpt, s.threads);
+    fclose(f);
 }
 
 }  // namespace
@@ -107,8 +184,9 @@ struct marnoldi_ctx {
     // reduction scratch and pinned read-back
     double *d_partial = nullptr;
     unsigned *d_ticket = nullptr;
-    double *d_out = nullptr;
-    double *h_out = nullptr;
+    double *d_out = nullptr, *d_range = nullptr;
+    BisectState *d_bisect = nullptr;
+    double *h_out = nullptr;   // 128-byte pinned read-back slot
 
     // solved state
     bool solved = false;
@@ -126,6 +204,7 @@ struct marnoldi_ctx {
     size_t ws_bytes = 0;
     int64_t batch_override = 0;
     int64_t last_batch = 0;
+    ColumnShape gs_shape{0, 0, 0};   // Gram-Schmidt launch shape of the last solve
 
     // regional mode: positions, box, cell list (built on first use) and the
     // last search radius that worked
@@ -582,7 +661,7 @@ size_t setup_bytes(int64_t nbr, int64_t nnzb, int prec)
     size_t b = 8 * (size_t)(nbr + 1) + 4 * (size_t)nnzb + 2 * 128 * (size_t)nnzb +
                8 * 4 * (size_t)nbr + 8 * (size_t)nnzb;           // rp ci H S diag(S) transpose map
     if (prec == MARNOLDI_MIXED) b += 2 * 128 * (size_t)nnzb;     // hi/lo FP32 copies of H and S
-    return b + (2 * kReduceBlocks + 2) * sizeof(double) + 16;    // reduction scratch
+    return b + kScratchBytes;                                   // reduction scratch
 }
 
 size_t cells_bytes(int64_t nbr, const double *box)
@@ -806,13 +885,15 @@ int marnoldi::setup_with_allocator(marnoldi_ctx **out, int64_t n_block_rows, con
         c->A.Sf = dSf;
     }
     // reduction scratch
-    void *p = dalloc(c, (2 * kReduceBlocks + 2) * sizeof(double) + 16);
+    void *p = dalloc(c, kScratchBytes);
     if (!p) { g_setup_err = "device allocation failed"; marnoldi_destroy(c); return MARNOLDI_ENOMEM; }
-    c->owned.push_back({p, (2 * kReduceBlocks + 2) * sizeof(double) + 16});
+    c->owned.push_back({p, kScratchBytes});
     c->d_partial = (double *)p;
-    c->d_out = c->d_partial + 2 * kReduceBlocks;
-    c->d_ticket = (unsigned *)(c->d_out + 2);
-    cudaError_t e = cudaMemsetAsync(p, 0, (2 * kReduceBlocks + 2) * sizeof(double) + 16, c->stream);
+    c->d_out = (double *)((char *)p + kOffOut);
+    c->d_range = (double *)((char *)p + kOffRange);
+    c->d_bisect = (BisectState *)((char *)p + kOffBisect);
+    c->d_ticket = (unsigned *)((char *)p + kOffTicket);
+    cudaError_t e = cudaMemsetAsync(p, 0, kScratchBytes, c->stream);
     if (e == cudaSuccess && !(c->h_out = pinned_slot())) e = cudaErrorMemoryAllocation;
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) {
@@ -852,6 +933,22 @@ int marnoldi_kernel_stats(marnoldi_ctx *c, int kind, const char **name, int64_t 
         c->launches[kind] = 0;
         c->ms[kind] = 0.0;
     }
+    return MARNOLDI_OK;
+}
+
+int marnoldi_set_autotune(int mode)
+{
+    if (mode != 0 && mode != 1) return MARNOLDI_EINVAL;
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_autotune = mode;
+    return MARNOLDI_OK;
+}
+
+int marnoldi_gs_shape(const marnoldi_ctx *c, int *values_per_thread, int *threads)
+{
+    if (!c) return MARNOLDI_EINVAL;
+    if (values_per_thread) *values_per_thread = c->gs_shape.vpt;
+    if (threads) *threads = c->gs_shape.threads;
     return MARNOLDI_OK;
 }
 
@@ -1034,6 +1131,52 @@ int marnoldi_solve(marnoldi_ctx *c, const int64_t *columns, int64_t ncols, int n
     const double tau = c->prec == 0 ? kTauFp64 : kTauMixed;
     const int64_t mp = shape.m_pad;
     int rc = MARNOLDI_OK;
+    // the Krylov build of one batch (the vectors are stored in the tile order
+    // that the support search sets); slot n holds w_n (unnormalised); H w_n
+    // goes to U and, for n >= 1, S w_n to its slot (S w_0 comes from the
+    // initialisation); the Gram-Schmidt of step n scales them and writes w_{n+1}
+    auto build = [&](const KrylovBatch &k) -> int {
+        int r;
+        if ((r = launch(c, KK_SUPPORT, [&] { return launch_support(c->A, rmp, k, c->stream); })))
+            return r;
+        if ((r = launch(c, KK_INIT, [&] {
+                 return regional ? launch_init_regional(c->A, c->rm, k, c->stream) : launch_init(c->A, k, c->stream);
+             })))
+            return r;
+        for (int n = 0; n < nu; ++n) {
+            const char *Kn = (const char *)k.K + (size_t)n * mp * vs;
+            char *SKn = n > 0 ? (char *)k.SK + (size_t)n * mp * vs : nullptr;
+            if (regional) {
+                if ((r = launch(c, KK_SPMM_H, [&] {
+                         return launch_spmm_regional(c->A, c->rm, 0, k, Kn, (int64_t)nu * mp, k.U, mp, n + 1,
+                                                     c->stream);
+                     })))
+                    return r;
+                if (SKn && (r = launch(c, KK_SPMM_S, [&] {
+                               return launch_spmm_regional(c->A, c->rm, 1, k, Kn, (int64_t)nu * mp, SKn,
+                                                           (int64_t)nu * mp, n + 1, c->stream);
+                           })))
+                    return r;
+            } else if ((r = launch(c, KK_SPMM_HS, [&] {
+                            return launch_spmm_hs(c->A, k, Kn, (int64_t)nu * mp, SKn, (int64_t)nu * mp, n + 1,
+                                                  c->stream);
+                        }))) {
+                return r;
+            }
+            if ((r = launch(c, KK_GS, [&] { return launch_gs(k, n, n + 1 < nu, tau, c->stream); })))
+                return r;
+        }
+        return MARNOLDI_OK;
+    };
+    const TuneKey key{c->prec, nu, regional ? 1 : 0, mp};
+    bool tune = false;
+    if (autotune_mode()) {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        load_tune_cache_locked();
+        auto it = g_tuned.find(key);
+        if (it != g_tuned.end()) kb.shape = it->second;
+        else tune = true;
+    }
     for (int64_t start = 0; start < nc; start += B) {
         kb.nb = (int)std::min<int64_t>(B, nc - start);
         kb.cols = c->d_cols + start;
@@ -1042,68 +1185,82 @@ int marnoldi_solve(marnoldi_ctx *c, const int64_t *columns, int64_t ncols, int n
             if ((rc = launch(c, KK_REGION, [&] { return launch_local_bsr(c->A, c->rm, kb, c->stream); })))
                 return rc;
         }
-        // the vectors are stored in the tile order that the support search sets
-        if ((rc = launch(c, KK_SUPPORT, [&] { return launch_support(c->A, rmp, kb, c->stream); })))
-            return rc;
-        if ((rc = launch(c, KK_INIT, [&] {
-                 return regional ? launch_init_regional(c->A, c->rm, kb, c->stream)
-                                 : launch_init(c->A, kb, c->stream);
-             })))
-            return rc;
-        for (int n = 0; n < nu; ++n) {
-            // slot n holds w_n (unnormalised); H w_n goes to U and, for n >= 1,
-            // S w_n to its slot (S w_0 comes from the initialisation); the MGS
-            // of step n scales them and writes w_{n+1}
-            const char *Kn = (const char *)kb.K + (size_t)n * mp * vs;
-            char *SKn = n > 0 ? (char *)kb.SK + (size_t)n * mp * vs : nullptr;
-            if (regional) {
-                if ((rc = launch(c, KK_SPMM_H, [&] {
-                         return launch_spmm_regional(c->A, c->rm, 0, kb, Kn, (int64_t)nu * mp, kb.U, mp,
-                                                     n + 1, c->stream);
-                     })))
-                    return rc;
-                if (SKn && (rc = launch(c, KK_SPMM_S, [&] {
-                                return launch_spmm_regional(c->A, c->rm, 1, kb, Kn, (int64_t)nu * mp, SKn,
-                                                            (int64_t)nu * mp, n + 1, c->stream);
-                            })))
-                    return rc;
-            } else if ((rc = launch(c, KK_SPMM_HS, [&] {
-                            return launch_spmm_hs(c->A, kb, Kn, (int64_t)nu * mp, SKn, (int64_t)nu * mp,
-                                                  n + 1, c->stream);
-                        }))) {
-                return rc;
+        if (tune) {
+            // time every shape on the batch's first columns (one run to warm
+            // up, one timed) and keep the fastest for this key from now on;
+            // the lock makes concurrent solves of the same key agree
+            std::lock_guard<std::mutex> lock(g_tune_mu);
+            auto it = g_tuned.find(key);
+            if (it != g_tuned.end()) {
+                kb.shape = it->second;
+            } else {
+                ColumnShape cand[3];
+                const int ncand = column_shape_candidates(mp, cand);
+                KrylovBatch ks = kb;
+                ks.nb = (int)std::min<int64_t>(kb.nb, kTuneColumns);
+                float best = 0.f;
+                ColumnShape pick = kb.shape;
+                cudaEvent_t e0 = get_event(c), e1 = get_event(c);
+                for (int q = 0; q < ncand && ncand > 1; ++q) {
+                    ks.shape = cand[q];
+                    float ms = 0.f;
+                    for (int rep = 0; rep < 2; ++rep) {
+                        if (rep == 1) cudaEventRecord(e0, c->stream);
+                        if ((rc = build(ks))) break;
+                        if (rep == 1) cudaEventRecord(e1, c->stream);
+                    }
+                    if (rc || (rc = sync(c, "autotune"))) break;
+                    if (cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+                        cudaGetLastError();
+                        continue;
+                    }
+                    if (q == 0 || ms < best) {
+                        best = ms;
+                        pick = cand[q];
+                    }
+                }
+                c->events.push_back(e0);
+                c->events.push_back(e1);
+                if (rc) return rc;
+                g_tuned[key] = pick;
+                save_tune_entry_locked(key, pick);
+                kb.shape = pick;
             }
-            if ((rc = launch(c, KK_GS, [&] { return launch_gs(kb, n, n + 1 < nu, tau, c->stream); })))
-                return rc;
+            tune = false;
         }
+        if ((rc = build(kb))) return rc;
         if ((rc = launch(c, KK_EIG, [&] { return launch_eig(c->A, kb, c->st, start, rmp, es, c->stream); })))
             return rc;
     }
+    c->gs_shape = kb.shape;
     // ---- Fermi level
     double mu = 0.0, N = 0.0, E = 0.0;
     if (mu_fixed) {
         mu = *mu_fixed;
         if ((rc = count_at(c, mu, kT, &N, &E))) return rc;
     } else {
-        if ((rc = launch(c, KK_MINMAX, [&] {
-                 return launch_minmax(c->st, c->d_partial, c->d_ticket, c->d_out, c->stream);
+        // level range and the whole bisection on the device, one read-back
+        if ((rc = launch(c, KK_COUNT, [&] {
+                 return launch_bisection(c->st, kT, electron_count, c->d_partial, c->d_ticket, c->d_range,
+                                         c->d_out, c->d_bisect, c->stream);
              })))
             return rc;
-        e = cudaMemcpyAsync(c->h_out, c->d_out, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
-        if (e != cudaSuccess) return fail_cuda(c, e, "minmax read-back");
-        if ((rc = sync(c, "minmax"))) return rc;
-        double lo = c->h_out[0] - 40.0 * kT, hi = c->h_out[1] + 40.0 * kT;
-        double Nlo, Nhi;
-        if ((rc = count_at(c, lo, kT, &Nlo, &E)) || (rc = count_at(c, hi, kT, &Nhi, &E))) return rc;
-        if (!(Nlo <= electron_count && electron_count <= Nhi))
+        e = cudaMemcpyAsync(c->h_out, c->d_bisect, sizeof(BisectState), cudaMemcpyDeviceToHost, c->stream);
+        if (e != cudaSuccess) return fail_cuda(c, e, "bisection read-back");
+        if ((rc = sync(c, "bisection"))) return rc;
+        BisectState bs;
+        memcpy(&bs, c->h_out, sizeof bs);
+        // one launch each of the range and of the graph was counted; add the
+        // loop's kernels (a step and a count per iteration)
+        c->launches[KK_MINMAX] += 1;
+        c->launches[KK_COUNT] += bs.steps - 1;
+        c->launches[KK_BISECT] += bs.steps;
+        if (bs.status == 1)
             return fail(c, MARNOLDI_ENOCONV, "electron count %.6g outside [N(lo) = %.6g, N(hi) = %.6g]",
-                        electron_count, Nlo, Nhi);
-        for (int it = 1; it <= kBisectMaxit; ++it) {
-            mu = 0.5 * (lo + hi);
-            if ((rc = count_at(c, mu, kT, &N, &E))) return rc;
-            if (std::fabs(N - electron_count) <= kBisectRtol * electron_count) break;
-            if (N < electron_count) lo = mu; else hi = mu;
-        }
+                        electron_count, bs.Nlo, bs.Nhi);
+        mu = bs.mu;
+        N = bs.N;
+        E = bs.E;
     }
     if ((rc = sync(c, "solve"))) return rc;
     std::vector<int> est(nc);

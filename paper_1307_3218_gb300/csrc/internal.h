@@ -24,6 +24,7 @@ enum KernelKind {
     KK_REGION,
     KK_SUPPORT,
     KK_SPMM_HS,
+    KK_BISECT,
     KK_NKINDS
 };
 
@@ -59,6 +60,9 @@ struct ColumnShape {
     int64_t m_pad;
 };
 ColumnShape column_shape(int64_t m, int prec);
+// Every shape the Gram-Schmidt kernel is built for with the same m_pad
+// (threads 256, 512 or 1024; at most 3); returns how many were written.
+int column_shape_candidates(int64_t m_pad, ColumnShape *out);
 
 // ---------------------------------------------------------------- Krylov build
 // All pointers are device pointers.  Batch layout (c = batch column):
@@ -208,6 +212,21 @@ cudaError_t launch_eig(const DeviceMatrix &A, const KrylovBatch &b, const Column
 constexpr int kReduceBlocks = 304;
 cudaError_t launch_minmax(const ColumnState &st, double *partial, unsigned *ticket, double *out,
                           cudaStream_t s);
+// Fermi-level bisection on the device: bracket [min eps - 40 kT, max eps + 40 kT],
+// stop at |N - N_e| <= 1e-12 N_e or after 200 halvings.
+constexpr double kBisectBracketKT = 40.0;
+constexpr double kBisectRtol = 1e-12;
+constexpr int kBisectMaxit = 200;
+struct BisectState {
+    double lo, hi, mu, N, E, Nlo, Nhi;
+    int it, phase, status, steps;   // status 1: N_e outside [N(lo), N(hi)]
+};
+// Level range into range[0..1], then a CUDA graph with a while node that
+// alternates bisect_step_kernel and count_kernel (mu read from bs->mu) until
+// the step ends the loop; bs holds the result once the stream reaches it.
+cudaError_t launch_bisection(const ColumnState &st, double kT, double electron_count, double *partial,
+                             unsigned *ticket, double *range, double *out, BisectState *bs,
+                             cudaStream_t s);
 cudaError_t launch_count(const ColumnState &st, double mu, double kT, double *partial,
                          unsigned *ticket, double *out, cudaStream_t s);
 cudaError_t launch_density(const DeviceMatrix &A, const ColumnState &st, double mu, double kT,

@@ -30,7 +30,8 @@ namespace marnoldi {
 const char *kernel_name(int kind)
 {
     static const char *names[KK_NKINDS] = {"init",   "spmm_H", "gs",      "spmm_S", "eigsub",
-                                           "minmax", "count",  "density", "green", "region", "support", "spmm_HS"};
+                                           "minmax", "count",  "density", "green", "region", "support", "spmm_HS",
+                                           "bisect_step"};
     return (kind >= 0 && kind < KK_NKINDS) ? names[kind] : "?";
 }
 
@@ -45,6 +46,15 @@ ColumnShape column_shape(int64_t m, int prec)
     int v = 1;
     while (v < 16 && (int64_t)v * T < m) v *= 2;
     return ColumnShape{v, T, (int64_t)v * T};
+}
+
+int column_shape_candidates(int64_t m_pad, ColumnShape *out)
+{
+    int n = 0;
+    for (int T : {256, 512, 1024})
+        for (int v = 1; v <= 16; v *= 2)
+            if ((int64_t)v * T == m_pad) out[n++] = ColumnShape{v, T, m_pad};
+    return n;
 }
 
 namespace {
@@ -700,31 +710,26 @@ cudaError_t gs_dispatch(const KrylovBatch &b, int n, int need_w, double tau, cud
     return cudaGetLastError();
 }
 
+template <typename VT, int T>
+cudaError_t gs_vpt(const KrylovBatch &b, int n, int need_w, double tau, cudaStream_t s)
+{
+    switch (b.shape.vpt) {
+    case 1: return gs_dispatch<VT, 1, T>(b, n, need_w, tau, s);
+    case 2: return gs_dispatch<VT, 2, T>(b, n, need_w, tau, s);
+    case 4: return gs_dispatch<VT, 4, T>(b, n, need_w, tau, s);
+    case 8: return gs_dispatch<VT, 8, T>(b, n, need_w, tau, s);
+    case 16: return gs_dispatch<VT, 16, T>(b, n, need_w, tau, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
 template <typename VT>
 cudaError_t gs_shape(const KrylovBatch &b, int n, int need_w, double tau, cudaStream_t s)
 {
-    if (b.shape.threads == 512) {   // FP32, 16 values per thread
-        if constexpr (sizeof(VT) == 4)
-            if (b.shape.vpt == 16) return gs_dispatch<VT, 16, 512>(b, n, need_w, tau, s);
-        return cudaErrorInvalidValue;
-    }
-    if (b.shape.threads == 1024) {
-        switch (b.shape.vpt) {
-        case 1: return gs_dispatch<VT, 1, 1024>(b, n, need_w, tau, s);
-        case 2: return gs_dispatch<VT, 2, 1024>(b, n, need_w, tau, s);
-        case 4: return gs_dispatch<VT, 4, 1024>(b, n, need_w, tau, s);
-        case 8: return gs_dispatch<VT, 8, 1024>(b, n, need_w, tau, s);
-        case 16: return gs_dispatch<VT, 16, 1024>(b, n, need_w, tau, s);
-        default: return cudaErrorInvalidValue;
-        }
-    }
-    if (b.shape.threads != 256) return cudaErrorInvalidValue;
-    switch (b.shape.vpt) {
-    case 1: return gs_dispatch<VT, 1, 256>(b, n, need_w, tau, s);
-    case 2: return gs_dispatch<VT, 2, 256>(b, n, need_w, tau, s);
-    case 4: return gs_dispatch<VT, 4, 256>(b, n, need_w, tau, s);
-    case 8: return gs_dispatch<VT, 8, 256>(b, n, need_w, tau, s);
-    case 16: return gs_dispatch<VT, 16, 256>(b, n, need_w, tau, s);
+    switch (b.shape.threads) {
+    case 256: return gs_vpt<VT, 256>(b, n, need_w, tau, s);
+    case 512: return gs_vpt<VT, 512>(b, n, need_w, tau, s);
+    case 1024: return gs_vpt<VT, 1024>(b, n, need_w, tau, s);
     default: return cudaErrorInvalidValue;
     }
 }

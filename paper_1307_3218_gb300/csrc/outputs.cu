@@ -46,7 +46,8 @@ __device__ __forceinline__ double2 block_reduce2(double a, double b)
 }
 
 // Per-block partials, then the last block to finish (atomic ticket) combines
-// them in block order; no thread waits on another block.
+// them: each thread folds the partials q = tid, tid + blockDim.x, ... and the
+// block reduces those in its fixed order.  No thread waits on another block.
 template <int OP>
 __device__ void finish_reduce(double a, double b, double *partial, unsigned *ticket, double *out)
 {
@@ -59,17 +60,20 @@ __device__ void finish_reduce(double a, double b, double *partial, unsigned *tic
         last = (atomicAdd(ticket, 1u) == gridDim.x - 1);
     }
     __syncthreads();
-    if (last && threadIdx.x == 0) {
+    if (last) {   // uniform over the block
         __threadfence();
         const volatile double *vp = partial;
-        double x = vp[0], y = vp[1];
-        for (unsigned q = 1; q < gridDim.x; ++q) {
+        double x = OP == 0 ? 0.0 : INFINITY, y = OP == 0 ? 0.0 : -INFINITY;
+        for (unsigned q = threadIdx.x; q < gridDim.x; q += blockDim.x) {
             if (OP == 0) { x += vp[2 * q]; y += vp[2 * q + 1]; }
             else { x = fmin(x, vp[2 * q]); y = fmax(y, vp[2 * q + 1]); }
         }
-        out[0] = x;
-        out[1] = y;
-        *ticket = 0u;
+        const double2 t = block_reduce2<OP>(x, y);
+        if (threadIdx.x == 0) {
+            out[0] = t.x;
+            out[1] = t.y;
+            *ticket = 0u;
+        }
     }
 }
 
@@ -90,25 +94,103 @@ __global__ void __launch_bounds__(256) minmax_kernel(int64_t total, int nu,
     finish_reduce<1>(lo, hi, partial, ticket, out);
 }
 
-__global__ void __launch_bounds__(256) count_kernel(int64_t total, int nu,
+// Beyond |x| = 40 the Fermi function needs no exponential: for x < -40,
+// 1 + e^x rounds to 1 in FP64, so f = 1 exactly; for x > 40, f < 4.3e-18 and
+// is taken as 0 (each level's weight changes by less than 1e-17).
+constexpr double kFermiCut = 40.0;
+
+// Level-major order: element (a, c) = level a of column c, consecutive columns
+// in consecutive lanes, so that the lanes of a warp hold levels at similar
+// energies and mostly agree on whether the exponential is needed; levels
+// a >= nu_eff[c] are skipped; the per-thread sums are reduced in a fixed
+// order.  mu from mu_dev when given (the bisection graph), else mu_val.
+__global__ void __launch_bounds__(256) count_kernel(int64_t ncols, int nu,
                                                     const int *__restrict__ nu_eff,
                                                     const double *__restrict__ eps,
-                                                    const double *__restrict__ w, double mu,
-                                                    double kT, double *partial, unsigned *ticket,
-                                                    double *out)
+                                                    const double *__restrict__ w, double mu_val,
+                                                    const double *__restrict__ mu_dev, double kT,
+                                                    double *partial, unsigned *ticket, double *out)
 {
+    const double mu = mu_dev ? *mu_dev : mu_val;
+    const double cut = kFermiCut * kT;
+    const int64_t total = ncols * nu, stride = (int64_t)gridDim.x * blockDim.x;
+    int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int64_t a = idx / ncols, c = idx - a * ncols;
+    const int64_t da = stride / ncols, dc = stride - da * ncols;
     double sn = 0.0, se = 0.0;
-    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
-         idx += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t c = idx / nu;
-        if (idx - c * nu < nu_eff[c]) {
-            const double ea = eps[idx];
-            const double f2w = 2.0 * fermi((ea - mu) / kT) * w[idx];
+    for (; idx < total; idx += stride) {
+        if (a < nu_eff[c]) {
+            const double ea = eps[c * nu + a], d = ea - mu;
+            const double f = d > cut ? 0.0 : (d < -cut ? 1.0 : fermi(d / kT));
+            const double f2w = 2.0 * f * w[c * nu + a];
             sn += f2w;
             se = fma(f2w, ea, se);
         }
+        a += da;
+        c += dc;
+        if (c >= ncols) {
+            c -= ncols;
+            ++a;
+        }
     }
     finish_reduce<0>(sn, se, partial, ticket, out);
+}
+
+// One step of the Fermi-level bisection, run by one thread between two level
+// counts inside the graph's while loop (same bracket, halving and stopping
+// rule as a host loop would apply): phase 0 sets the bracket from the level
+// range and asks for N(lo), phase 1 asks for N(hi), phase 2 checks that the
+// bracket holds N_e, phase 3 halves until |N - N_e| <= rtol N_e or maxit
+// halvings.  `steps` bounds the loop whatever the counts hold.
+__global__ void bisect_step_kernel(BisectState *bs, const double *__restrict__ range,
+                                   const double *__restrict__ out, double kT, double Ne,
+                                   cudaGraphConditionalHandle loop)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    BisectState s = *bs;
+    bool more = true;
+    switch (s.phase) {
+    case 0:
+        // rounded like the host's (min - 40 kT): no contraction into an FMA
+        s.lo = __dsub_rn(range[0], __dmul_rn(kBisectBracketKT, kT));
+        s.hi = __dadd_rn(range[1], __dmul_rn(kBisectBracketKT, kT));
+        s.mu = s.lo;
+        s.phase = 1;
+        break;
+    case 1:
+        s.Nlo = out[0];
+        s.mu = s.hi;
+        s.phase = 2;
+        break;
+    case 2:
+        s.Nhi = out[0];
+        if (!(s.Nlo <= Ne && Ne <= s.Nhi)) {
+            s.status = 1;
+            more = false;
+        } else {
+            s.it = 1;
+            s.mu = 0.5 * (s.lo + s.hi);
+            s.phase = 3;
+        }
+        break;
+    case 3:
+        s.N = out[0];
+        s.E = out[1];
+        if (fabs(s.N - Ne) <= kBisectRtol * Ne || s.it >= kBisectMaxit) {
+            more = false;
+        } else {
+            if (s.N < Ne) s.lo = s.mu; else s.hi = s.mu;
+            s.mu = 0.5 * (s.lo + s.hi);
+            ++s.it;
+        }
+        break;
+    default:
+        more = false;
+    }
+    if (++s.steps >= kBisectMaxit + 3) more = false;
+    if (!more) s.phase = 4;
+    *bs = s;
+    cudaGraphSetConditional(loop, more ? 1u : 0u);
 }
 
 // One CTA per solved column: y = 2 f t (and 2 f eps t), then the pattern rows
@@ -206,9 +288,57 @@ cudaError_t launch_minmax(const ColumnState &st, double *partial, unsigned *tick
 cudaError_t launch_count(const ColumnState &st, double mu, double kT, double *partial,
                          unsigned *ticket, double *out, cudaStream_t s)
 {
-    count_kernel<<<kReduceBlocks, 256, 0, s>>>(st.ncols * st.nu, st.nu, st.nu_eff, st.eps, st.w,
-                                                mu, kT, partial, ticket, out);
+    count_kernel<<<kReduceBlocks, 256, 0, s>>>(st.ncols, st.nu, st.nu_eff, st.eps, st.w, mu, nullptr,
+                                                kT, partial, ticket, out);
     return cudaGetLastError();
+}
+
+cudaError_t launch_bisection(const ColumnState &st, double kT, double electron_count, double *partial,
+                             unsigned *ticket, double *range, double *out, BisectState *bs,
+                             cudaStream_t s)
+{
+    // the level range, then one graph whose while node alternates a bisection
+    // step and a level count until the step clears the loop condition
+    minmax_kernel<<<kReduceBlocks, 256, 0, s>>>(st.ncols * st.nu, st.nu, st.nu_eff, st.eps, partial,
+                                                 ticket, range);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemsetAsync(bs, 0, sizeof(BisectState), s);
+    if (e != cudaSuccess) return e;
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t ex = nullptr;
+    cudaStream_t cap = nullptr;
+    if ((e = cudaGraphCreate(&g, 0)) != cudaSuccess) return e;
+    cudaGraphConditionalHandle loop;
+    e = cudaGraphConditionalHandleCreate(&loop, g, 1, cudaGraphCondAssignDefault);
+    cudaGraphNodeParams np = {};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = loop;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    cudaGraphNode_t node;
+    if (e == cudaSuccess) e = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np);
+    // the loop body, recorded from a private stream (capture mode local to
+    // this thread, so other threads' CUDA calls are unaffected)
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+    if (e == cudaSuccess) {
+        cudaGraph_t body = np.conditional.phGraph_out[0];
+        e = cudaStreamBeginCaptureToGraph(cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            bisect_step_kernel<<<1, 32, 0, cap>>>(bs, range, out, kT, electron_count, loop);
+            count_kernel<<<kReduceBlocks, 256, 0, cap>>>(st.ncols, st.nu, st.nu_eff, st.eps, st.w, 0.0,
+                                                          &bs->mu, kT, partial, ticket, out);
+            const cudaError_t el = cudaGetLastError();
+            e = cudaStreamEndCapture(cap, &body);
+            if (e == cudaSuccess) e = el;
+        }
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&ex, g, 0);
+    if (e == cudaSuccess) e = cudaGraphLaunch(ex, s);
+    // destruction waits for nothing: launched work completes on its own
+    if (ex) cudaGraphExecDestroy(ex);
+    if (cap) cudaStreamDestroy(cap);
+    cudaGraphDestroy(g);
+    return e;
 }
 
 cudaError_t launch_density(const DeviceMatrix &A, const ColumnState &st, double mu, double kT,

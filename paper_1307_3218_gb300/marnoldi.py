@@ -88,6 +88,8 @@ def load(path: str | None = None):
         "marnoldi_kernel_stats": (i32, [P, i32, C.POINTER(C.c_char_p), C.POINTER(i64),
                                         C.POINTER(d), i32]),
         "marnoldi_count_noalloc": (i32, [P, P, P, i64, i32, d, d, P, P]),
+        "marnoldi_set_autotune": (i32, [i32]),
+        "marnoldi_gs_shape": (i32, [P, P, P]),
         "marnoldi_device_bytes": (i32, [P, P, P]),
         "marnoldi_footprint": (i32, [i64, P, P, P, i32, i32, i32, i64, P, P]),
         "marnoldi_server_create": (i32, [C.POINTER(P), i32, C.c_size_t]),
@@ -367,6 +369,18 @@ def marnoldi_destroy(ctx: Context) -> None:
     if ctx is not None and ctx.handle is not None and ctx.handle.value:
         load().marnoldi_destroy(ctx.handle)
         ctx.handle = C.c_void_p(None)
+
+
+def marnoldi_set_autotune(mode: int) -> None:
+    """0 = fixed launch-shape rule, 1 = time the Gram-Schmidt shapes on first use (process-wide)."""
+    _check(load().marnoldi_set_autotune(int(mode)))
+
+
+def marnoldi_gs_shape(ctx: Context) -> tuple[int, int]:
+    """(values per thread, threads per CTA) of the Gram-Schmidt kernel in the last solve."""
+    v, t = C.c_int(), C.c_int()
+    _check(load().marnoldi_gs_shape(ctx.handle, C.byref(v), C.byref(t)), ctx)
+    return v.value, t.value
 
 
 def marnoldi_device_bytes(ctx: Context) -> tuple[int, int]:

@@ -13,7 +13,7 @@ import numpy as np
 import pytest
 
 from paper_1307_3218_gb300 import shard
-from tbsynth import config_c1, tiny_hydrocarbon
+from tbsynth import amorphous_system, config_c1, tiny_hydrocarbon
 
 KT = 0.1
 NU = 12
@@ -123,3 +123,24 @@ def test_two_contexts_as_ranks_reproduce_one_context():
         m.marnoldi_level_range(fresh)
     for c in ctxs + [whole, fresh]:
         m.marnoldi_destroy(c)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("prec", [0, 1])
+def test_device_bisection_equals_host_loop(prec):
+    """The solve's bisection (a CUDA-graph while loop on the device) takes the
+    same steps as the host loop over marnoldi_fermi_at: same bracket, same
+    counts, so the same mu, N and E bit for bit."""
+    import paper_1307_3218_gb300 as m
+    t = amorphous_system(256, seed=2)
+    ctx = m.setup_system(t, prec)
+    m.marnoldi_solve(ctx, None, NU, 0, float(t.n_electrons), KT)
+    E0, mu0, N0 = m.marnoldi_energy(ctx)
+    lo, hi = shard.level_bracket(*m.marnoldi_level_range(ctx), KT, lambda v: v, lambda v: v)
+    mu, N, E, it = shard.fermi_bisect(lambda x: m.marnoldi_fermi_at(ctx, x, KT), lo, hi,
+                                      float(t.n_electrons), lambda a: a)
+    assert (mu, N, E) == (mu0, N0, E0)
+    assert 10 < it < shard.BISECT_MAXIT
+    stats = m.marnoldi_kernel_stats(ctx)
+    assert stats["bisect_step"][0] == it + 3   # bracket, N(lo), N(hi), then one per halving
+    m.marnoldi_destroy(ctx)
