@@ -63,6 +63,9 @@ def parse():
     p.add_argument("--no-extra", action="store_true",
                    help="skip the nu=100 and regional side measurements")
     p.add_argument("--no-serving", action="store_true", help="skip the request-server measurement")
+    p.add_argument("--order-n", default="",
+                   help="comma-separated atom counts for the order-N study (regional mode), e.g. "
+                        "4096,16384,65536,262144; empty = skip")
     p.add_argument("--fixed-shapes", action="store_true",
                    help="fixed Gram-Schmidt launch-shape rule instead of the autotuner")
     p.add_argument("--serve-requests", type=int, default=60)
@@ -462,6 +465,19 @@ def main():
     }
     mu_gpu = res["mu"]
     checks = {"headline": gpu_outputs(m, res["ctx"], cols, args.nu, prec)}
+    if not args.no_extra and len(cols) == len(t.real_columns()):
+        # forces from the headline solve: density, derivative upload, one kernel, read-back
+        from tbsynth import build_tb_derivatives
+        dH, dS = build_tb_derivatives(t)
+        m.marnoldi_forces(res["ctx"], dH, dS)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        F = m.marnoldi_forces(res["ctx"], dH, dS)
+        line["forces"] = {"ms": round((time.perf_counter() - t0) * 1e3, 3),
+                          "includes": "rho and rho^E on the device, dH/dS upload (host arrays), "
+                                      "force kernel, read-back",
+                          "max_abs_eV_per_A": round(float(np.abs(F).max()), 6),
+                          "abs_sum_eV_per_A": float(np.abs(F.sum(axis=0)).max())}
     m.marnoldi_destroy(res["ctx"])
 
     if not args.no_fp64 and prec == 1:
@@ -504,6 +520,10 @@ def main():
                 checks[label] = gpu_outputs(m, rx["ctx"], cl, nu_x, pr)
             m.marnoldi_destroy(rx["ctx"])
 
+    if args.order_n and world == 1:
+        sizes = [int(x) for x in args.order_n.split(",")]
+        line["order_n"] = order_n(m, t, sizes, 256, prec)
+
     if not args.no_serving and world == 1:
         line["serving"] = serving(m, t, args.serve_requests, args.serve_workers,
                                   int(args.serve_budget_gb * 2**30), prec)
@@ -526,6 +546,60 @@ def main():
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def order_n(m, t4096, sizes, n_reg: int, prec: int, nu: int = 30):
+    """The method's order-N claim on one GPU, and the error of the regions.
+
+    Time: regional solves (n_reg-atom regions, all real orbitals, mu by
+    bisection, density on the device) of amorphous carbon of each size, one
+    timed solve each after one untimed solve of the smallest.  Error: on the
+    4,096-atom structure in FP64, regional solves at N_reg = 64 .. 1,024
+    against the global-mode solve at the same nu (8, 16 and nu): band energy
+    per atom, largest density-matrix entry difference and the Fermi level.
+    """
+    import torch
+    from tbsynth import amorphous_system
+
+    def solve(t, p, reg, nu_x):
+        ctx = m.setup_system(t, p)
+        rho = torch.empty(t.nnzb * 16, dtype=torch.float64, device="cuda")
+        rhoE = torch.empty_like(rho)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        m.marnoldi_solve(ctx, None, nu_x, reg, float(t.n_electrons), KT)
+        m.marnoldi_density_device(ctx, rho, rhoE)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        E, mu, N = m.marnoldi_energy(ctx)
+        m.marnoldi_destroy(ctx)
+        return dt, E, mu, rho
+
+    out = {"time": [], "error": []}
+    first = True
+    for n in sizes:
+        t = t4096 if n == t4096.n_block_rows else amorphous_system(n, seed=0)
+        if first:
+            solve(t, prec, n_reg, nu)
+            first = False
+        dt, E, mu, _ = solve(t, prec, n_reg, nu)
+        ncols = int(t.real_columns().size)
+        out["time"].append({"atoms": n, "columns": ncols, "seconds": round(dt, 3),
+                            "columns_per_s": round(ncols / dt, 1), "E_band_per_atom_eV": E / n})
+        del t
+    for nu_e in (8, 16, nu):
+        _, E0, mu0, rho0 = solve(t4096, 0, 0, nu_e)
+        r0 = rho0.cpu().numpy()
+        for reg in (64, 128, 256, 512, 1024):
+            _, E, mu, rho = solve(t4096, 0, reg, nu_e)
+            out["error"].append({"nu": nu_e, "region_atoms": reg,
+                                 "dE_band_per_atom_eV": abs(E - E0) / t4096.n_block_rows,
+                                 "max_abs_drho": float(np.abs(rho.cpu().numpy() - r0).max()),
+                                 "dmu_eV": abs(mu - mu0)})
+    out["setup"] = (f"amorphous carbon, seed 0, {n_reg}-atom regions, nu={nu}, "
+                    f"{'mixed' if prec else 'fp64'} for the times; errors in FP64 against global mode "
+                    f"at the same nu on {t4096.n_block_rows} atoms")
+    return out
 
 
 SERVE_SIZES = (256, 512, 1024, 2048, 4096)

@@ -179,6 +179,23 @@ int marnoldi_fermi_at(marnoldi_ctx *ctx, double mu, double kT, double *N, double
 int marnoldi_green(marnoldi_ctx *ctx, const double *z_re_im, int nz, double *G_re_im);
 
 /*
+ * Atomic forces F_K = -Tr(rho dH/dR_K) + Tr(rho^E dS/dR_K) from the density and
+ * energy-density matrices of the last solve at its Fermi level (arXiv:1307.3218,
+ * Section 2: the Green's function gives the total energy and the force; the
+ * formula is the standard one for a non-orthogonal basis, with the column
+ * results symmetrised, rho_bar = (rho + rho^T) / 2, so that
+ * F_K = 2 sum_{J != K} sum_ab (rho_bar_KJ dH_KJ - rho^E_bar_KJ dS_KJ)_ab).
+ *   dH_dd, dS_dd  host, [3][nnzb][4][4]: block (I, J) of H and S differentiated
+ *                 with respect to d = R_J - R_I along x, y, z (two-centre
+ *                 models: dH_IJ/dR_J = +dH_dd, dH_IJ/dR_I = -dH_dd); on-site
+ *                 blocks are ignored.
+ *   F             host, [n_block_rows][3].
+ * Needs a successful solve (MARNOLDI_ESTATE); device scratch of 8 nnzb 16
+ * doubles plus F during the call.
+ */
+int marnoldi_forces(marnoldi_ctx *ctx, const double *dH_dd, const double *dS_dd, double *F);
+
+/*
  * Per-column results of the last solve, in the order of the solved columns
  * (host arrays; any may be NULL): nu_eff[ncols], eps[ncols*nu] (ascending
  * subspace levels, zero past nu_eff), w[ncols*nu] (weights

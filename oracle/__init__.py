@@ -373,3 +373,34 @@ def solve(sysm, nu: int, kT: float, Ne: float | None = None, mu_fixed: float | N
         it = 0
     rr, rre = density_rows(c, mu, kT)
     return Solution(mu, N, E, scatter_pattern(sysm, c, rr), scatter_pattern(sysm, c, rre), c, it)
+
+
+def forces(sysm, rho: np.ndarray, rhoE: np.ndarray, dH: np.ndarray, dS: np.ndarray) -> np.ndarray:
+    """Atomic forces F_K = -Tr(rho dH/dR_K) + Tr(rho^E dS/dR_K), shape (n_atoms, 3).
+
+    Section 2: the Green's function (here its density and energy-density
+    matrices) gives the total energy and the force; the paper prints no force
+    formula, so this is the standard one for a non-orthogonal basis, with the
+    unsymmetrised column results symmetrised, rho_bar = (rho + rho^T) / 2.
+    dH, dS: (3, nnzb, 4, 4), block (I, J) differentiated with respect to
+    d = R_J - R_I, so dH_IJ/dR_I = -dH[., k] and dH_IJ/dR_J = +dH[., k].
+    Entries of columns that were not computed (NaN) count as 0.
+    """
+    nb = sysm.nnzb
+    rows = np.repeat(np.arange(sysm.n_block_rows), np.diff(sysm.row_ptr))
+    cols = np.asarray(sysm.col_idx, dtype=np.int64)
+    bidx = block_index(sysm)
+    kt = np.array([bidx[(int(J), int(I))] for I, J in zip(rows, cols)], dtype=np.int64)
+    r = np.nan_to_num(np.asarray(rho, dtype=np.float64).reshape(nb, 4, 4))
+    rE = np.nan_to_num(np.asarray(rhoE, dtype=np.float64).reshape(nb, 4, 4))
+    rbar = 0.5 * (r + r[kt].transpose(0, 2, 1))
+    rEbar = 0.5 * (rE + rE[kt].transpose(0, 2, 1))
+    F = np.zeros((sysm.n_block_rows, 3))
+    for x in range(3):
+        trH = np.einsum("kab,kab->k", rbar, dH[x])     # Tr(rho_bar_k^T dH_k), one block
+        trS = np.einsum("kab,kab->k", rEbar, dS[x])
+        # -Tr(rho dH/dR_K) + Tr(rho^E dS/dR_K): block k = (I, J) enters K = I with
+        # dH/dR_I = -dH_k and K = J with dH/dR_J = +dH_k
+        np.add.at(F[:, x], rows, trH - trS)
+        np.add.at(F[:, x], cols, -trH + trS)
+    return F

@@ -1385,6 +1385,34 @@ int marnoldi_green(marnoldi_ctx *c, const double *z, int nz, double *G)
     return rc ? rc : rs;
 }
 
+int marnoldi_forces(marnoldi_ctx *c, const double *dH, const double *dS, double *F)
+{
+    if (!c || !dH || !dS || !F) return MARNOLDI_EINVAL;
+    if (!c->solved) return fail(c, MARNOLDI_ESTATE, "forces requested before a successful solve");
+    const size_t vals = (size_t)c->nnzb * 16, bytes = (size_t)(2 + 6) * vals * sizeof(double) +
+                                                      (size_t)c->nbr * 3 * sizeof(double);
+    double *d = (double *)dalloc(c, bytes);
+    if (!d) return fail(c, MARNOLDI_ENOMEM, "device allocation of %zu bytes for forces failed", bytes);
+    double *rho = d, *rhoE = d + vals, *dHd = d + 2 * vals, *dSd = d + 5 * vals, *Fd = d + 8 * vals;
+    int rc = marnoldi_density_device(c, rho, rhoE);
+    cudaError_t e = cudaSuccess;
+    if (!rc) {
+        e = cudaMemcpyAsync(dHd, dH, 3 * vals * sizeof(double), cudaMemcpyHostToDevice, c->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(dSd, dS, 3 * vals * sizeof(double), cudaMemcpyHostToDevice, c->stream);
+        if (e != cudaSuccess) rc = fail_cuda(c, e, "force inputs upload");
+    }
+    if (!rc)
+        rc = launch(c, KK_FORCE, [&] { return launch_forces(c->A, rho, rhoE, dHd, dSd, Fd, c->stream); });
+    if (!rc) {
+        e = cudaMemcpyAsync(F, Fd, (size_t)c->nbr * 3 * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+        if (e != cudaSuccess) rc = fail_cuda(c, e, "force read-back");
+    }
+    const int rs = sync(c, "forces");
+    dfree(c, d, bytes);
+    return rc ? rc : rs;
+}
+
 int marnoldi_column_stats(marnoldi_ctx *c, int32_t *nu_eff, double *eps, double *w)
 {
     if (!c) return MARNOLDI_EINVAL;

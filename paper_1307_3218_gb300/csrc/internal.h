@@ -25,6 +25,7 @@ enum KernelKind {
     KK_SUPPORT,
     KK_SPMM_HS,
     KK_BISECT,
+    KK_FORCE,
     KK_NKINDS
 };
 
@@ -227,6 +228,11 @@ struct BisectState {
 cudaError_t launch_bisection(const ColumnState &st, double kT, double electron_count, double *partial,
                              unsigned *ticket, double *range, double *out, BisectState *bs,
                              cudaStream_t s);
+// F[n_atoms][3] = 2 sum_J sum_ab (rho_bar dH - rho_bar^E dS) over the blocks
+// (K, J != K); rho, rhoE, dH, dS device arrays in the BSR layout (dH, dS
+// [3][nnzb][16]).
+cudaError_t launch_forces(const DeviceMatrix &A, const double *rho, const double *rhoE, const double *dH,
+                          const double *dS, double *F, cudaStream_t s);
 cudaError_t launch_count(const ColumnState &st, double mu, double kT, double *partial,
                          unsigned *ticket, double *out, cudaStream_t s);
 cudaError_t launch_density(const DeviceMatrix &A, const ColumnState &st, double mu, double kT,

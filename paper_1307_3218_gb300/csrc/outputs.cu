@@ -275,7 +275,56 @@ __global__ void __launch_bounds__(128) green_kernel(
     }
 }
 
+// Atomic forces from the density and energy-density matrices: one warp per
+// atom K; lane l < 16 takes entry (a, b) = (l / 4, l % 4) of every block
+// (K, J), J != K, with rho_bar = (rho_KJ + rho_JK^T) / 2 (k' = tmap[k] is the
+// block (J, K)); F_K = 2 sum_J sum_ab (rho_bar dH - rho_bar^E dS), the lanes
+// summed in a fixed order.  dH, dS: [3][nnzb][16], derivatives with respect
+// to d = R_J - R_I.
+__global__ void __launch_bounds__(256) force_kernel(int64_t nbr, int64_t nnzb, const int64_t *__restrict__ rp,
+                                                    const int32_t *__restrict__ ci,
+                                                    const int64_t *__restrict__ tmap,
+                                                    const double *__restrict__ rho,
+                                                    const double *__restrict__ rhoE,
+                                                    const double *__restrict__ dH,
+                                                    const double *__restrict__ dS, double *__restrict__ F)
+{
+    const int64_t K = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (K >= nbr) return;   // uniform over the warp
+    double f[3] = {0.0, 0.0, 0.0};
+    if (lane < 16) {
+        const int lt = (lane & 3) * 4 + (lane >> 2);   // entry (b, a) of the mirror block
+        for (int64_t k = rp[K]; k < rp[K + 1]; ++k) {
+            if (ci[k] == K) continue;
+            const int64_t kt = tmap[k];
+            const double r = 0.5 * (rho[k * 16 + lane] + rho[kt * 16 + lt]);
+            const double re = 0.5 * (rhoE[k * 16 + lane] + rhoE[kt * 16 + lt]);
+#pragma unroll
+            for (int x = 0; x < 3; ++x) {
+                const int64_t o = ((int64_t)x * nnzb + k) * 16 + lane;
+                f[x] = fma(r, dH[o], fma(-re, dS[o], f[x]));
+            }
+        }
+    }
+#pragma unroll
+    for (int x = 0; x < 3; ++x) {
+        double v = f[x];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+        if (lane == 0) F[3 * K + x] = 2.0 * v;
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_forces(const DeviceMatrix &A, const double *rho, const double *rhoE, const double *dH,
+                          const double *dS, double *F, cudaStream_t s)
+{
+    const unsigned blocks = (unsigned)((A.nbr + 7) / 8);
+    force_kernel<<<blocks, 256, 0, s>>>(A.nbr, A.nnzb, A.rp, A.ci, A.tmap, rho, rhoE, dH, dS, F);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_minmax(const ColumnState &st, double *partial, unsigned *ticket, double *out,
                           cudaStream_t s)

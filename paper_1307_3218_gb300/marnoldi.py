@@ -88,6 +88,7 @@ def load(path: str | None = None):
         "marnoldi_kernel_stats": (i32, [P, i32, C.POINTER(C.c_char_p), C.POINTER(i64),
                                         C.POINTER(d), i32]),
         "marnoldi_count_noalloc": (i32, [P, P, P, i64, i32, d, d, P, P]),
+        "marnoldi_forces": (i32, [P, P, P, P]),
         "marnoldi_set_autotune": (i32, [i32]),
         "marnoldi_gs_shape": (i32, [P, P, P]),
         "marnoldi_device_bytes": (i32, [P, P, P]),
@@ -307,6 +308,17 @@ def marnoldi_green(ctx: Context, zs) -> np.ndarray:
     G = np.empty((z.size, ctx.nnzb, 4, 4), np.complex128)
     _check(load().marnoldi_green(ctx.handle, _ptr(zri), int(z.size), _ptr(G)), ctx)
     return G
+
+
+def marnoldi_forces(ctx: Context, dH_dd, dS_dd) -> np.ndarray:
+    """Forces (n_block_rows, 3) from the last solve; dH_dd, dS_dd of shape (3, nnzb, 4, 4)."""
+    dH = np.ascontiguousarray(dH_dd, dtype=np.float64)
+    dS = np.ascontiguousarray(dS_dd, dtype=np.float64)
+    if dH.size != 3 * 16 * ctx.nnzb or dS.size != 3 * 16 * ctx.nnzb:
+        raise MarnoldiError(MARNOLDI_EINVAL, "dH_dd and dS_dd must hold 3 x nnzb x 16 values")
+    F = np.empty((ctx.n_block_rows, 3))
+    _check(load().marnoldi_forces(ctx.handle, _ptr(dH), _ptr(dS), _ptr(F)), ctx)
+    return F
 
 
 def marnoldi_solved_shape(ctx: Context) -> tuple[int, int]:

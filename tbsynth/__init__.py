@@ -14,11 +14,11 @@ carbon atom, neighbour blocks from atom pairs inside a cutoff.
 """
 
 from .structures import Structure, diamond, amorphous_carbon, spatial_sort
-from .tbmodel import (TBSystem, amorphous_system, build_tb, carbon_params, config_c1,
-                      config_c2, tiny_hydrocarbon, tiny_system)
+from .tbmodel import (TBSystem, amorphous_system, build_tb, build_tb_derivatives, carbon_params,
+                      config_c1, config_c2, tiny_hydrocarbon, tiny_system)
 
 __all__ = [
     "Structure", "diamond", "amorphous_carbon", "spatial_sort",
-    "TBSystem", "build_tb", "carbon_params", "config_c1", "config_c2", "tiny_system",
+    "TBSystem", "build_tb", "build_tb_derivatives", "carbon_params", "config_c1", "config_c2", "tiny_system",
     "amorphous_system", "tiny_hydrocarbon",
 ]

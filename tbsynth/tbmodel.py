@@ -132,6 +132,70 @@ def _sk_blocks(d: np.ndarray, V: np.ndarray) -> np.ndarray:
     return B
 
 
+def _sk_block_derivatives(d: np.ndarray, V: np.ndarray) -> np.ndarray:
+    """d/d(d_x) of the blocks of _sk_blocks when every amplitude scales as r^-2.
+
+    Returns (P, 3, 4, 4).  With c = d / r, g_p = (delta_px - c_p c_x) / r
+    (= dc_p / dd_x) and dV/dd_x = -2 V c_x / r:
+        dB/dd_x = -2 (c_x / r) B + [0, V_sps g_b; -V_sps g_a, (g_a c_b + c_a g_b)(V_pps - V_ppp)].
+    """
+    r = np.linalg.norm(d, axis=1)
+    c = d / r[:, None]
+    B = _sk_blocks(d, V)
+    P = d.shape[0]
+    out = np.zeros((P, 3, 4, 4))
+    eye = np.eye(3)
+    for x in range(3):
+        g = (eye[x][None, :] - c * c[:, x:x + 1]) / r[:, None]          # (P, 3)
+        D = -2.0 * (c[:, x] / r)[:, None, None] * B
+        D[:, 0, 1:] += g * V[:, 1:2]
+        D[:, 1:, 0] -= g * V[:, 1:2]
+        D[:, 1:, 1:] += (g[:, :, None] * c[:, None, :] + c[:, :, None] * g[:, None, :]) \
+            * (V[:, 2] - V[:, 3])[:, None, None]
+        out[:, x] = D
+    return out
+
+
+def pair_amplitudes(si: np.ndarray, sj: np.ndarray, r: np.ndarray, params: dict) -> tuple[np.ndarray, np.ndarray]:
+    """(V, coupled): Slater-Koster amplitudes V0 (r0 / r)^2 of each pair and whether the pair couples."""
+    V = np.zeros((si.size, 4))
+    keep = np.ones(si.size, bool)
+    for (a, b), hop in params["hop"].items():
+        sel = ((si == a) & (sj == b)) | ((si == b) & (sj == a))
+        if hop is None:
+            keep &= ~sel
+            continue
+        V[sel] = np.array(hop[:4])[None, :] * ((hop[4] / r[sel]) ** 2)[:, None]
+    return V, keep
+
+
+def build_tb_derivatives(sysm: "TBSystem", params: dict | None = None) -> tuple[np.ndarray, np.ndarray]:
+    """dH, dS of shape (3, nnzb, 4, 4): block (I, J) differentiated with respect to
+    the displacement d = R_J - R_I (minimum image) along x, y, z; on-site blocks 0.
+
+    Aligned with sysm's blocks; couplings to padding orbitals stay 0.
+    """
+    p = params or carbon_params()
+    s = sysm.structure
+    rows = np.repeat(np.arange(sysm.n_block_rows), np.diff(sysm.row_ptr))
+    cols = sysm.col_idx.astype(np.int64)
+    off = np.nonzero(rows != cols)[0]
+    i, j = rows[off], cols[off]
+    d = min_image(s.positions[j] - s.positions[i], s.box)
+    V, keep = pair_amplitudes(s.species[i], s.species[j], np.linalg.norm(d, axis=1), p)
+    dH = np.zeros((3, sysm.nnzb, 4, 4))
+    dS = np.zeros((3, sysm.nnzb, 4, 4))
+    Dh = _sk_block_derivatives(d, V) * keep[:, None, None, None]
+    Ds = _sk_block_derivatives(d, V * p["overlap_factor"]) * keep[:, None, None, None]
+    real = sysm.orbital_mask.reshape(-1, 4).astype(bool)
+    pad = ~(real[i][:, :, None] & real[j][:, None, :])                     # (P, 4, 4)
+    for D in (Dh, Ds):
+        D *= ~pad[:, None, :, :]
+    dH[:, off] = np.moveaxis(Dh, 1, 0)
+    dS[:, off] = np.moveaxis(Ds, 1, 0)
+    return dH, dS
+
+
 def neighbour_pairs(s: Structure, cutoff: float) -> tuple[np.ndarray, np.ndarray, np.ndarray]:
     """All ordered pairs (i, j), i != j, closer than cutoff; displacement j - i (minimum image)."""
     from scipy.spatial import cKDTree
@@ -152,17 +216,7 @@ def build_tb(s: Structure, params: dict | None = None, check_spd: bool = True,
     p = params or carbon_params()
     n = s.n_atoms
     i, j, d = neighbour_pairs(s, p["cutoff"])
-    si, sj = s.species[i], s.species[j]
-    keep = np.ones(i.size, bool)
-    V = np.zeros((i.size, 4))
-    for (a, b), hop in p["hop"].items():
-        sel = ((si == a) & (sj == b)) | ((si == b) & (sj == a))
-        if hop is None:
-            keep &= ~sel
-            continue
-        r = np.linalg.norm(d[sel], axis=1)
-        scale = (hop[4] / r) ** 2
-        V[sel] = np.array(hop[:4])[None, :] * scale[:, None]
+    V, keep = pair_amplitudes(s.species[i], s.species[j], np.linalg.norm(d, axis=1), p)
     i, j, d, V = i[keep], j[keep], d[keep], V[keep]
     Hoff = _sk_blocks(d, V)
     Soff = _sk_blocks(d, V * p["overlap_factor"])
