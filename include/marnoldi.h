@@ -222,6 +222,34 @@ int marnoldi_kernel_stats(marnoldi_ctx *ctx, int kind, const char **name, int64_
                           double *ms, int reset);
 
 /*
+ * Members: one context holding several independent structures as a
+ * block-diagonal union, solved in the same kernel launches (one launch per
+ * step covers the columns of every member), each member with its own
+ * electron count and Fermi level.
+ *   marnoldi_set_members(ctx, n, atom_offsets[n + 1], electron_counts[n])
+ *     Member q is atoms [atom_offsets[q], atom_offsets[q + 1]); offsets run
+ *     from 0 to n_block_rows, every member starts at a multiple of 8 atoms (pad
+ *     with atoms whose four orbitals are padding orbitals), and no block may
+ *     couple two members (MARNOLDI_EINVAL otherwise).  n = 0 removes the
+ *     members.  Clears the last solve.
+ *   A marnoldi_solve of a context with members takes every real orbital
+ *   (columns = NULL), global mode, nu <= 253 and mu by bisection (mu_fixed =
+ *   NULL; electron_count is ignored): each member's mu solves N(mu) = its
+ *   electron count over its own columns with the usual bracket and rule.  The
+ *   Krylov vectors are as long as the largest member needs, so a member solved
+ *   in a union whose largest member has the same padded length gets the same
+ *   results as alone, bit for bit.  marnoldi_density, _density_device, _forces
+ *   and _green use each member's own mu; marnoldi_energy returns the sums of
+ *   E_band and N over the members (mu of member 0); marnoldi_level_range and
+ *   marnoldi_fermi_at return MARNOLDI_EINVAL.
+ *   marnoldi_member_energy(ctx, q, ...): E_band, mu and N(mu) of member q.
+ */
+int marnoldi_set_members(marnoldi_ctx *ctx, int n_members, const int64_t *atom_offsets,
+                         const double *electron_counts);
+int marnoldi_member_energy(marnoldi_ctx *ctx, int member, double *band_energy, double *mu,
+                           double *electron_count_out);
+
+/*
  * Launch-shape autotuner of the Gram-Schmidt kernel (process-wide).
  *   marnoldi_set_autotune: mode 0 (default, also when MARNOLDI_AUTOTUNE is
  *     unset or not "1") uses a fixed rule: 256 threads per CTA up to m = 4096,
@@ -318,10 +346,20 @@ int marnoldi_footprint(int64_t n_block_rows, const int64_t *row_ptr, const uint8
  *                  in bytes and the batch size,
  *       message    the request's error message (empty on success), truncated
  *                  to cap - 1 characters.
- *   marnoldi_server_stats(srv, stats[7])
+ *   marnoldi_server_stats(srv, stats[9])
  *     queued, running, completed, footprint bytes in use, most footprint bytes
- *     in use at once, most requests running at once, the pool's most reserved
- *     bytes.
+ *     in use at once, most launch groups running at once, the pool's most
+ *     reserved bytes, groups of two or more requests formed, the largest group.
+ *   marnoldi_server_set_group_limit(srv, n)
+ *     Continuous batching: when a worker starts a request, up to n - 1 queued
+ *     requests of the same precision, nu and kT, global mode, nu <= 253, whose
+ *     Krylov vectors have the same padded length (and that all want or all skip
+ *     the density) join it as members of one context (marnoldi_set_members;
+ *     union <= 4,096 atoms), while the union's footprint fits beside the running
+ *     requests.  Each member's results equal its results alone, bit for bit.
+ *     Default 16; 1 runs every request on its own.  MARNOLDI_EINVAL outside
+ *     [1, 64].  For members of a group, result[6] and result[7] of
+ *     marnoldi_server_wait are the group's footprint and batch.
  *   marnoldi_server_destroy(srv)
  *     Waits for every submitted request to finish, then frees the workers,
  *     streams and pool.  Records never waited for are dropped.
@@ -339,6 +377,7 @@ int marnoldi_server_submit(marnoldi_server *srv, int64_t n_block_rows, const int
 int marnoldi_server_wait(marnoldi_server *srv, int64_t request_id, double timeout_s, int *status,
                          double *result, char *message, size_t message_cap);
 int marnoldi_server_stats(marnoldi_server *srv, int64_t *stats);
+int marnoldi_server_set_group_limit(marnoldi_server *srv, int max_members);
 const char *marnoldi_server_last_error(void);
 void marnoldi_server_destroy(marnoldi_server *srv);
 

@@ -206,6 +206,14 @@ struct marnoldi_ctx {
     int64_t last_batch = 0;
     ColumnShape gs_shape{0, 0, 0};   // Gram-Schmidt launch shape of the last solve
 
+    // members: a block-diagonal union of independent structures (atom ranges
+    // starting at multiples of 8 atoms), each with its own electron count and
+    // Fermi level, solved in the same launches
+    std::vector<int64_t> mem_atom;   // n + 1 atom offsets (empty: one structure)
+    std::vector<double> mem_ne;
+    std::vector<int64_t> mem_col;    // n + 1 offsets into the solved columns
+    std::vector<double> mem_mu, mem_N, mem_E;
+
     // regional mode: positions, box, cell list (built on first use) and the
     // last search radius that worked
     bool cells_ready = false;
@@ -559,7 +567,7 @@ size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
 // grown across solves.
 struct SolvePlan {
     size_t o_cols, o_poff, o_nue, o_est, o_eps, o_w, o_t, o_P, state_bytes;
-    int64_t B;
+    int64_t B, ntile;
     ColumnShape shape;
     size_t vs;
     bool a_global;
@@ -590,7 +598,7 @@ int64_t clamp_batch(int64_t B, int64_t nc, bool regional)
 // false when nu with blocks rows of `maxrow` blocks does not fit the
 // eigensolver's shared memory.
 bool plan_solve(int64_t m_vec, int prec, int nu, int region_atoms, int maxrow, int64_t nc,
-                int64_t prow, int64_t B, SolvePlan &p)
+                int64_t prow, int64_t B, int64_t ntile_min, SolvePlan &p)
 {
     const bool regional = region_atoms > 0;
     p.o_cols = 0;
@@ -606,7 +614,9 @@ bool plan_solve(int64_t m_vec, int prec, int nu, int region_atoms, int maxrow, i
     p.B = B;
     p.shape = column_shape(m_vec, prec);
     p.vs = prec == 0 ? 8 : 4;
-    const size_t mp = (size_t)p.shape.m_pad, vs = p.vs, nt = mp / 32;
+    const size_t mp = (size_t)p.shape.m_pad, vs = p.vs;
+    const size_t nt = std::max<size_t>(mp / 32, (size_t)ntile_min);   // 8-atom tiles of the structure
+    p.ntile = (int64_t)nt;
     const size_t rg = regional ? (size_t)region_atoms : 0;
     p.oK = 0;
     p.oSK = p.oK + al256((size_t)B * nu * mp * vs);
@@ -669,6 +679,22 @@ size_t cells_bytes(int64_t nbr, const double *box)
     int64_t ncells = 1;
     for (int d = 0; d < 3; ++d) ncells *= (int64_t)std::max(1.0, std::min(256.0, std::floor(box[d] / 2.6)));
     return 24 * (size_t)nbr + 24 + 4 * (size_t)(ncells + 1) + 4 * (size_t)nbr;
+}
+
+// The solved columns [c0, c1) as a column state of their own (P stays shared:
+// p_off holds absolute offsets).
+ColumnState column_view(const ColumnState &st, int64_t c0, int64_t c1)
+{
+    ColumnState v = st;
+    v.ncols = c1 - c0;
+    v.cols = st.cols + c0;
+    v.p_off = st.p_off + c0;
+    v.nu_eff = st.nu_eff + c0;
+    v.eig_status = st.eig_status + c0;
+    v.eps = st.eps + c0 * st.nu;
+    v.w = st.w + c0 * st.nu;
+    v.t = st.t + c0 * st.nu;
+    return v;
 }
 
 void free_state(marnoldi_ctx *c)
@@ -744,44 +770,60 @@ int marnoldi_footprint(int64_t n_block_rows, const int64_t *row_ptr, const uint8
     if (!bytes) return fail(nullptr, MARNOLDI_EINVAL, "bytes is NULL");
     if (n_block_rows < 1 || n_block_rows > (int64_t)1 << 30 || !row_ptr)
         return fail(nullptr, MARNOLDI_EINVAL, "need n_block_rows >= 1 and row_ptr");
+    PatternStats st;
+    const int rc = pattern_stats(n_block_rows, row_ptr, orbital_mask, st);
+    if (rc) return rc;
+    return footprint_of(st, precision, nu, region_atoms, box, batch_columns, bytes, batch_used);
+}
+
+}  // extern "C"
+
+int marnoldi::pattern_stats(int64_t n_block_rows, const int64_t *row_ptr, const uint8_t *orbital_mask,
+                            PatternStats &st)
+{
+    st = PatternStats{};
+    st.nbr = n_block_rows;
+    st.nnzb = row_ptr[n_block_rows];
+    st.m_vec = 4 * n_block_rows;
+    for (int64_t I = 0; I < n_block_rows; ++I) {
+        const int64_t len = row_ptr[I + 1] - row_ptr[I];
+        if (len < 1) return fail(nullptr, MARNOLDI_EINVAL, "block row %lld is empty", (long long)I);
+        st.maxrow = std::max<int>(st.maxrow, (int)len);
+        for (int a = 0; a < 4; ++a)
+            if (!orbital_mask || orbital_mask[4 * I + a]) {
+                ++st.nc;
+                st.prow += 4 * len;
+            }
+    }
+    if (st.nc < 1) return fail(nullptr, MARNOLDI_EINVAL, "no real orbitals");
+    return MARNOLDI_OK;
+}
+
+int marnoldi::footprint_of(const PatternStats &st, int precision, int nu, int region_atoms, const double *box,
+                           int64_t batch_columns, size_t *bytes, int64_t *batch_used)
+{
     if (precision != MARNOLDI_FP64 && precision != MARNOLDI_MIXED)
         return fail(nullptr, MARNOLDI_EINVAL, "unknown precision %d", precision);
     if (batch_columns < 1) return fail(nullptr, MARNOLDI_EINVAL, "batch_columns must be >= 1");
     const bool regional = region_atoms > 0;
-    if (region_atoms < 0 || region_atoms > kMaxRegion || region_atoms > n_block_rows || (regional && !box))
+    if (region_atoms < 0 || region_atoms > kMaxRegion || region_atoms > st.nbr || (regional && !box))
         return fail(nullptr, MARNOLDI_EINVAL, "region_atoms = %d invalid (regional mode needs box)", region_atoms);
-    if (!regional && 4 * n_block_rows > kMaxGlobalM)
+    if (!regional && 4 * st.nbr > kMaxGlobalM)
         return fail(nullptr, MARNOLDI_EINVAL, "global mode supports M <= %lld", (long long)kMaxGlobalM);
     if (nu < 1 || nu > kMaxNu || (regional && nu > 4 * region_atoms))
         return fail(nullptr, MARNOLDI_EINVAL, "nu = %d out of range", nu);
-    const int64_t nnzb = row_ptr[n_block_rows];
-    int maxrow = 1;
-    int64_t nc = 0, prow = 0;
-    for (int64_t I = 0; I < n_block_rows; ++I) {
-        const int64_t len = row_ptr[I + 1] - row_ptr[I];
-        if (len < 1) return fail(nullptr, MARNOLDI_EINVAL, "block row %lld is empty", (long long)I);
-        maxrow = std::max<int>(maxrow, (int)len);
-        for (int a = 0; a < 4; ++a)
-            if (!orbital_mask || orbital_mask[4 * I + a]) {
-                ++nc;
-                prow += 4 * len;
-            }
-    }
-    if (nc < 1) return fail(nullptr, MARNOLDI_EINVAL, "no real orbitals");
-    const int64_t B = clamp_batch(batch_columns, nc, regional);
+    const int64_t B = clamp_batch(batch_columns, st.nc, regional);
     SolvePlan plan;
-    if (!plan_solve(regional ? 4 * (int64_t)region_atoms : 4 * n_block_rows, precision, nu, region_atoms,
-                    maxrow, nc, prow, B, plan))
+    if (!plan_solve(regional ? 4 * (int64_t)region_atoms : st.m_vec, precision, nu, region_atoms, st.maxrow,
+                    st.nc, st.prow, B, regional ? 0 : (st.nbr + 7) / 8, plan))
         return fail(nullptr, MARNOLDI_EINVAL, "nu = %d exceeds the eigensolver's shared memory", nu);
-    size_t total = setup_bytes(n_block_rows, nnzb, precision) + plan.state_bytes + plan.ws_bytes +
-                   (size_t)nnzb * 16 * sizeof(double) * 2;   // marnoldi_density's staging
-    if (regional) total += cells_bytes(n_block_rows, box);
+    size_t total = setup_bytes(st.nbr, st.nnzb, precision) + plan.state_bytes + plan.ws_bytes +
+                   (size_t)st.nnzb * 16 * sizeof(double) * 2;   // marnoldi_density's staging
+    if (regional) total += cells_bytes(st.nbr, box);
     *bytes = total;
     if (batch_used) *batch_used = B;
     return MARNOLDI_OK;
 }
-
-}  // extern "C"
 
 int marnoldi::setup_with_allocator(marnoldi_ctx **out, int64_t n_block_rows, const int64_t *row_ptr,
                                    const int32_t *col_idx, const double *H_vals, const double *S_vals,
@@ -936,6 +978,52 @@ int marnoldi_kernel_stats(marnoldi_ctx *c, int kind, const char **name, int64_t 
     return MARNOLDI_OK;
 }
 
+int marnoldi_set_members(marnoldi_ctx *c, int n_members, const int64_t *atom_offsets,
+                         const double *electron_counts)
+{
+    if (!c) return MARNOLDI_EINVAL;
+    c->err.clear();
+    c->solved = false;
+    c->mem_atom.clear();
+    c->mem_ne.clear();
+    c->mem_col.clear();
+    if (n_members == 0) return MARNOLDI_OK;
+    if (n_members < 0 || !atom_offsets || !electron_counts)
+        return fail(c, MARNOLDI_EINVAL, "need n_members >= 0, atom_offsets and electron_counts");
+    if (atom_offsets[0] != 0 || atom_offsets[n_members] != c->nbr)
+        return fail(c, MARNOLDI_EINVAL, "atom_offsets must run from 0 to n_block_rows");
+    for (int q = 0; q < n_members; ++q) {
+        if (atom_offsets[q + 1] <= atom_offsets[q])
+            return fail(c, MARNOLDI_EINVAL, "member %d is empty or the offsets descend", q);
+        if (atom_offsets[q] % 8 != 0)
+            return fail(c, MARNOLDI_EINVAL, "member %d starts at atom %lld, not a multiple of 8", q,
+                        (long long)atom_offsets[q]);
+        if (!(electron_counts[q] > 0.0) || !std::isfinite(electron_counts[q]))
+            return fail(c, MARNOLDI_EINVAL, "member %d: electron count must be positive and finite", q);
+        for (int64_t I = atom_offsets[q]; I < atom_offsets[q + 1]; ++I)
+            for (int64_t k = c->rp[I]; k < c->rp[I + 1]; ++k)
+                if (c->ci[k] < atom_offsets[q] || c->ci[k] >= atom_offsets[q + 1])
+                    return fail(c, MARNOLDI_EINVAL, "block (%lld, %d) couples member %d to another member",
+                                (long long)I, c->ci[k], q);
+    }
+    c->mem_atom.assign(atom_offsets, atom_offsets + n_members + 1);
+    c->mem_ne.assign(electron_counts, electron_counts + n_members);
+    return MARNOLDI_OK;
+}
+
+int marnoldi_member_energy(marnoldi_ctx *c, int member, double *band_energy, double *mu,
+                           double *electron_count_out)
+{
+    if (!c) return MARNOLDI_EINVAL;
+    if (!c->solved) return fail(c, MARNOLDI_ESTATE, "energy requested before a successful solve");
+    if (c->mem_atom.empty() || member < 0 || member + 1 >= (int)c->mem_atom.size())
+        return fail(c, MARNOLDI_EINVAL, "no member %d", member);
+    if (band_energy) *band_energy = c->mem_E[member];
+    if (mu) *mu = c->mem_mu[member];
+    if (electron_count_out) *electron_count_out = c->mem_N[member];
+    return MARNOLDI_OK;
+}
+
 int marnoldi_set_autotune(int mode)
 {
     if (mode != 0 && mode != 1) return MARNOLDI_EINVAL;
@@ -995,8 +1083,17 @@ int marnoldi_solve(marnoldi_ctx *c, const int64_t *columns, int64_t ncols, int n
     }
     if (!(kT > 0.0) || !std::isfinite(kT)) return fail(c, MARNOLDI_EINVAL, "kT must be positive and finite");
     if (mu_fixed && !std::isfinite(*mu_fixed)) return fail(c, MARNOLDI_EINVAL, "mu_fixed must be finite");
-    if (!mu_fixed && !(electron_count > 0.0 && std::isfinite(electron_count)))
+    const bool members = !c->mem_atom.empty();
+    if (members) {
+        // every member's own bisection, over its own columns, in global mode
+        if (regional || columns || mu_fixed)
+            return fail(c, MARNOLDI_EINVAL, "a solve of members takes every real orbital, global mode and "
+                                            "a Fermi level by bisection");
+        if (nu > 253)
+            return fail(c, MARNOLDI_EINVAL, "a solve of members needs nu <= 253 (got %d)", nu);
+    } else if (!mu_fixed && !(electron_count > 0.0 && std::isfinite(electron_count))) {
         return fail(c, MARNOLDI_EINVAL, "electron_count must be positive and finite");
+    }
     // column list
     std::vector<int64_t> cols;
     if (!columns) {
@@ -1041,7 +1138,14 @@ int marnoldi_solve(marnoldi_ctx *c, const int64_t *columns, int64_t ncols, int n
         const int64_t J = cols[q] >> 2;
         prow += 4 * (c->rp[J + 1] - c->rp[J]);
     }
-    const int64_t m_vec = regional ? 4 * (int64_t)region_atoms : c->m;
+    // vector length: the region, the largest member, or the structure
+    int64_t m_vec = regional ? 4 * (int64_t)region_atoms : c->m;
+    if (members) {
+        m_vec = 0;
+        for (size_t q = 0; q + 1 < c->mem_atom.size(); ++q)
+            m_vec = std::max<int64_t>(m_vec, 4 * (c->mem_atom[q + 1] - c->mem_atom[q]));
+    }
+    const int64_t ntile_min = regional ? 0 : (c->nbr + 7) / 8;
     int64_t B = c->batch_override;
     if (B <= 0) {
         const ColumnShape shape = column_shape(m_vec, c->prec);
@@ -1053,7 +1157,7 @@ int marnoldi_solve(marnoldi_ctx *c, const int64_t *columns, int64_t ncols, int n
     }
     B = clamp_batch(B, nc, regional);
     SolvePlan plan;
-    if (!plan_solve(m_vec, c->prec, nu, region_atoms, c->maxrow, nc, prow, B, plan))
+    if (!plan_solve(m_vec, c->prec, nu, region_atoms, c->maxrow, nc, prow, B, ntile_min, plan))
         return fail(c, MARNOLDI_EINVAL, "nu = %d with %d blocks per row exceeds the eigensolver's shared memory",
                     nu, c->maxrow);
     c->last_batch = B;
@@ -1107,7 +1211,7 @@ int marnoldi_solve(marnoldi_ctx *c, const int64_t *columns, int64_t ncols, int n
     kb.status = (int *)(wb + plan.oS);
     kb.nu_eff = (int *)(wb + plan.oN);
     kb.m = m_vec;
-    kb.ntile = (int)(shape.m_pad / 32);
+    kb.ntile = (int)plan.ntile;
     kb.thop = (uint8_t *)(wb + plan.oTh);
     kb.tinv = (uint16_t *)(wb + plan.oTo);
     kb.tcnt = (int *)(wb + plan.oTc);
@@ -1239,28 +1343,55 @@ int marnoldi_solve(marnoldi_ctx *c, const int64_t *columns, int64_t ncols, int n
         mu = *mu_fixed;
         if ((rc = count_at(c, mu, kT, &N, &E))) return rc;
     } else {
-        // level range and the whole bisection on the device, one read-back
-        if ((rc = launch(c, KK_COUNT, [&] {
-                 return launch_bisection(c->st, kT, electron_count, c->d_partial, c->d_ticket, c->d_range,
-                                         c->d_out, c->d_bisect, c->stream);
-             })))
-            return rc;
-        e = cudaMemcpyAsync(c->h_out, c->d_bisect, sizeof(BisectState), cudaMemcpyDeviceToHost, c->stream);
-        if (e != cudaSuccess) return fail_cuda(c, e, "bisection read-back");
-        if ((rc = sync(c, "bisection"))) return rc;
-        BisectState bs;
-        memcpy(&bs, c->h_out, sizeof bs);
-        // one launch each of the range and of the graph was counted; add the
-        // loop's kernels (a step and a count per iteration)
-        c->launches[KK_MINMAX] += 1;
-        c->launches[KK_COUNT] += bs.steps - 1;
-        c->launches[KK_BISECT] += bs.steps;
-        if (bs.status == 1)
-            return fail(c, MARNOLDI_ENOCONV, "electron count %.6g outside [N(lo) = %.6g, N(hi) = %.6g]",
-                        electron_count, bs.Nlo, bs.Nhi);
-        mu = bs.mu;
-        N = bs.N;
-        E = bs.E;
+        // level range and the whole bisection on the device, one read-back;
+        // members: one bisection over each member's columns
+        const size_t nmem = members ? c->mem_atom.size() - 1 : 1;
+        std::vector<int64_t> col0(nmem + 1, 0);
+        if (members) {
+            size_t q = 0;
+            for (size_t m = 0; m < nmem; ++m) {
+                col0[m] = (int64_t)q;
+                while (q < cols.size() && (cols[q] >> 2) < c->mem_atom[m + 1]) ++q;
+            }
+        }
+        col0[nmem] = nc;
+        std::vector<double> mmu(nmem), mN(nmem), mE(nmem);
+        for (size_t m = 0; m < nmem; ++m) {
+            const double ne = members ? c->mem_ne[m] : electron_count;
+            const ColumnState sub = column_view(c->st, col0[m], col0[m + 1]);
+            if (sub.ncols == 0)
+                return fail(c, MARNOLDI_EINVAL, "member %zu has no real orbitals", m);
+            if ((rc = launch(c, KK_COUNT, [&] {
+                     return launch_bisection(sub, kT, ne, c->d_partial, c->d_ticket, c->d_range, c->d_out,
+                                             c->d_bisect, c->stream);
+                 })))
+                return rc;
+            e = cudaMemcpyAsync(c->h_out, c->d_bisect, sizeof(BisectState), cudaMemcpyDeviceToHost, c->stream);
+            if (e != cudaSuccess) return fail_cuda(c, e, "bisection read-back");
+            if ((rc = sync(c, "bisection"))) return rc;
+            BisectState bs;
+            memcpy(&bs, c->h_out, sizeof bs);
+            // one launch each of the range and of the graph was counted; add the
+            // loop's kernels (a step and a count per iteration)
+            c->launches[KK_MINMAX] += 1;
+            c->launches[KK_COUNT] += bs.steps - 1;
+            c->launches[KK_BISECT] += bs.steps;
+            if (bs.status == 1)
+                return fail(c, MARNOLDI_ENOCONV, "electron count %.6g outside [N(lo) = %.6g, N(hi) = %.6g]%s",
+                            ne, bs.Nlo, bs.Nhi, members ? " for a member" : "");
+            mmu[m] = bs.mu;
+            mN[m] = bs.N;
+            mE[m] = bs.E;
+            N += bs.N;
+            E += bs.E;
+        }
+        mu = mmu[0];
+        if (members) {
+            c->mem_col = col0;
+            c->mem_mu = mmu;
+            c->mem_N = mN;
+            c->mem_E = mE;
+        }
     }
     if ((rc = sync(c, "solve"))) return rc;
     std::vector<int> est(nc);
@@ -1292,9 +1423,18 @@ int marnoldi_density_device(marnoldi_ctx *c, double *rho, double *rhoE)
     cudaError_t e = cudaMemsetAsync(rho, 0, bytes, c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(rhoE, 0, bytes, c->stream);
     if (e != cudaSuccess) return fail_cuda(c, e, "density clear");
-    return launch(c, KK_DENSITY, [&] {
-        return launch_density(c->A, c->st, c->mu, c->kT, rho, rhoE, c->stream);
-    });
+    if (c->mem_atom.empty())
+        return launch(c, KK_DENSITY, [&] {
+            return launch_density(c->A, c->st, c->mu, c->kT, rho, rhoE, c->stream);
+        });
+    for (size_t m = 0; m + 1 < c->mem_col.size(); ++m) {   // each member at its own Fermi level
+        const ColumnState sub = column_view(c->st, c->mem_col[m], c->mem_col[m + 1]);
+        const int rc = launch(c, KK_DENSITY, [&] {
+            return launch_density(c->A, sub, c->mem_mu[m], c->kT, rho, rhoE, c->stream);
+        });
+        if (rc) return rc;
+    }
+    return MARNOLDI_OK;
 }
 
 int marnoldi_density(marnoldi_ctx *c, double *rho, double *rhoE)
@@ -1330,6 +1470,7 @@ int marnoldi_level_range(marnoldi_ctx *c, double *eps_min, double *eps_max)
 {
     if (!c || !eps_min || !eps_max) return MARNOLDI_EINVAL;
     if (!c->solved) return fail(c, MARNOLDI_ESTATE, "level range requested before a successful solve");
+    if (!c->mem_atom.empty()) return fail(c, MARNOLDI_EINVAL, "level range of a context with members");
     int rc = launch(c, KK_MINMAX, [&] {
         return launch_minmax(c->st, c->d_partial, c->d_ticket, c->d_out, c->stream);
     });
@@ -1346,6 +1487,7 @@ int marnoldi_fermi_at(marnoldi_ctx *c, double mu, double kT, double *N, double *
 {
     if (!c || !(kT > 0.0) || !std::isfinite(mu) || !std::isfinite(kT)) return MARNOLDI_EINVAL;
     if (!c->solved) return fail(c, MARNOLDI_ESTATE, "Fermi level set before a successful solve");
+    if (!c->mem_atom.empty()) return fail(c, MARNOLDI_EINVAL, "one Fermi level for a context with members");
     double n = 0.0, en = 0.0;
     const int rc = count_at(c, mu, kT, &n, &en);
     if (rc) return rc;

@@ -43,6 +43,19 @@ int setup_with_allocator(marnoldi_ctx **out, int64_t n_block_rows, const int64_t
                          int precision, void *cuda_stream, marnoldi_alloc_fn alloc,
                          marnoldi_free_fn free_fn, void *user);
 
+// What a solve's memory depends on, from a block pattern: block rows, blocks,
+// real orbitals (columns), their pattern rows, the longest block row, and the
+// Krylov-vector length (4 n_block_rows; for a union of structures, 4 x the
+// largest member's span).
+struct PatternStats {
+    int64_t nbr = 0, nnzb = 0, nc = 0, prow = 0, m_vec = 0;
+    int maxrow = 1;
+};
+int pattern_stats(int64_t n_block_rows, const int64_t *row_ptr, const uint8_t *orbital_mask, PatternStats &st);
+// marnoldi_footprint from the statistics (every real orbital solved).
+int footprint_of(const PatternStats &st, int precision, int nu, int region_atoms, const double *box,
+                 int64_t batch_columns, size_t *bytes, int64_t *batch_used);
+
 // Let `kernel` launch with up to `bytes` of dynamic shared memory.  The limit
 // only grows, and callers on several threads may race: one lock orders them.
 cudaError_t allow_dynamic_smem(const void *kernel, size_t bytes);
@@ -98,6 +111,8 @@ struct KrylovBatch {
     // Column c's vectors (K, SK, U, Ulo) are stored in its tile order: entry r
     // at position vpos(r) = 32 tinv[r / 32] + r % 32.  w_i vanishes outside
     // the first tcnt[i] tiles, S w_i and H w_i outside the first tcnt[i + 1].
+    // ntile (tiles of the structure) is at least m_pad / 32; it is larger for
+    // a union of structures, whose columns only ever use their own tiles.
     int ntile = 0;
     uint8_t *thop = nullptr;
     uint16_t *tinv = nullptr;

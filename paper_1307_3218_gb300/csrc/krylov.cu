@@ -301,7 +301,9 @@ __global__ void __launch_bounds__(256) spmm_hs_kernel(
     }
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
-        if (!L[h].live) continue;
+        // rows outside the support get their zeros, except rows of another
+        // structure of a union, whose tiles may sit past this column's positions
+        if (!L[h].live || yo[h] >= ldu) continue;
         if constexpr (kF) {
             float yh[4], yl[4];
 #pragma unroll
@@ -699,7 +701,7 @@ template <typename VT, int VPT, int T>
 cudaError_t gs_dispatch(const KrylovBatch &b, int n, int need_w, double tau, cudaStream_t s)
 {
     using Cfg = GsCfg<VT, VPT, T>;
-    if (b.shape.m_pad != (int64_t)VPT * T || b.ntile != VPT * T / 32 || !b.tcnt || !b.Lsub)
+    if (b.shape.m_pad != (int64_t)VPT * T || (int64_t)b.ntile * 32 < b.shape.m_pad || !b.tcnt || !b.Lsub)
         return cudaErrorInvalidValue;
     const size_t smem = (size_t)VPT * T * sizeof(VT) * Cfg::kSmemVectors;
     cudaError_t e = allow_dynamic_smem((const void *)gs_kernel<VT, VPT, T>, smem);

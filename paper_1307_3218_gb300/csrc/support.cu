@@ -10,6 +10,12 @@
 // cell cover a small part of it: on 4096-atom amorphous carbon at nu = 30 the
 // Gram-Schmidt sweeps touch about two thirds of the dense entries.
 //
+// A structure may be a block-diagonal union of independent structures whose
+// atom ranges start at multiples of 8 atoms: the search from J never leaves
+// J's own structure, so only its tiles get the first positions and the
+// vectors need only as many positions as the largest of them (tiles of the
+// other structures sort behind and are never read or written).
+//
 // support_kernel: one CTA per batch column runs a breadth-first search from
 // J over the block pattern (global mode) or the region's local pattern
 // (regional mode), capped at nu + 1 hops, and summarises it per tile of 8
@@ -97,7 +103,10 @@ cudaError_t launch_support(const DeviceMatrix &A, const RegionMaps *rm, const Kr
     // hop counts up to nu + 1 matter; a uint8 holds up to 254 of them (255 =
     // farther), and a tile beyond 254 hops is live for every level from 255 on
     const int nlev = b.nu + 1, maxlev = nlev < 254 ? nlev : 254;
-    if (b.ntile > kMaxTiles || b.ntile * 32 != b.shape.m_pad) return cudaErrorInvalidValue;
+    if (b.ntile > kMaxTiles || (int64_t)b.ntile * 32 < b.shape.m_pad) return cudaErrorInvalidValue;
+    // more tiles than vector positions (a union of structures, each within
+    // m_pad): only tiles within the search depth may get positions in use
+    if ((int64_t)b.ntile * 32 > b.shape.m_pad && maxlev < nlev) return cudaErrorInvalidValue;
     if (rm) {
         if (rm->n_reg > kMaxRegion) return cudaErrorInvalidValue;
         support_kernel<true><<<b.nb, 256, rm->n_reg, s>>>(

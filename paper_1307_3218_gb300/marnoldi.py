@@ -89,6 +89,8 @@ def load(path: str | None = None):
                                         C.POINTER(d), i32]),
         "marnoldi_count_noalloc": (i32, [P, P, P, i64, i32, d, d, P, P]),
         "marnoldi_forces": (i32, [P, P, P, P]),
+        "marnoldi_set_members": (i32, [P, i32, P, P]),
+        "marnoldi_member_energy": (i32, [P, i32, P, P, P]),
         "marnoldi_set_autotune": (i32, [i32]),
         "marnoldi_gs_shape": (i32, [P, P, P]),
         "marnoldi_device_bytes": (i32, [P, P, P]),
@@ -98,6 +100,7 @@ def load(path: str | None = None):
                                          P]),
         "marnoldi_server_wait": (i32, [P, i64, d, P, P, P, C.c_size_t]),
         "marnoldi_server_stats": (i32, [P, P]),
+        "marnoldi_server_set_group_limit": (i32, [P, i32]),
         "marnoldi_server_last_error": (C.c_char_p, []),
         "marnoldi_server_destroy": (None, [P]),
         "marnoldi_last_error": (C.c_char_p, [P]),
@@ -310,6 +313,60 @@ def marnoldi_green(ctx: Context, zs) -> np.ndarray:
     return G
 
 
+def marnoldi_set_members(ctx: Context, atom_offsets, electron_counts) -> None:
+    """Declare the context's structure a block-diagonal union of members (see the C header)."""
+    off = np.ascontiguousarray(atom_offsets, dtype=np.int64)
+    ne = np.ascontiguousarray(electron_counts, dtype=np.float64)
+    n = off.size - 1 if off.size else 0
+    if n and ne.size != n:
+        raise MarnoldiError(MARNOLDI_EINVAL, "one electron count per member")
+    _check(load().marnoldi_set_members(ctx.handle, int(n), _ptr(off) if n else None,
+                                       _ptr(ne) if n else None), ctx)
+
+
+def marnoldi_member_energy(ctx: Context, member: int) -> tuple[float, float, float]:
+    E, mu, N = C.c_double(), C.c_double(), C.c_double()
+    _check(load().marnoldi_member_energy(ctx.handle, int(member), C.byref(E), C.byref(mu), C.byref(N)), ctx)
+    return E.value, mu.value, N.value
+
+
+def union_of(systems, pad_to: int = 8):
+    """Block-diagonal union of TBSystem-like structures, each starting at a multiple of
+    `pad_to` atoms (padding atoms carry four padding orbitals: H = 0, S = I, no coupling).
+
+    Returns (n_block_rows, row_ptr, col_idx, H, S, orbital_mask, atom_offsets, block_offsets),
+    block_offsets[q] being the first block of member q (its blocks are contiguous).
+    """
+    rps, cis, Hs, Ss, masks, offs, boffs = [], [], [], [], [], [0], []
+    nb_total = 0
+    atom = 0
+    for q, t in enumerate(systems):
+        boffs.append(nb_total)
+        n = int(t.n_block_rows)
+        nnzb = int(t.row_ptr[-1])
+        rps.append(np.asarray(t.row_ptr[1:], dtype=np.int64) + nb_total)
+        cis.append(np.asarray(t.col_idx, dtype=np.int64) + atom)
+        Hs.append(np.asarray(t.H, dtype=np.float64).reshape(nnzb, 4, 4))
+        Ss.append(np.asarray(t.S, dtype=np.float64).reshape(nnzb, 4, 4))
+        masks.append(np.asarray(t.orbital_mask, dtype=np.uint8).reshape(-1)
+                     if t.orbital_mask is not None else np.ones(4 * n, np.uint8))
+        atom += n
+        nb_total += nnzb
+        pad = (-atom) % pad_to if q + 1 < len(systems) else 0
+        if pad:
+            rps.append(nb_total + 1 + np.arange(pad, dtype=np.int64))
+            cis.append(atom + np.arange(pad, dtype=np.int64))
+            Hs.append(np.zeros((pad, 4, 4)))
+            Ss.append(np.broadcast_to(np.eye(4), (pad, 4, 4)).copy())
+            masks.append(np.zeros(4 * pad, np.uint8))
+            atom += pad
+            nb_total += pad
+        offs.append(atom)
+    row_ptr = np.concatenate([[0]] + rps).astype(np.int64)
+    return (atom, row_ptr, np.concatenate(cis).astype(np.int32), np.concatenate(Hs), np.concatenate(Ss),
+            np.concatenate(masks), np.array(offs, dtype=np.int64), np.array(boffs, dtype=np.int64))
+
+
 def marnoldi_forces(ctx: Context, dH_dd, dS_dd) -> np.ndarray:
     """Forces (n_block_rows, 3) from the last solve; dH_dd, dS_dd of shape (3, nnzb, 4, 4)."""
     dH = np.ascontiguousarray(dH_dd, dtype=np.float64)
@@ -503,11 +560,15 @@ class Server:
                 "t_start": res[4], "t_end": res[5], "latency_s": res[5] - res[3],
                 "footprint_bytes": int(res[6]), "batch": int(res[7]), "rho": held[7], "rhoE": held[8]}
 
+    def set_group_limit(self, max_members: int) -> None:
+        """Most requests run as members of one launch group (1 = no grouping)."""
+        _server_check(load().marnoldi_server_set_group_limit(self.handle, int(max_members)))
+
     def stats(self) -> dict:
-        v = np.zeros(7, np.int64)
+        v = np.zeros(9, np.int64)
         _server_check(load().marnoldi_server_stats(self.handle, _ptr(v)))
         keys = ("queued", "running", "completed", "bytes_in_use", "peak_bytes", "peak_running",
-                "pool_reserved_high")
+                "pool_reserved_high", "groups", "largest_group")
         return {k: int(x) for k, x in zip(keys, v)}
 
     def close(self) -> None:

@@ -157,6 +157,7 @@ def test_admission_by_footprint(gpu):
     fp, _ = m.marnoldi_footprint(a.n_block_rows, a.row_ptr, a.orbital_mask, None, 1, 30, 0, 1 << 40)
     budget = int(1.5 * fp)   # one request at a time fits, two do not
     with m.Server(workers=4, hbm_budget_bytes=budget) as srv:
+        srv.set_group_limit(1)   # requests one by one (grouping is tested below)
         ids = [srv.submit_system(a, 1, 30, 0, a.n_electrons, KT, batch_columns=1 << 40) for _ in range(4)]
         res = [srv.wait(i) for i in ids]
         st = srv.stats()
@@ -228,3 +229,25 @@ def test_footprint_equals_device_peak(gpu, prec, region):
         m.marnoldi_destroy(ctx)
         assert peak == fp, (B, peak, fp)
         assert cur < peak
+
+
+@pytest.mark.gpu
+def test_queued_requests_share_launches(gpu):
+    """Requests of one class that wait together run as members of one union."""
+    small = [amorphous_system(160, seed=11), amorphous_system(256, seed=12), amorphous_system(200, seed=13),
+             amorphous_system(256, seed=14)]                 # M 640..1024: vectors of 1,024 entries
+    tiny = [config_c1(seed=1), config_c1(seed=2)]           # M 256
+    with m.Server(workers=1, hbm_budget_bytes=8 << 30) as srv:
+        big = srv.submit_system(amorphous_system(1024, seed=4), 1, 30)   # keeps the worker busy
+        ids = [srv.submit_system(t, 1, 30, 0, t.n_electrons, KT) for t in small + tiny]
+        srv.wait(big)
+        got = [srv.wait(i) for i in ids]
+        st = srv.stats()
+    assert st["groups"] >= 2 and st["largest_group"] >= 3
+    starts = {round(g["t_start"], 9) for g in got}
+    assert len(starts) <= 3                                   # a few launch groups, not six requests
+    for t, g in zip(small + tiny, got):
+        a = _alone(t, 1, 30, 0)
+        assert (g["band_energy"], g["mu"], g["N"]) == (a["band_energy"], a["mu"], a["N"])
+        np.testing.assert_array_equal(g["rho"], a["rho"])
+        np.testing.assert_array_equal(g["rhoE"], a["rhoE"])
