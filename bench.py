@@ -643,17 +643,18 @@ def serving(m, t4096, requests: int, workers: int, budget: int, prec: int):
         shapes[f"{n}_atoms_nu{nu}"] = "x".join(map(str, m.marnoldi_gs_shape(ctx)))
         m.marnoldi_destroy(ctx)
 
-    def run(nworkers, gaps=None):
+    def run(nworkers, gaps=None, group=16, reqs=None):
+        reqs = [(pool[n], nu) for n, nu in trace] if reqs is None else reqs
         with m.Server(workers=nworkers, hbm_budget_bytes=budget) as srv:
+            srv.set_group_limit(group)
             # warm the server's memory pool once
             srv.wait(srv.submit_system(pool[512], prec, 30, 0, pool[512].n_electrons, 0.1))
             ids, t0 = [], time.perf_counter()
-            for k, (n, nu) in enumerate(trace):
+            for k, (sysm, nu) in enumerate(reqs):
                 if gaps is not None:
                     due = t0 + gaps[k]
                     while time.perf_counter() < due:
                         time.sleep(min(0.002, max(0.0, due - time.perf_counter())))
-                sysm = pool[n]
                 ids.append(srv.submit_system(sysm, prec, nu, 0, sysm.n_electrons, 0.1))
             res = [srv.wait(i) for i in ids]
             st = srv.stats()
@@ -662,14 +663,31 @@ def serving(m, t4096, requests: int, workers: int, budget: int, prec: int):
         lat = np.array([r["latency_s"] for r in res]) * 1e3
         return dict(wall=wall, lat=lat, stats=st)
 
-    seq = run(1)
+    seq = run(1, group=1)
     burst = run(workers)
     rate = 0.6 * requests / burst["wall"]
     gaps = np.cumsum(rng.exponential(1.0 / rate, size=requests))
     gaps -= gaps[0]
     pois = run(workers, gaps)
     lat = pois["lat"]
+    # many small molecules: 64-atom diamond cells (8 seeds), all at once, with
+    # and without grouping queued requests into shared launches
+    from tbsynth import config_c1
+    cells = [config_c1(seed=s) for s in range(8)]
+    small = [(cells[k % 8], 30) for k in range(128)]
+    run(workers, group=16, reqs=small[:16])   # warm-up of this class
+    solo = run(workers, group=1, reqs=small)
+    grouped = run(workers, group=16, reqs=small)
+    ncols_small = sum(c.real_columns().size for c, _ in small)
+    out_small = {"requests": len(small), "atoms": 64, "nu": 30, "columns": int(ncols_small),
+                 "one_by_one": {"columns_per_s": round(ncols_small / solo["wall"], 1),
+                                "p50_ms": round(float(np.percentile(solo["lat"], 50)), 2)},
+                 "grouped": {"columns_per_s": round(ncols_small / grouped["wall"], 1),
+                             "p50_ms": round(float(np.percentile(grouped["lat"], 50)), 2),
+                             "groups": grouped["stats"]["groups"],
+                             "largest_group": grouped["stats"]["largest_group"]}}
     return {
+        "small_molecules": out_small,
         "trace": f"{requests} requests, atoms {list(SERVE_SIZES)} with p {list(SERVE_SIZE_P)}, "
                  f"nu 30 (nu 100 for 1/4 of those <= 1024 atoms), {'mixed' if prec else 'fp64'}, "
                  f"all real orbitals, density matrices returned to the host",
@@ -679,8 +697,9 @@ def serving(m, t4096, requests: int, workers: int, budget: int, prec: int):
         "concurrent": {"wall_s": round(burst["wall"], 3),
                        "columns_per_s": round(ncols_total / burst["wall"], 1),
                        "peak_running": burst["stats"]["peak_running"],
+                       "groups": burst["stats"]["groups"], "largest_group": burst["stats"]["largest_group"],
                        "peak_footprint_gb": round(burst["stats"]["peak_bytes"] / 2**30, 2)},
-        "poisson": {"offered_requests_per_s": round(rate, 2),
+        "poisson": {"offered_requests_per_s": round(rate, 2), "groups": pois["stats"]["groups"],
                     "p50_ms": round(float(np.percentile(lat, 50)), 2),
                     "p99_ms": round(float(np.percentile(lat, 99)), 2),
                     "mean_ms": round(float(lat.mean()), 2), "max_ms": round(float(lat.max()), 2),
