@@ -196,6 +196,32 @@ int marnoldi_green(marnoldi_ctx *ctx, const double *z_re_im, int nz, double *G_r
 int marnoldi_forces(marnoldi_ctx *ctx, const double *dH_dd, const double *dS_dd, double *F);
 
 /*
+ * The k-th eigen level and eigenvector from the subspace levels and vectors
+ * (arXiv:1307.3218, Section 2, the paragraph on the k-th eigen level, Eq. 3,
+ * and the sign rule of the Appendix), after a global-mode marnoldi_solve of
+ * every real orbital of one structure (no members) with nu <= 128.
+ *   n(eta) = sum_j sum_a w_a f((eps_a - eta) / sigma) (the integrated density
+ *   of states, each level's step smoothed by the Fermi function of width
+ *   sigma), eta(n) its inverse by bisection (eta(0) = -inf, eta(M_real) =
+ *   +inf), *eps_k = eta(k - 1/2).  phi (host, M doubles; 0 on padding
+ *   orbitals and on columns without weight in the window) gets
+ *   phi_j = sum_a s_a t_a W_a with t_a = e_j^T K v_a, the window
+ *   W_a = f((eps_a - eta(k)) / sigma) - f((eps_a - eta(k-1)) / sigma) (the
+ *   smoothed delta of Eq. 3 integrated from eta(k-1) to eta(k)) and the signs
+ *   s_a = sign(v_ref^T K v_a) (+1 at 0), v_ref the subspace eigenvector K v_a
+ *   (over all M rows) of largest |t_a W_a| over all columns and levels, the
+ *   first among equals.  Columns whose largest |t_a W_a| is below 1e-12 of the
+ *   reference's are left 0.  eta_bounds (may be NULL): eta(k-1), eta(k).
+ * The signs come from a second pass: the reference column's subspace vector by
+ * inverse iteration, then a solve of the columns in the window with the
+ * projection of their stored vectors on it.  The context's last solve stays.
+ * Errors: MARNOLDI_EINVAL (k outside [1, M_real], sigma <= 0, nu > 128, a
+ * regional, partial or member solve), MARNOLDI_ESTATE (no solve).
+ */
+int marnoldi_eigenstate(marnoldi_ctx *ctx, int64_t k, double sigma, double *eps_k, double *phi,
+                        double *eta_bounds);
+
+/*
  * Per-column results of the last solve, in the order of the solved columns
  * (host arrays; any may be NULL): nu_eff[ncols], eps[ncols*nu] (ascending
  * subspace levels, zero past nu_eff), w[ncols*nu] (weights

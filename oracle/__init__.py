@@ -404,3 +404,58 @@ def forces(sysm, rho: np.ndarray, rhoE: np.ndarray, dH: np.ndarray, dS: np.ndarr
         np.add.at(F[:, x], rows, trH - trS)
         np.add.at(F[:, x], cols, -trH + trS)
     return F
+
+
+def _fermi_np(x):
+    """f(x) = 1 / (1 + e^x) elementwise, through e^(-|x|); +-inf give 0 and 1."""
+    x = np.asarray(x, dtype=np.float64)
+    e = np.exp(-np.abs(x))
+    return np.where(x >= 0, e / (1.0 + e), 1.0 / (1.0 + e))
+
+
+def idos(c: Columns, eta: float, sigma: float) -> float:
+    """Integrated density of states n(eta) = sum_j sum_a w_a f((eps_a - eta) / sigma), one state per
+    level (no spin factor): the count of levels below eta, each step smoothed by the Fermi function
+    of width sigma (Section 2, the paragraph on the k-th eigen level)."""
+    e, w = valid_levels(c)
+    return float(np.sum(w * _fermi_np((e - eta) / sigma)))
+
+
+def eigenstate(sysm, k: int, nu: int, sigma: float, tau: float = TAU_FP64):
+    """The k-th eigen level and vector from the subspace levels and vectors (Section 2, Eq. 3 of the
+    paper's eigenstate paragraph, and the inner-product sign rule of its Appendix).
+
+    n(eta) as in idos(); eta(n) its inverse by the bisection of bisect() on 2 n (the count there
+    carries the spin factor 2), eta(0) = -inf and eta(M_real) = +inf; eps_k = eta(k - 1/2).  The
+    smoothed delta of Eq. 3 is read as the derivative of the Fermi step of width sigma, so
+    int_{eta(k-1)}^{eta(k)} delta(eps - eps_a) = f((eps_a - eta(k)) / sigma) - f((eps_a - eta(k-1)) / sigma)
+    =: W_a.  Component j of phi_k: sum_a s_a t_a W_a with t_a = e_j^T K v_a.  Signs: the reference is
+    the subspace eigenvector (full-space K v_a over all columns j and levels a) of largest |t_a W_a|
+    (first in column, then level order among equals); s_a = sign(v_ref^T K v_a), +1 when it is 0.
+    Returns (eps_k, phi (M,), info).  Small systems only: it keeps every column's full vectors.
+    """
+    cols = sysm.real_columns()
+    c = columns(sysm, cols, nu, tau=tau, full_rows=True)
+    e, w = valid_levels(c)
+    m_real = cols.size
+
+    def eta(n):
+        if n <= 0:
+            return -np.inf
+        if n >= m_real:
+            return np.inf
+        return bisect(e, w, 2.0 * n, sigma)[0]
+
+    lo, ek, hi = eta(k - 1), eta(k - 0.5), eta(k)
+    valid = np.arange(nu)[None, :] < c.nu_eff[:, None]
+    W = np.where(valid, _fermi_np((c.eps - hi) / sigma) - _fermi_np((c.eps - lo) / sigma), 0.0)
+    a = np.where(valid, c.t * W, 0.0)
+    q, al = np.unravel_index(int(np.argmax(np.abs(a))), a.shape)
+    M = sysm.M
+    Yc = c.Y.reshape(cols.size, M, nu)
+    vref = Yc[q, :, al]
+    dots = np.einsum("r,crl->cl", vref, Yc)
+    s = np.where(dots < 0.0, -1.0, 1.0)
+    phi = np.zeros(M)
+    phi[cols] = np.sum(s * a, axis=1)
+    return ek, phi, dict(eta=(lo, hi), ref=(int(cols[q]), int(al)), columns=c)

@@ -19,7 +19,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 SOURCES = ["api.cu", "krylov.cu", "eigsub.cu", "outputs.cu", "region.cu", "support.cu", "noalloc.cu",
-           "server.cu"]
+           "server.cu", "eigstate.cu"]
 HEADERS = [os.path.join(CSRC, "internal.h"), os.path.join(INCLUDE, "marnoldi.h")]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -205,6 +205,13 @@ struct marnoldi_ctx {
     int64_t batch_override = 0;
     int64_t last_batch = 0;
     ColumnShape gs_shape{0, 0, 0};   // Gram-Schmidt launch shape of the last solve
+    KrylovBatch last_kb{};           // the last batch of the last solve (its workspace stays)
+    bool last_regional = false, last_all_real = false;
+    // projection of the stored vectors on proj_vec (M rows, device), turned
+    // by the eigensolve into proj_out[g * nu + a] = proj_vec^T K v_a
+    const double *proj_vec = nullptr;
+    double *proj_out = nullptr;
+    bool shares_structure = false;   // a view of another context's device structure
 
     // members: a block-diagonal union of independent structures (atom ranges
     // starting at multiples of 8 atoms), each with its own electron count and
@@ -273,6 +280,18 @@ void dfree(marnoldi_ctx *c, void *p, size_t bytes)
     if (c->free_fn) c->free_fn(p, bytes, (void *)c->stream, c->user);
     else cudaFreeAsync(p, c->stream);
 }
+
+// A device allocation of a context released (in stream order) at scope exit.
+struct DeviceBuffer {
+    marnoldi_ctx *c;
+    size_t bytes;
+    double *p;
+    DeviceBuffer(marnoldi_ctx *ctx, size_t n) : c(ctx), bytes(n), p(n ? (double *)dalloc(ctx, n) : nullptr) {}
+    ~DeviceBuffer() { if (p) dfree(c, p, bytes); }
+    DeviceBuffer(const DeviceBuffer &) = delete;
+    DeviceBuffer &operator=(const DeviceBuffer &) = delete;
+    double *get() const { return p; }
+};
 
 template <typename T>
 int dupload(marnoldi_ctx *c, T **dst, const T *src, size_t n, const char *what)
@@ -642,7 +661,7 @@ bool plan_solve(int64_t m_vec, int prec, int nu, int region_atoms, int maxrow, i
     // shared memory when it fits, else in a global scratch per subspace
     EigScratch &es = p.es;
     es = EigScratch{};
-    es.nr_max = 4 * maxrow + 2;
+    es.nr_max = 4 * maxrow + 3;   // e_1, q, the pattern rows and an optional projection row
     es.rcap = (int64_t)8 * nu * nu;
     es.scap = (int64_t)40 * nu;
     const size_t kSmemCap = (size_t)227 * 1024;
@@ -1272,6 +1291,9 @@ int marnoldi_solve(marnoldi_ctx *c, const int64_t *columns, int64_t ncols, int n
         }
         return MARNOLDI_OK;
     };
+    // projection scratch (batch columns x nu) while proj_vec is set
+    DeviceBuffer proj_buf(c, c->proj_vec ? (size_t)B * nu * sizeof(double) : 0);
+    if (c->proj_vec && !proj_buf.get()) return fail(c, MARNOLDI_ENOMEM, "device allocation for the projection failed");
     const TuneKey key{c->prec, nu, regional ? 1 : 0, mp};
     bool tune = false;
     if (autotune_mode()) {
@@ -1333,10 +1355,21 @@ int marnoldi_solve(marnoldi_ctx *c, const int64_t *columns, int64_t ncols, int n
             tune = false;
         }
         if ((rc = build(kb))) return rc;
+        if (c->proj_vec) {
+            if ((rc = launch(c, KK_EIGSTATE, [&] {
+                     return launch_project(kb, c->proj_vec, c->m, proj_buf.get(), c->stream);
+                 })))
+                return rc;
+            es.proj = proj_buf.get();
+            es.proj_out = c->proj_out;
+        }
         if ((rc = launch(c, KK_EIG, [&] { return launch_eig(c->A, kb, c->st, start, rmp, es, c->stream); })))
             return rc;
     }
     c->gs_shape = kb.shape;
+    c->last_kb = kb;
+    c->last_regional = regional;
+    c->last_all_real = columns == nullptr;
     // ---- Fermi level
     double mu = 0.0, N = 0.0, E = 0.0;
     if (mu_fixed) {
@@ -1553,6 +1586,155 @@ int marnoldi_forces(marnoldi_ctx *c, const double *dH, const double *dS, double 
     const int rs = sync(c, "forces");
     dfree(c, d, bytes);
     return rc ? rc : rs;
+}
+
+int marnoldi_eigenstate(marnoldi_ctx *c, int64_t k, double sigma, double *eps_k, double *phi,
+                        double *eta_bounds)
+{
+    if (!c || !eps_k || !phi) return MARNOLDI_EINVAL;
+    if (!c->solved) return fail(c, MARNOLDI_ESTATE, "eigenstate requested before a successful solve");
+    if (!c->mem_atom.empty() || c->last_regional || !c->last_all_real)
+        return fail(c, MARNOLDI_EINVAL, "the eigenstate needs a global-mode solve of every real orbital "
+                                        "of one structure");
+    if (c->nu > eigvec_max_nu())
+        return fail(c, MARNOLDI_EINVAL, "the eigenstate supports nu <= %d (got %d)", eigvec_max_nu(), c->nu);
+    if (!(sigma > 0.0) || !std::isfinite(sigma)) return fail(c, MARNOLDI_EINVAL, "sigma must be positive and finite");
+    const int64_t m_real = c->ncols;
+    if (k < 1 || k > m_real)
+        return fail(c, MARNOLDI_EINVAL, "k = %lld outside [1, %lld]", (long long)k, (long long)m_real);
+    // eta(n): the inverse integrated density of states, by the bisection on
+    // the level count (which carries the spin factor 2, so N = 2 n)
+    auto eta = [&](double n, double *out) -> int {
+        if (n <= 0.0) { *out = -INFINITY; return MARNOLDI_OK; }
+        if (n >= (double)m_real) { *out = INFINITY; return MARNOLDI_OK; }
+        int rc = launch(c, KK_COUNT, [&] {
+            return launch_bisection(c->st, sigma, 2.0 * n, c->d_partial, c->d_ticket, c->d_range, c->d_out,
+                                    c->d_bisect, c->stream);
+        });
+        if (rc) return rc;
+        cudaError_t e = cudaMemcpyAsync(c->h_out, c->d_bisect, sizeof(BisectState), cudaMemcpyDeviceToHost, c->stream);
+        if (e != cudaSuccess) return fail_cuda(c, e, "bisection read-back");
+        if ((rc = sync(c, "eigenstate bisection"))) return rc;
+        BisectState bs;
+        memcpy(&bs, c->h_out, sizeof bs);
+        c->launches[KK_MINMAX] += 1;
+        c->launches[KK_COUNT] += bs.steps - 1;
+        c->launches[KK_BISECT] += bs.steps;
+        if (bs.status == 1) return fail(c, MARNOLDI_ENOCONV, "n = %.6g outside the bracket of the levels", n);
+        *out = bs.mu;
+        return MARNOLDI_OK;
+    };
+    double lo, ek, hi;
+    int rc;
+    if ((rc = eta((double)k - 1.0, &lo)) || (rc = eta((double)k - 0.5, &ek)) || (rc = eta((double)k, &hi))) return rc;
+    const int64_t nc = c->ncols, M = c->m;
+    const int nu = c->nu;
+    // the weights of the window and the reference (column, level)
+    DeviceBuffer wbuf(c, (size_t)nc * (sizeof(double) + sizeof(int)) + 16);
+    if (!wbuf.get()) return fail(c, MARNOLDI_ENOMEM, "device allocation for the eigenstate failed");
+    double *colmax = wbuf.get();
+    int *colarg = (int *)(colmax + nc);
+    int64_t *argmax = (int64_t *)(((uintptr_t)(colarg + nc) + 7) & ~(uintptr_t)7);
+    if ((rc = launch(c, KK_EIGSTATE, [&] {
+             return launch_window(c->st, lo, hi, sigma, colmax, colarg, argmax, c->stream);
+         })))
+        return rc;
+    std::vector<double> hmax(nc);
+    std::vector<int> harg(nc);
+    int64_t cstar = -1;
+    cudaError_t e = cudaMemcpyAsync(hmax.data(), colmax, nc * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(harg.data(), colarg, nc * sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&cstar, argmax, sizeof(int64_t), cudaMemcpyDeviceToHost, c->stream);
+    if (e != cudaSuccess) return fail_cuda(c, e, "eigenstate weights read-back");
+    if ((rc = sync(c, "eigenstate weights"))) return rc;
+    *eps_k = ek;
+    if (eta_bounds) {
+        eta_bounds[0] = lo;
+        eta_bounds[1] = hi;
+    }
+    memset(phi, 0, (size_t)M * sizeof(double));
+    if (cstar < 0 || !(hmax[cstar] > 0.0)) return MARNOLDI_OK;   // no weight in the window
+    // columns whose contributions matter, in solved order
+    std::vector<int64_t> sel;
+    for (int64_t q = 0; q < nc; ++q)
+        if (hmax[q] > 0.0 && hmax[q] >= 1e-12 * hmax[cstar]) sel.push_back(c->cols[q]);
+    // a view of the structure with its own state and workspace: first the
+    // reference column alone (its vector K v_a, from its batch's workspace),
+    // then the selected columns with the projection on that vector
+    marnoldi_ctx *v = new marnoldi_ctx();
+    v->stream = c->stream;
+    v->prec = c->prec;
+    v->nbr = c->nbr;
+    v->nnzb = c->nnzb;
+    v->m = c->m;
+    v->maxrow = c->maxrow;
+    v->rp = c->rp;
+    v->ci = c->ci;
+    v->mask = c->mask;
+    v->alloc = c->alloc;
+    v->free_fn = c->free_fn;
+    v->user = c->user;
+    v->A = c->A;
+    v->shares_structure = true;
+    v->batch_override = c->batch_override;
+    auto done = [&](int code) {
+        for (int q = 0; q < KK_NKINDS; ++q) {
+            c->launches[q] += v->launches[q];
+            c->ms[q] += v->ms[q];
+        }
+        if (code && c->err.empty()) c->err = v->err;
+        marnoldi_destroy(v);
+        return code;
+    };
+    {
+        void *p = dalloc(v, kScratchBytes);
+        if (!p) return done(fail(c, MARNOLDI_ENOMEM, "device allocation for the eigenstate failed"));
+        v->owned.push_back({p, kScratchBytes});
+        v->d_partial = (double *)p;
+        v->d_out = (double *)((char *)p + kOffOut);
+        v->d_range = (double *)((char *)p + kOffRange);
+        v->d_bisect = (BisectState *)((char *)p + kOffBisect);
+        v->d_ticket = (unsigned *)((char *)p + kOffTicket);
+        e = cudaMemsetAsync(p, 0, kScratchBytes, v->stream);
+        if (e != cudaSuccess) return done(fail_cuda(c, e, "eigenstate scratch"));
+        if (!(v->h_out = pinned_slot())) return done(fail(c, MARNOLDI_ENOMEM, "pinned read-back slot"));
+    }
+    const double zero = 0.0;
+    const int64_t jref = c->cols[cstar];
+    if ((rc = marnoldi_solve(v, &jref, 1, nu, 0, 0.0, sigma, &zero))) return done(rc);
+    double eref = 0.0;
+    e = cudaMemcpyAsync(&eref, v->st.eps + harg[cstar], sizeof(double), cudaMemcpyDeviceToHost, v->stream);
+    if (e != cudaSuccess) return done(fail_cuda(c, e, "reference level read-back"));
+    if ((rc = sync(v, "reference level"))) return done(rc);
+    // buffers owned by the view, released with it
+    auto vbuf = [&](size_t bytes) -> double * {
+        void *q = dalloc(v, bytes);
+        if (q) v->owned.push_back({q, bytes});
+        return (double *)q;
+    };
+    double *vref = vbuf((size_t)M * sizeof(double));
+    double *proj = vbuf(sel.size() * (size_t)nu * sizeof(double));
+    double *phid = vbuf((size_t)M * sizeof(double));
+    if (!vref || !proj || !phid) return done(fail(c, MARNOLDI_ENOMEM, "eigenstate buffers"));
+    e = cudaMemsetAsync(vref, 0, (size_t)M * sizeof(double), v->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(phid, 0, (size_t)M * sizeof(double), v->stream);
+    if (e != cudaSuccess) return done(fail_cuda(c, e, "eigenstate buffers"));
+    if ((rc = launch(v, KK_EIGSTATE, [&] { return launch_eigvec(v->last_kb, 0, eref, M, vref, v->stream); })))
+        return done(rc);
+    v->proj_vec = vref;
+    v->proj_out = proj;
+    rc = marnoldi_solve(v, sel.data(), (int64_t)sel.size(), nu, 0, 0.0, sigma, &zero);
+    v->proj_vec = nullptr;
+    v->proj_out = nullptr;
+    if (rc) return done(rc);
+    if ((rc = launch(v, KK_EIGSTATE, [&] {
+             return launch_combine(v->st, proj, lo, hi, sigma, phid, v->stream);
+         })))
+        return done(rc);
+    e = cudaMemcpyAsync(phi, phid, (size_t)M * sizeof(double), cudaMemcpyDeviceToHost, v->stream);
+    if (e != cudaSuccess) return done(fail_cuda(c, e, "eigenvector read-back"));
+    rc = sync(v, "eigenvector");
+    return done(rc);
 }
 
 int marnoldi_column_stats(marnoldi_ctx *c, int32_t *nu_eff, double *eps, double *w)

@@ -61,7 +61,7 @@ __global__ void __launch_bounds__(kTriThreads) eig_tridiag_kernel(
     const int64_t *__restrict__ bcols, const int64_t *__restrict__ rp,
     const int32_t *__restrict__ ci, const int *__restrict__ reg, int n_reg, int cofs,
     double *__restrict__ D, double *__restrict__ E, double *__restrict__ RQ, int nr_max,
-    double *__restrict__ Ag, const double *__restrict__ Lsub)
+    double *__restrict__ Ag, const double *__restrict__ Lsub, const double *__restrict__ proj)
 {
     const int sc = blockIdx.x;
     const int c = cofs + sc;
@@ -84,7 +84,7 @@ __global__ void __launch_bounds__(kTriThreads) eig_tridiag_kernel(
     const int64_t jl = Rg ? 4 * (int64_t)(pJ < 0 ? 0 : pJ) + (j & 3) : j;
     const int64_t kb = rp[J];
     const int npat = 4 * (int)(rp[J + 1] - kb);
-    const int nr = npat + 2;
+    const int nr = npat + 2 + (proj ? 1 : 0);   // the projection row last
     const VT *Kc = K + (int64_t)c * nu * m_pad;
     for (int idx = tid; idx < n * n; idx += T) {
         const int i = idx / n, l = idx - (idx / n) * n;
@@ -99,6 +99,8 @@ __global__ void __launch_bounds__(kTriThreads) eig_tridiag_kernel(
             val = i == 0 ? 1.0 : 0.0;
         } else if (r == 1) {
             val = si * (double)Kc[(int64_t)i * m_pad + vpos(tinv, nb, c, jl)];
+        } else if (r == npat + 2) {
+            val = si * proj[(int64_t)c * nu + i];
         } else {
             const int atom = ci[kb + ((r - 2) >> 2)];
             const int64_t lr = Rg ? find_sorted(Rg, n_reg, atom) : atom;
@@ -341,7 +343,7 @@ __global__ void __launch_bounds__(kApplyThreads) eig_apply_kernel(
     const int2 *__restrict__ sweep, int64_t scap, const int *__restrict__ nsweep,
     int *__restrict__ nu_eff_out, double *__restrict__ eps_out, double *__restrict__ w_out,
     double *__restrict__ t_out, double *__restrict__ P_out, const int64_t *__restrict__ p_off,
-    int *__restrict__ eig_status)
+    int *__restrict__ eig_status, double *__restrict__ proj_out)
 {
     const int sc = blockIdx.x;
     const int c = cofs + sc;
@@ -356,7 +358,7 @@ __global__ void __launch_bounds__(kApplyThreads) eig_apply_kernel(
     const int64_t j = bcols[c];
     const int64_t J = j >> 2;
     const int npat = 4 * (int)(rp[J + 1] - rp[J]);
-    const int nr = npat + 2;
+    const int nr = npat + 2 + (proj_out ? 1 : 0);
     const double *RQc = RQ + (int64_t)sc * nr_max * nu;
     for (int idx = tid; idx < nr * n; idx += T) {
         const int r = idx / n, i = idx - (idx / n) * n;
@@ -406,6 +408,7 @@ __global__ void __launch_bounds__(kApplyThreads) eig_apply_kernel(
         eps_out[g * nu + a] = ea;
         t_out[g * nu + a] = ta;
         w_out[g * nu + a] = wa;
+        if (proj_out) proj_out[g * nu + a] = a < n ? R[(npat + 2) * ldr + perm[a]] : 0.0;
     }
     double *P = P_out + p_off[g];
     for (int idx = tid; idx < npat * nu; idx += T) {
@@ -428,7 +431,8 @@ cudaError_t tridiag_dispatch(const DeviceMatrix &A, const KrylovBatch &b, const 
     if (e != cudaSuccess) return e;
     eig_tridiag_kernel<VT><<<nb2, kTriThreads, smem, s>>>(
         b.Hsub, b.nu_eff, b.scale, (const VT *)b.K, b.shape.m_pad, b.tinv, b.nb, nu, b.cols, A.rp, A.ci,
-        rm ? rm->reg : nullptr, rm ? rm->n_reg : 0, cofs, es.D, es.E, es.RQ, es.nr_max, es.Ag, b.Lsub);
+        rm ? rm->reg : nullptr, rm ? rm->n_reg : 0, cofs, es.D, es.E, es.RQ, es.nr_max, es.Ag, b.Lsub,
+        es.proj);
     return cudaGetLastError();
 }
 
@@ -452,6 +456,7 @@ size_t eig_smem_bytes(int nu, int nr_max, bool a_global)
 cudaError_t launch_eig(const DeviceMatrix &A, const KrylovBatch &b, const ColumnState &st,
                        int64_t col0, const RegionMaps *rm, const EigScratch &es, cudaStream_t s)
 {
+    if ((es.proj == nullptr) != (es.proj_out == nullptr)) return cudaErrorInvalidValue;
     const int nu = b.nu, ldr = nu | 1;
     const size_t qsmem = (size_t)2 * nu * 32 * sizeof(double);
     const size_t asmem = (size_t)es.nr_max * ldr * sizeof(double) + (size_t)nu * (sizeof(double) + sizeof(int));
@@ -470,7 +475,7 @@ cudaError_t launch_eig(const DeviceMatrix &A, const KrylovBatch &b, const Column
         eig_apply_kernel<<<nb2, kApplyThreads, asmem, s>>>(
             b.nu_eff, b.status, cofs, nu, b.cols, A.sdiag, A.rp, col0, es.D, es.RQ, es.nr_max,
             es.rot, es.rcap, es.sweep, es.scap, es.nsweep, st.nu_eff, st.eps, st.w, st.t, st.P,
-            st.p_off, st.eig_status);
+            st.p_off, st.eig_status, es.proj ? es.proj_out : nullptr);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     return cudaSuccess;

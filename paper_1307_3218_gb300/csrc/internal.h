@@ -26,6 +26,7 @@ enum KernelKind {
     KK_SPMM_HS,
     KK_BISECT,
     KK_FORCE,
+    KK_EIGSTATE,
     KK_NKINDS
 };
 
@@ -212,6 +213,11 @@ struct EigScratch {
     int2 *sweep = nullptr;
     int *nsweep = nullptr;
     double *Ag = nullptr;   // chunk x nu x (nu | 1) doubles when H_sub does not fit in shared memory
+    // optional extra row of R: proj[c * nu + i] = v^T w_i (batch column c, stored
+    // vector i) for a given vector v; the eigensolve then writes v^T K v_a of
+    // every level a (ascending) to proj_out[g * nu + a] (g = solved column)
+    const double *proj = nullptr;
+    double *proj_out = nullptr;
 };
 // Dynamic shared memory of the tridiagonalisation and the largest one of the
 // eigensolve kernels, with H_sub in shared (a_global = false) or global memory.
@@ -243,6 +249,21 @@ struct BisectState {
 cudaError_t launch_bisection(const ColumnState &st, double kT, double electron_count, double *partial,
                              unsigned *ticket, double *range, double *out, BisectState *bs,
                              cudaStream_t s);
+// The k-th eigen level and vector (eigstate.cu).
+//   launch_window   colmax[c] = max_a |t_a W_a|, colarg[c] its level, argmax[0] the column
+//                   of the largest (W_a = f((eps_a - hi) / sigma) - f((eps_a - lo) / sigma))
+//   launch_project  proj[c * nu + i] = v^T w_i for the batch's stored vectors (v over M rows)
+//   launch_eigvec   out[r] (M rows, untouched outside the column's tiles) = row r of K v_a for
+//                   the level eps of batch column c (nu <= eigvec_max_nu())
+//   launch_combine  phi[cols[c]] = sum_a sign(proj[c nu + a]) t_a W_a over the solved columns
+cudaError_t launch_window(const ColumnState &st, double lo, double hi, double sigma, double *colmax, int *colarg,
+                          int64_t *argmax, cudaStream_t s);
+cudaError_t launch_project(const KrylovBatch &b, const double *v, int64_t M, double *proj, cudaStream_t s);
+int eigvec_max_nu();
+cudaError_t launch_eigvec(const KrylovBatch &b, int c, double eps, int64_t M, double *out, cudaStream_t s);
+cudaError_t launch_combine(const ColumnState &st, const double *proj, double lo, double hi, double sigma,
+                           double *phi, cudaStream_t s);
+
 // F[n_atoms][3] = 2 sum_J sum_ab (rho_bar dH - rho_bar^E dS) over the blocks
 // (K, J != K); rho, rhoE, dH, dS device arrays in the BSR layout (dH, dS
 // [3][nnzb][16]).

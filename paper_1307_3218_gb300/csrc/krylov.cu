@@ -31,7 +31,7 @@ const char *kernel_name(int kind)
 {
     static const char *names[KK_NKINDS] = {"init",   "spmm_H", "gs",      "spmm_S", "eigsub",
                                            "minmax", "count",  "density", "green", "region", "support", "spmm_HS",
-                                           "bisect_step", "force"};
+                                           "bisect_step", "force", "eigenstate"};
     return (kind >= 0 && kind < KK_NKINDS) ? names[kind] : "?";
 }
 

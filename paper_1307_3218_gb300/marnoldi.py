@@ -89,6 +89,7 @@ def load(path: str | None = None):
                                         C.POINTER(d), i32]),
         "marnoldi_count_noalloc": (i32, [P, P, P, i64, i32, d, d, P, P]),
         "marnoldi_forces": (i32, [P, P, P, P]),
+        "marnoldi_eigenstate": (i32, [P, i64, d, P, P, P]),
         "marnoldi_set_members": (i32, [P, i32, P, P]),
         "marnoldi_member_energy": (i32, [P, i32, P, P, P]),
         "marnoldi_set_autotune": (i32, [i32]),
@@ -365,6 +366,15 @@ def union_of(systems, pad_to: int = 8):
     row_ptr = np.concatenate([[0]] + rps).astype(np.int64)
     return (atom, row_ptr, np.concatenate(cis).astype(np.int32), np.concatenate(Hs), np.concatenate(Ss),
             np.concatenate(masks), np.array(offs, dtype=np.int64), np.array(boffs, dtype=np.int64))
+
+
+def marnoldi_eigenstate(ctx: Context, k: int, sigma: float) -> tuple[float, np.ndarray, tuple[float, float]]:
+    """(eps_k, phi_k over the M orbitals, (eta(k-1), eta(k))) from the last solve (see the C header)."""
+    ek = C.c_double()
+    phi = np.empty(4 * ctx.n_block_rows)
+    eb = np.empty(2)
+    _check(load().marnoldi_eigenstate(ctx.handle, int(k), float(sigma), C.byref(ek), _ptr(phi), _ptr(eb)), ctx)
+    return ek.value, phi, (float(eb[0]), float(eb[1]))
 
 
 def marnoldi_forces(ctx: Context, dH_dd, dS_dd) -> np.ndarray:
