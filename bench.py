@@ -679,6 +679,24 @@ def serving(m, t4096, requests: int, workers: int, budget: int, prec: int):
     solo = run(workers, group=1, reqs=small)
     grouped = run(workers, group=16, reqs=small)
     ncols_small = sum(c.real_columns().size for c, _ in small)
+    # uneven polymer chains: fluorene-like units (69 atoms each), lengths
+    # log-uniform in 4..59 units (the global-mode limit of 4,096 atoms), nu 30
+    # or 100, all submitted at once
+    from tbsynth import polymer_system
+    prng = np.random.default_rng(7)
+    chains = []
+    for q in range(24):
+        units = int(round(np.exp(prng.uniform(np.log(4), np.log(59)))))
+        chains.append((polymer_system(units, seed=q), 100 if prng.random() < 0.25 else 30))
+    run(workers, group=16, reqs=chains[:2])   # warm-up
+    poly = run(workers, group=16, reqs=chains)
+    ncols_poly = sum(c.real_columns().size for c, _ in chains)
+    out_poly = {"requests": len(chains), "units": [int(c.n_block_rows // 69) for c, _ in chains],
+                "atoms_total": int(sum(c.n_block_rows for c, _ in chains)), "columns": int(ncols_poly),
+                "columns_per_s": round(ncols_poly / poly["wall"], 1),
+                "p50_ms": round(float(np.percentile(poly["lat"], 50)), 2),
+                "p99_ms": round(float(np.percentile(poly["lat"], 99)), 2),
+                "groups": poly["stats"]["groups"], "largest_group": poly["stats"]["largest_group"]}
     out_small = {"requests": len(small), "atoms": 64, "nu": 30, "columns": int(ncols_small),
                  "one_by_one": {"columns_per_s": round(ncols_small / solo["wall"], 1),
                                 "p50_ms": round(float(np.percentile(solo["lat"], 50)), 2)},
@@ -688,6 +706,7 @@ def serving(m, t4096, requests: int, workers: int, budget: int, prec: int):
                              "largest_group": grouped["stats"]["largest_group"]}}
     return {
         "small_molecules": out_small,
+        "polymer_chains": out_poly,
         "trace": f"{requests} requests, atoms {list(SERVE_SIZES)} with p {list(SERVE_SIZE_P)}, "
                  f"nu 30 (nu 100 for 1/4 of those <= 1024 atoms), {'mixed' if prec else 'fp64'}, "
                  f"all real orbitals, density matrices returned to the host",

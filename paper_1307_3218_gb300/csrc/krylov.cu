@@ -250,7 +250,10 @@ __global__ void __launch_bounds__(256) spmm_hs_kernel(
     constexpr bool kF = sizeof(VT) == 4;
     constexpr int BS = kF ? 32 : 16;   // stored values per block
     const int64_t I = (int64_t)blockIdx.x * 8 + threadIdx.y;
-    if (I >= nbr) return;   // uniform over the warp
+    // rows past nbr in the last tile of 8 get their zeros stored (the
+    // workspace holds the previous batch's vectors there otherwise)
+    if (I >= ((nbr + 7) & ~(int64_t)7)) return;   // uniform over the warp
+    const bool phantom = I >= nbr;
     int cc[2];
     RowLive L[2];
     int64_t yo[2];
@@ -258,6 +261,7 @@ __global__ void __launch_bounds__(256) spmm_hs_kernel(
     for (int h = 0; h < 2; ++h) {
         cc[h] = blockIdx.y * 64 + 32 * h + threadIdx.x;
         L[h] = row_live(thop, blockIdx.x, ncols, cc[h], lim);
+        if (phantom) L[h].act = false;
         yo[h] = L[h].live ? 4 * apos(tinv, ncols, cc[h], I) : 0;
     }
     VT hi[2][4], lo[2][4], sy[2][4];
@@ -573,7 +577,10 @@ __global__ void __launch_bounds__(T, T == 256 ? 4 : T == 512 ? 2 : 1) gs_kernel(
             const double beta2 = tg[n];
             if (!(beta2 > 0.0) || beta2 <= tau2 * (beta2 + cn2[c])) {
                 stop = 1;
-                status[c] = (beta2 >= 0.0) ? 1 : 2;   // 2: negative or NaN S-norm
+                // a square norm below zero by no more than the threshold times the
+                // projected part is rounding at breakdown (FP32 vectors near linear
+                // dependence); further below, or NaN, it is not a norm (2)
+                status[c] = (beta2 >= -sqrt(tau2) * cn2[c]) ? 1 : 2;
                 nu_eff[c] = n;
             } else {
                 sn = 1.0 / sqrt(beta2);

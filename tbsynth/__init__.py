@@ -14,11 +14,12 @@ carbon atom, neighbour blocks from atom pairs inside a cutoff.
 """
 
 from .structures import Structure, diamond, amorphous_carbon, spatial_sort
+from .polymer import polyfluorene
 from .tbmodel import (TBSystem, amorphous_system, build_tb, build_tb_derivatives, carbon_params,
-                      config_c1, config_c2, tiny_hydrocarbon, tiny_system)
+                      config_c1, config_c2, polymer_system, tiny_hydrocarbon, tiny_system)
 
 __all__ = [
     "Structure", "diamond", "amorphous_carbon", "spatial_sort",
     "TBSystem", "build_tb", "build_tb_derivatives", "carbon_params", "config_c1", "config_c2", "tiny_system",
-    "amorphous_system", "tiny_hydrocarbon",
+    "amorphous_system", "tiny_hydrocarbon", "polyfluorene", "polymer_system",
 ]

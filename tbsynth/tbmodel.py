@@ -319,6 +319,14 @@ def tiny_system(n_atoms: int, seed: int = 0, radius: float | None = None,
     return t
 
 
+def polymer_system(n_units: int, seed: int = 0, **kw) -> TBSystem:
+    """A fluorene-like chain of n_units units (69 atoms each; see tbsynth.polymer)."""
+    from .polymer import polyfluorene
+    t = build_tb(polyfluorene(n_units, seed=seed, **kw))
+    t.meta.update(name=f"polyfluorene-{n_units}", seed=seed)
+    return t
+
+
 def tiny_hydrocarbon(n_atoms: int, n_hydrogen: int, seed: int = 0, box: float = 12.0) -> TBSystem:
     """A small cluster in which n_hydrogen of the atoms are hydrogen (one s
     orbital padded to a 4x4 block with three masked dummy orbitals)."""

@@ -133,6 +133,26 @@ def test_batching_and_determinism(m, c1):
     assert a["E"] == b["E"] == c["E"]
 
 
+@pytest.mark.parametrize("prec,region", [(0, 0), (1, 0), (0, 100), (1, 100)])
+def test_batches_with_a_partial_last_tile(m, prec, region):
+    # 300 atoms and 100-atom regions: the last tile of 8 atoms is partly empty,
+    # and later batches reuse the workspace of earlier ones
+    t = amorphous_system(300, seed=5)
+    assert t.n_block_rows % 8 and (region == 0 or region % 8)
+    runs = []
+    for batch in (0, 37):
+        ctx = m.setup_system(t, prec)
+        if batch:
+            m.marnoldi_set_batch(ctx, batch)
+        m.marnoldi_solve(ctx, None, 30, region, t.n_electrons, KT)
+        rho, rhoE = m.marnoldi_density(ctx)
+        runs.append((m.marnoldi_energy(ctx), rho, rhoE))
+        m.marnoldi_destroy(ctx)
+    assert runs[0][0] == runs[1][0]
+    np.testing.assert_array_equal(runs[0][1], runs[1][1])
+    np.testing.assert_array_equal(runs[0][2], runs[1][2])
+
+
 def test_green_function(m, c1):
     g = gpu_solve(m, c1, 30)
     ref = oracle.columns(c1, c1.real_columns(), 30)
