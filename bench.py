@@ -41,10 +41,10 @@ L2_FLUSH_BYTES = 256 << 20
 FP64_PEAK_NOTE = "152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz (nominal 1.25 TFLOP/s FP64)"
 # (dram__bytes_read + dram__bytes_write) / algorithmic bytes of one captured
 # Gram-Schmidt launch (ncu --set full, mixed precision, 608 columns, step n = 20):
-# (1.789804e9 + 0.033579e9) / (1.929072e9 read + 0.039846e9 written over the
+# (1.788508e9 + 0.033725e9) / (1.929072e9 read + 0.039846e9 written over the
 # supports); below 1 because the subtraction re-reads the last blocks from L2.
 # Must be re-measured (or removed) whenever the kernel changes.
-GS_DRAM_PER_ALGORITHMIC = {"mixed": 0.9261}
+GS_DRAM_PER_ALGORITHMIC = {"mixed": 0.9255}
 
 
 def parse():
@@ -63,6 +63,8 @@ def parse():
     p.add_argument("--no-extra", action="store_true",
                    help="skip the nu=100 and regional side measurements")
     p.add_argument("--no-serving", action="store_true", help="skip the request-server measurement")
+    p.add_argument("--large", type=int, default=0,
+                   help="atoms of the paper-scale regional run (e.g. 1048576); 0 = skip")
     p.add_argument("--order-n", default="",
                    help="comma-separated atom counts for the order-N study (regional mode), e.g. "
                         "4096,16384,65536,262144; empty = skip")
@@ -520,6 +522,9 @@ def main():
                 checks[label] = gpu_outputs(m, rx["ctx"], cl, nu_x, pr)
             m.marnoldi_destroy(rx["ctx"])
 
+    if args.large and world == 1:
+        line["large"] = large_structure(m, args.large, 256, 65536)
+
     if args.order_n and world == 1:
         sizes = [int(x) for x in args.order_n.split(",")]
         line["order_n"] = order_n(m, t, sizes, 256, prec)
@@ -599,6 +604,55 @@ def order_n(m, t4096, sizes, n_reg: int, prec: int, nu: int = 30):
     out["setup"] = (f"amorphous carbon, seed 0, {n_reg}-atom regions, nu={nu}, "
                     f"{'mixed' if prec else 'fp64'} for the times; errors in FP64 against global mode "
                     f"at the same nu on {t4096.n_block_rows} atoms")
+    return out
+
+
+def large_structure(m, n_atoms: int, n_reg: int, batch: int):
+    """The paper-scale configuration on one GPU: amorphous carbon of n_atoms
+    atoms (1,048,576 by default) in regional mode (n_reg-atom regions).  Times
+    (a) the whole structure at nu = 30 in mixed precision (every real orbital,
+    mu by bisection, density on the device) and (b) one batch of `batch`
+    columns (the first ones) at nu = 100 in mixed precision and in FP64 (mu
+    fixed at the nu = 30 solve's level, so that only the batch is timed)."""
+    import torch
+    from tbsynth import amorphous_system
+    t0 = time.perf_counter()
+    t = amorphous_system(n_atoms, seed=0)
+    gen_s = time.perf_counter() - t0
+    out = {"atoms": n_atoms, "M": t.M, "nnzb": t.nnzb, "region_atoms": n_reg,
+           "generation_s": round(gen_s, 1)}
+    for prec in (1, 0):
+        t0 = time.perf_counter()
+        ctx = m.setup_system(t, prec)
+        torch.cuda.synchronize()
+        out[f"setup_s_{'mixed' if prec else 'fp64'}"] = round(time.perf_counter() - t0, 1)
+        if prec == 1:
+            rho = torch.empty(t.nnzb * 16, dtype=torch.float64, device="cuda")
+            rhoE = torch.empty_like(rho)
+            t0 = time.perf_counter()
+            m.marnoldi_solve(ctx, None, 30, n_reg, float(t.n_electrons), KT)
+            m.marnoldi_density_device(ctx, rho, rhoE)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            E, mu, N = m.marnoldi_energy(ctx)
+            out["nu30_all_columns"] = {"columns": int(t.M), "seconds": round(dt, 2),
+                                       "columns_per_s": round(t.M / dt, 1),
+                                       "E_band_per_atom_eV": E / n_atoms, "mu_eV": mu}
+            mu30 = mu
+            del rho, rhoE
+        cols = np.arange(batch, dtype=np.int64)
+        m.marnoldi_solve(ctx, cols[:256], 100, n_reg, 0.0, KT, mu_fixed=mu30)   # warm-up
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        m.marnoldi_solve(ctx, cols, 100, n_reg, 0.0, KT, mu_fixed=mu30)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        out[f"nu100_batch_{'mixed' if prec else 'fp64'}"] = {"columns": batch, "seconds": round(dt, 2),
+                                                              "columns_per_s": round(batch / dt, 1)}
+        m.marnoldi_destroy(ctx)
+        torch.cuda.empty_cache()
+    out["note"] = ("regional mode (the order-N form); the nu = 100 lines time one batch of the first "
+                   f"{batch} columns at the nu = 30 Fermi level")
     return out
 
 

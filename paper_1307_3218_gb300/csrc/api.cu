@@ -1262,6 +1262,9 @@ int marnoldi_solve(marnoldi_ctx *c, const int64_t *columns, int64_t ncols, int n
         int r;
         if ((r = launch(c, KK_SUPPORT, [&] { return launch_support(c->A, rmp, k, c->stream); })))
             return r;
+        const int rows = regional ? region_atoms : (int)c->nbr;
+        if ((rows & 7) && (r = launch(c, KK_INIT, [&] { return launch_zero_partial_tile(k, rows, c->stream); })))
+            return r;
         if ((r = launch(c, KK_INIT, [&] {
                  return regional ? launch_init_regional(c->A, c->rm, k, c->stream) : launch_init(c->A, k, c->stream);
              })))

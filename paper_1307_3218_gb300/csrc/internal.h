@@ -178,6 +178,10 @@ __device__ __forceinline__ int find_sorted(const int *__restrict__ R, int n, int
 
 cudaError_t launch_init(const DeviceMatrix &A, const KrylovBatch &b, cudaStream_t s);
 // Fills thop / tinv / tcnt of the batch (rm = null in global mode).
+// Zeros at the positions of the rows past `rows` (atoms, or region atoms) in
+// their last tile of 8, in U, Ulo and the S w slots of every batch column; a
+// no-op when rows is a multiple of 8.
+cudaError_t launch_zero_partial_tile(const KrylovBatch &b, int rows, cudaStream_t s);
 cudaError_t launch_support(const DeviceMatrix &A, const RegionMaps *rm, const KrylovBatch &b,
                            cudaStream_t s);
 // U (and Ulo) = H X and, when SY is not null, SY = S X for the batch (X and

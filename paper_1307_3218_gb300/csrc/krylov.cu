@@ -250,10 +250,7 @@ __global__ void __launch_bounds__(256) spmm_hs_kernel(
     constexpr bool kF = sizeof(VT) == 4;
     constexpr int BS = kF ? 32 : 16;   // stored values per block
     const int64_t I = (int64_t)blockIdx.x * 8 + threadIdx.y;
-    // rows past nbr in the last tile of 8 get their zeros stored (the
-    // workspace holds the previous batch's vectors there otherwise)
-    if (I >= ((nbr + 7) & ~(int64_t)7)) return;   // uniform over the warp
-    const bool phantom = I >= nbr;
+    if (I >= nbr) return;   // uniform over the warp
     int cc[2];
     RowLive L[2];
     int64_t yo[2];
@@ -261,7 +258,6 @@ __global__ void __launch_bounds__(256) spmm_hs_kernel(
     for (int h = 0; h < 2; ++h) {
         cc[h] = blockIdx.y * 64 + 32 * h + threadIdx.x;
         L[h] = row_live(thop, blockIdx.x, ncols, cc[h], lim);
-        if (phantom) L[h].act = false;
         yo[h] = L[h].live ? 4 * apos(tinv, ncols, cc[h], I) : 0;
     }
     VT hi[2][4], lo[2][4], sy[2][4];

@@ -241,12 +241,10 @@ __global__ void __launch_bounds__(256) spmm_regional_kernel(
 {
     const int p = blockIdx.x * 32 + threadIdx.x;
     const int c = blockIdx.y * 8 + threadIdx.y;
-    // rows past n_reg in its last tile of 8 are stored too (as zeros): the
-    // workspace holds the previous batch's vectors there otherwise
-    if (p >= ((n_reg + 7) & ~7) || c >= ncols) return;
+    if (p >= n_reg || c >= ncols) return;
     const VT *x = X + (int64_t)c * ldx;
     const int64_t base = (int64_t)c * maxrow * n_reg;
-    const bool act = p < n_reg && (int)thop[(int64_t)(p >> 3) * ncols + c] <= lim;
+    const bool act = (int)thop[(int64_t)(p >> 3) * ncols + c] <= lim;
     const int cnt = act ? lcnt[(int64_t)c * n_reg + p] : 0;
     VT acc[4] = {VT(0), VT(0), VT(0), VT(0)}, acl[4] = {VT(0), VT(0), VT(0), VT(0)};
     for (int s = 0; s < cnt; ++s) {

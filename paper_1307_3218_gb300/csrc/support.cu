@@ -95,7 +95,45 @@ __global__ void __launch_bounds__(256) support_kernel(
     }
 }
 
+// Rows past the last atom (or region atom) in its tile of 8 belong to no
+// atom: the products never write them, so a later batch would read the
+// previous batch's values there.  One CTA per batch column stores zeros at
+// their positions in U (and its lo word) and in every S w slot (slot 0 is
+// cleared by the initialisation, the K slots by every Gram-Schmidt writeout).
+template <typename VT>
+__global__ void zero_partial_tile_kernel(int rows, int nb, int nu, int64_t m_pad, const uint16_t *__restrict__ tinv,
+                                         VT *__restrict__ SK, VT *__restrict__ U, VT *__restrict__ Ulo)
+{
+    const int c = blockIdx.x;
+    const int r0 = rows, r1 = (rows + 7) & ~7;
+    const int64_t base = 32 * (int64_t)tinv[(int64_t)(r0 >> 3) * nb + c];   // the tile's first entry
+    if (base >= m_pad) return;   // a tile of another structure of a union: no position here
+    const int nent = 4 * (r1 - r0);
+    const int64_t e0 = base + 4 * (int64_t)(r0 & 7);
+    for (int idx = threadIdx.x; idx < (nu + 1) * nent; idx += blockDim.x) {
+        const int slot = idx / nent, e = idx - slot * nent;
+        if (slot < nu) {
+            if (slot > 0) SK[((int64_t)c * nu + slot) * m_pad + e0 + e] = VT(0);
+        } else {
+            U[(int64_t)c * m_pad + e0 + e] = VT(0);
+            if (Ulo) Ulo[(int64_t)c * m_pad + e0 + e] = VT(0);
+        }
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_zero_partial_tile(const KrylovBatch &b, int rows, cudaStream_t s)
+{
+    if ((rows & 7) == 0 || b.nb < 1) return cudaSuccess;
+    if (b.prec == 0)
+        zero_partial_tile_kernel<double><<<b.nb, 128, 0, s>>>(rows, b.nb, b.nu, b.shape.m_pad, b.tinv, (double *)b.SK,
+                                                              (double *)b.U, nullptr);
+    else
+        zero_partial_tile_kernel<float><<<b.nb, 128, 0, s>>>(rows, b.nb, b.nu, b.shape.m_pad, b.tinv, (float *)b.SK,
+                                                             (float *)b.U, (float *)b.Ulo);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_support(const DeviceMatrix &A, const RegionMaps *rm, const KrylovBatch &b,
                            cudaStream_t s)
