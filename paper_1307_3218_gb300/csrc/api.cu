@@ -1273,15 +1273,10 @@ int marnoldi_solve(marnoldi_ctx *c, const int64_t *columns, int64_t ncols, int n
             const char *Kn = (const char *)k.K + (size_t)n * mp * vs;
             char *SKn = n > 0 ? (char *)k.SK + (size_t)n * mp * vs : nullptr;
             if (regional) {
-                if ((r = launch(c, KK_SPMM_H, [&] {
-                         return launch_spmm_regional(c->A, c->rm, 0, k, Kn, (int64_t)nu * mp, k.U, mp, n + 1,
-                                                     c->stream);
+                if ((r = launch(c, KK_SPMM_HS, [&] {
+                         return launch_spmm_regional_hs(c->A, c->rm, k, Kn, (int64_t)nu * mp, SKn,
+                                                        (int64_t)nu * mp, n + 1, c->stream);
                      })))
-                    return r;
-                if (SKn && (r = launch(c, KK_SPMM_S, [&] {
-                               return launch_spmm_regional(c->A, c->rm, 1, k, Kn, (int64_t)nu * mp, SKn,
-                                                           (int64_t)nu * mp, n + 1, c->stream);
-                           })))
                     return r;
             } else if ((r = launch(c, KK_SPMM_HS, [&] {
                             return launch_spmm_hs(c->A, k, Kn, (int64_t)nu * mp, SKn, (int64_t)nu * mp, n + 1,

@@ -161,9 +161,11 @@ cudaError_t launch_local_bsr(const DeviceMatrix &A, const RegionMaps &rm, const 
                              cudaStream_t s);
 cudaError_t launch_init_regional(const DeviceMatrix &A, const RegionMaps &rm, const KrylovBatch &b,
                                  cudaStream_t s);
-cudaError_t launch_spmm_regional(const DeviceMatrix &A, const RegionMaps &rm, int which,
-                                 const KrylovBatch &b, const void *X, int64_t ldx, void *Y,
-                                 int64_t ldy, int lim, cudaStream_t s);
+// H x (to b.U, b.Ulo) and, when SY is given, S x (to SY) in one pass over the
+// local block lists, with the sums of the separate products.
+cudaError_t launch_spmm_regional_hs(const DeviceMatrix &A, const RegionMaps &rm, const KrylovBatch &b,
+                                    const void *X, int64_t ldx, void *SY, int64_t ldsy, int lim,
+                                    cudaStream_t s);
 
 // Position of atom a in the ascending list R[0..n), or -1.
 __device__ __forceinline__ int find_sorted(const int *__restrict__ R, int n, int a)

@@ -17,9 +17,9 @@
 //                      local column lci and global block index lgk, stored
 //                      slot-major ([c][slot][p]) so that lanes over p coalesce
 //   init_regional:     k_1 = e_{jl} / sqrt(S_jj), S k_1 from row j's local blocks
-//   spmm_regional:     y = A_local x for every column, x and y of length
-//                      m_pad >= 4 n_reg, matrix values gathered from the
-//                      global BSR through lgk
+//   spmm_regional_hs:  H_local x and S_local x for every column in one pass,
+//                      x and y of length m_pad >= 4 n_reg, matrix values
+//                      gathered from the global BSR through lgk
 #include "internal.h"
 
 #include <cfloat>
@@ -225,20 +225,25 @@ __device__ __forceinline__ void df_add(float &hi, float &lo, float h2, float l2)
     lo = __fadd_rn(lo, __fadd_rn(l2, err));
 }
 
-// y = A_local x.  Lanes run over local block rows of one column, so the
-// local-structure reads coalesce and the x gathers stay inside the column's
-// short local vector.  MODE 0: FP64.  MODE 1: FP32 with hi values (S).
-// MODE 2: FP32, exact products and two-sums over hi + lo, output as a
-// (hi, lo) pair (H; the subspace matrix entries use it).  Rows whose support
-// tile lies more than `lim` hops from the column's atom are exact zeros and
-// are written without being computed.
-template <typename VT, int MODE>
-__global__ void __launch_bounds__(256) spmm_regional_kernel(
+// y = H_local x and, with kS, S_local x in one pass (both feed the same
+// Gram-Schmidt step and share the local block list, so the x gathers and the
+// index reads serve both).  Lanes run over local block rows of one column, so
+// the local-structure reads coalesce and the x gathers stay inside the
+// column's short local vector.  FP32: H by exact products and two-sums over
+// its hi + lo values, output as a (hi, lo) pair (the subspace matrix entries
+// use it), S by FMAs over its hi values; FP64: FMAs.  Rows whose support tile
+// lies more than `lim` hops from the column's atom are exact zeros and are
+// written without being computed.
+template <typename VT, bool kS>
+__global__ void __launch_bounds__(256) spmm_regional_hs_kernel(
     int n_reg, int maxrow, const int *__restrict__ lcnt, const int *__restrict__ lci,
-    const int *__restrict__ lgk, const VT *__restrict__ vals, const VT *__restrict__ X,
-    int64_t ldx, VT *__restrict__ Y, VT *__restrict__ Ylo, int64_t ldy, int ncols,
-    const uint8_t *__restrict__ thop, const uint16_t *__restrict__ tinv, int lim)
+    const int *__restrict__ lgk, const VT *__restrict__ Hv, const VT *__restrict__ Sv,
+    const VT *__restrict__ X, int64_t ldx, VT *__restrict__ U, VT *__restrict__ Ulo, int64_t ldu,
+    VT *__restrict__ SY, int64_t ldsy, int ncols, const uint8_t *__restrict__ thop,
+    const uint16_t *__restrict__ tinv, int lim)
 {
+    constexpr bool kF = sizeof(VT) == 4;
+    constexpr int stride = kF ? 32 : 16;
     const int p = blockIdx.x * 32 + threadIdx.x;
     const int c = blockIdx.y * 8 + threadIdx.y;
     if (p >= n_reg || c >= ncols) return;
@@ -247,6 +252,7 @@ __global__ void __launch_bounds__(256) spmm_regional_kernel(
     const bool act = (int)thop[(int64_t)(p >> 3) * ncols + c] <= lim;
     const int cnt = act ? lcnt[(int64_t)c * n_reg + p] : 0;
     VT acc[4] = {VT(0), VT(0), VT(0), VT(0)}, acl[4] = {VT(0), VT(0), VT(0), VT(0)};
+    VT sacc[4] = {VT(0), VT(0), VT(0), VT(0)};
     for (int s = 0; s < cnt; ++s) {
         const int q = lci[base + (int64_t)s * n_reg + p];
         const int64_t k = lgk[base + (int64_t)s * n_reg + p];
@@ -254,27 +260,28 @@ __global__ void __launch_bounds__(256) spmm_regional_kernel(
         const VT *xq = x + 32 * (int64_t)tinv[(int64_t)(q >> 3) * ncols + c] + 4 * (q & 7);
 #pragma unroll
         for (int e = 0; e < 4; ++e) xv[e] = xq[e];
-        constexpr int stride = MODE == 0 ? 16 : 32;
-        const VT *B = vals + stride * k;
+        const VT *Hb = Hv + stride * k;
+        const VT *Sb = Sv + stride * k;
 #pragma unroll
         for (int a = 0; a < 4; ++a) {
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
-                if constexpr (MODE == 2) {
-                    const float h = B[4 * a + e], l = B[16 + 4 * a + e];
+                if constexpr (kF) {
+                    const float h = Hb[4 * a + e], l = Hb[16 + 4 * a + e];
                     const float pr = __fmul_rn(h, xv[e]);
                     const float er = __fmaf_rn(h, xv[e], -pr);
                     df_add(acc[a], acl[a], pr, __fmaf_rn(l, xv[e], er));
                 } else {
-                    acc[a] = fma(B[4 * a + e], xv[e], acc[a]);
+                    acc[a] = fma(Hb[4 * a + e], xv[e], acc[a]);
                 }
+                if constexpr (kS) sacc[a] = fma(Sb[4 * a + e], xv[e], sacc[a]);
             }
         }
     }
     const int64_t yp = 32 * (int64_t)tinv[(int64_t)(p >> 3) * ncols + c] + 4 * (p & 7);
-    VT *y = Y + (int64_t)c * ldy + yp;
-    if constexpr (MODE == 2) {
-        VT *yl = Ylo + (int64_t)c * ldy + yp;
+    VT *y = U + (int64_t)c * ldu + yp;
+    if constexpr (kF) {
+        VT *yl = Ulo + (int64_t)c * ldu + yp;
 #pragma unroll
         for (int a = 0; a < 4; ++a) {
             const float h = __fadd_rn(acc[a], acl[a]);
@@ -285,9 +292,44 @@ __global__ void __launch_bounds__(256) spmm_regional_kernel(
 #pragma unroll
         for (int a = 0; a < 4; ++a) y[a] = acc[a];
     }
+    if constexpr (kS) {
+        VT *sy = SY + (int64_t)c * ldsy + yp;
+#pragma unroll
+        for (int a = 0; a < 4; ++a) sy[a] = sacc[a];
+    }
 }
 
 }  // namespace
+
+cudaError_t launch_spmm_regional_hs(const DeviceMatrix &A, const RegionMaps &rm, const KrylovBatch &b,
+                                    const void *X, int64_t ldx, void *SY, int64_t ldsy, int lim,
+                                    cudaStream_t s)
+{
+    if (!b.thop || !b.tinv || b.ntile * 8 < rm.n_reg) return cudaErrorInvalidValue;
+    const dim3 block(32, 8);
+    const dim3 grid((unsigned)((rm.n_reg + 31) / 32), (unsigned)((b.nb + 7) / 8));
+    const int64_t ldu = b.shape.m_pad;
+    if (b.prec == 0) {
+        if (SY)
+            spmm_regional_hs_kernel<double, true><<<grid, block, 0, s>>>(
+                rm.n_reg, rm.maxrow, rm.lcnt, rm.lci, rm.lgk, A.Hd, A.Sd, (const double *)X, ldx, (double *)b.U,
+                nullptr, ldu, (double *)SY, ldsy, b.nb, b.thop, b.tinv, lim);
+        else
+            spmm_regional_hs_kernel<double, false><<<grid, block, 0, s>>>(
+                rm.n_reg, rm.maxrow, rm.lcnt, rm.lci, rm.lgk, A.Hd, A.Sd, (const double *)X, ldx, (double *)b.U,
+                nullptr, ldu, nullptr, 0, b.nb, b.thop, b.tinv, lim);
+    } else {
+        if (SY)
+            spmm_regional_hs_kernel<float, true><<<grid, block, 0, s>>>(
+                rm.n_reg, rm.maxrow, rm.lcnt, rm.lci, rm.lgk, A.Hf, A.Sf, (const float *)X, ldx, (float *)b.U,
+                (float *)b.Ulo, ldu, (float *)SY, ldsy, b.nb, b.thop, b.tinv, lim);
+        else
+            spmm_regional_hs_kernel<float, false><<<grid, block, 0, s>>>(
+                rm.n_reg, rm.maxrow, rm.lcnt, rm.lci, rm.lgk, A.Hf, A.Sf, (const float *)X, ldx, (float *)b.U,
+                (float *)b.Ulo, ldu, nullptr, 0, b.nb, b.thop, b.tinv, lim);
+    }
+    return cudaGetLastError();
+}
 
 cudaError_t launch_region(const RegionMaps &rm, const KrylovBatch &b, double rs, int cap,
                           cudaStream_t s)
@@ -330,26 +372,5 @@ cudaError_t launch_init_regional(const DeviceMatrix &A, const RegionMaps &rm, co
     return cudaGetLastError();
 }
 
-cudaError_t launch_spmm_regional(const DeviceMatrix &A, const RegionMaps &rm, int which,
-                                 const KrylovBatch &b, const void *X, int64_t ldx, void *Y,
-                                 int64_t ldy, int lim, cudaStream_t s)
-{
-    if (!b.thop || !b.tinv || b.ntile * 8 < rm.n_reg) return cudaErrorInvalidValue;
-    const dim3 block(32, 8);
-    const dim3 grid((unsigned)((rm.n_reg + 31) / 32), (unsigned)((b.nb + 7) / 8));
-    if (b.prec == 0)
-        spmm_regional_kernel<double, 0><<<grid, block, 0, s>>>(
-            rm.n_reg, rm.maxrow, rm.lcnt, rm.lci, rm.lgk, which ? A.Sd : A.Hd, (const double *)X,
-            ldx, (double *)Y, nullptr, ldy, b.nb, b.thop, b.tinv, lim);
-    else if (which == 0)
-        spmm_regional_kernel<float, 2><<<grid, block, 0, s>>>(
-            rm.n_reg, rm.maxrow, rm.lcnt, rm.lci, rm.lgk, A.Hf, (const float *)X, ldx, (float *)Y,
-            (float *)b.Ulo, ldy, b.nb, b.thop, b.tinv, lim);
-    else
-        spmm_regional_kernel<float, 1><<<grid, block, 0, s>>>(
-            rm.n_reg, rm.maxrow, rm.lcnt, rm.lci, rm.lgk, A.Sf, (const float *)X, ldx, (float *)Y,
-            nullptr, ldy, b.nb, b.thop, b.tinv, lim);
-    return cudaGetLastError();
-}
 
 }  // namespace marnoldi
