@@ -236,6 +236,27 @@ def spmm_algorithmic(nu: int, m: int, nnzb: int, nbr: int, vbytes: int, ncols: i
     return apps * 2 * m * vbytes * ncols, apps * 2.0 * 16 * nnzb * ncols
 
 
+FP32_INST_PEAK = 152 * 128 * 2.07e9   # FP32 instructions/s: 152 SMs x 128 lanes x 2.07 GHz (nominal)
+
+
+def spmm_instructions_support(t, tcnt, nu: int, prec: int):
+    """FP32 (mixed) or FP64 arithmetic instructions of the fused H and S products
+    over the rows within the output support, summed over the columns and steps.
+
+    Step n computes the rows of tiles within n + 1 hops (8 rows per tile, the
+    structure's mean blocks per row); per block and column: 16 products of H,
+    each an exact product, a fused lo product and a two-sum (11 FP32
+    instructions; FP64: 1 FMA), plus 16 FMAs of S from step 1 on.
+    """
+    rows = 8.0 * np.asarray(tcnt).sum(axis=0)            # rows within L hops, summed over columns
+    bpr = t.nnzb / t.n_block_rows
+    h_inst = 11.0 if prec == 1 else 1.0
+    total = 0.0
+    for n in range(nu):
+        total += rows[n + 1] * bpr * 16.0 * (h_inst + (1.0 if n > 0 else 0.0))
+    return total
+
+
 # ------------------------------------------------------------------------ GPU arm
 
 def time_gpu(m, t, cols, args, prec, steps, warmup, dev, measure_clocks=False):
@@ -448,6 +469,17 @@ def main():
                 "peak_source": peak_src, "launches": nlaunch, "avg_launch_ms": round(dom_ms / nlaunch, 4),
                 "algorithmic_per_step": {"bytes": by, "flops": fl}}
 
+    spmm_roof = None
+    if tcnt is not None and stats.get("spmm_HS", (0, 0.0))[1] > 0:
+        inst = spmm_instructions_support(t, tcnt, args.nu, prec) * steps
+        ach_i = inst / (stats["spmm_HS"][1] / 1e3)
+        pk = FP32_INST_PEAK if prec == 1 else FP32_INST_PEAK / 64.0
+        spmm_roof = {"kernel": "spmm_HS", "bound": "alu", "achieved": round(ach_i / 1e12, 3), "peak": round(pk / 1e12, 3),
+                     "unit": "T FP32 inst/s" if prec == 1 else "T FP64 inst/s", "frac": round(ach_i / pk, 4),
+                     "peak_source": "nominal: 152 SMs x 128 FP32 lanes x 2.07 GHz (FP64: 1/64)",
+                     "note": "H products error-free in FP32 (11 instructions each) over L2-resident "
+                             "panels: bound by FP32 issue, not by HBM"}
+
     line = {
         "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(step_s * 1e3, 3),
@@ -460,6 +492,7 @@ def main():
                    "l2": f"flushed between timed steps ({L2_FLUSH_BYTES >> 20} MB write)",
                    "parallelism": f"{world} independent replica(s)" if world > 1 else "1 GPU"},
         "roofline": roof,
+        "spmm_roofline": spmm_roof,
         "gpu_launches": int(launches),
         "kernel_ms_per_step": {k: round(v[1] / steps, 3) for k, v in stats.items() if v[0]},
         "clocks": res["clocks"],
