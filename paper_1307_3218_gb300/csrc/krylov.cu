@@ -402,20 +402,31 @@ __device__ __forceinline__ void for_live(int nv, F &&f)
     }
 }
 
-// Sum of N <= 16 per-thread accumulators over the CTA in a fixed order.  In
-// each warp a reduce-scatter butterfly over NP = 2^ceil(log2 N) slots leaves
-// slot q on lanes q (32 / NP) .. (q + 1) (32 / NP) - 1 (each lane sends half of
-// its slots per round, so N values cost about as many shuffles as two); then
-// warp w sums values w, w + NW, ... over the warps and its lane 0 runs
+// Barrier of a group of the CTA's threads: 0 = the whole CTA, else the named
+// barrier `bar` over `nthreads` threads (whole warps).
+__device__ __forceinline__ void group_sync(int bar, int nthreads)
+{
+    if (bar == 0) __syncthreads();
+    else asm volatile("bar.sync %0, %1;" ::"r"(bar), "r"(nthreads) : "memory");
+}
+
+// Sum of N <= 16 per-thread accumulators over a group of warps (the CTA, or
+// one of its halves) in a fixed order.  In each warp a reduce-scatter
+// butterfly over NP = 2^ceil(log2 N) slots leaves slot q on lanes
+// q (32 / NP) .. (q + 1) (32 / NP) - 1 (each lane sends half of its slots per
+// round, so N values cost about as many shuffles as two); then warp w of the
+// group sums values w, w + gnw, ... over its warps and its lane 0 runs
 // epi(q, total).  `buf` alternates the partial slots (part holds
-// 2 x 16 x 32 doubles) so that two barriers per reduction suffice.
+// 2 x 16 x stride doubles, stride >= gnw) so that two barriers per reduction
+// suffice; `bar` selects the group's barrier (0: the CTA's).
 template <typename VT, int N, typename Epi>
-__device__ __forceinline__ void block_sum(const DotAcc<VT> (&in)[N], double *part, int &buf, Epi epi)
+__device__ __forceinline__ void block_sum(const DotAcc<VT> (&in)[N], double *part, int &buf, Epi epi,
+                                          int gwarp, int gnw, int stride, int bar)
 {
     static_assert(N >= 1 && N <= 16, "1 <= N <= 16");
     constexpr int LOGN = N > 8 ? 4 : N > 4 ? 3 : N > 2 ? 2 : N > 1 ? 1 : 0;
     constexpr int NP = 1 << LOGN;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    const int lane = threadIdx.x & 31;
     DotAcc<VT> a[NP];
 #pragma unroll
     for (int q = 0; q < N; ++q) a[q] = in[q];
@@ -434,16 +445,16 @@ __device__ __forceinline__ void block_sum(const DotAcc<VT> (&in)[N], double *par
 #pragma unroll
     for (int o = 16 >> LOGN; o > 0; o >>= 1) a[0].merge(a[0].shfl_xor(o));
     const int qm = lane >> (5 - LOGN);
-    if ((lane & ((32 >> LOGN) - 1)) == 0 && qm < N) part[(buf * 16 + qm) * 32 + warp] = a[0].pack();
-    __syncthreads();
-    for (int q = warp; q < N; q += nw) {
+    if ((lane & ((32 >> LOGN) - 1)) == 0 && qm < N) part[(buf * 16 + qm) * stride + gwarp] = a[0].pack();
+    group_sync(bar, gnw * 32);
+    for (int q = gwarp; q < N; q += gnw) {
         DotAcc<VT> x;
-        if (lane < nw) x.unpack(part[(buf * 16 + q) * 32 + lane]);
+        if (lane < gnw) x.unpack(part[(buf * 16 + q) * stride + lane]);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) x.merge(x.shfl_xor(o));
         if (lane == 0) epi(q, x.value());
     }
-    __syncthreads();
+    group_sync(bar, gnw * 32);
     buf ^= 1;
 }
 
@@ -524,27 +535,46 @@ __global__ void __launch_bounds__(T, T == 256 ? 4 : T == 512 ? 2 : 1) gs_kernel(
         return m;
     };
 
-    // ---- coefficient sweep over the stored vectors i <= n
-    for (int i0 = 0; i0 <= n; i0 += kB) {
+    // ---- coefficient sweep over the stored vectors i <= n.  With G = 2 the
+    // CTA's halves take alternate blocks of vectors, each over all entries
+    // (thread t of a half owns positions t + v T/2), and reduce on their own
+    // barriers, so that one half's loads overlap the other's reduction.  This
+    // pays for FP64 vectors (6 % on a 16,384-entry sweep); FP32 vectors, whose
+    // error-free sums need more registers, ran slower with it (spills, or
+    // fewer loads in flight) and keep one group.
+    constexpr int G = (sizeof(VT) == 8 && T == 1024 && kWs && VPT >= 8) ? 2 : 1;
+    constexpr int TG = T / G, VG = VPT * G;
+    const int grp = tid / TG, gtid = tid - grp * TG, gwarp = gtid >> 5;
+    double *gpart = red + grp * (2 * 16 * 32 / G);
+    const VT *ug = U + (int64_t)c * MP + gtid;
+    auto glive = [&](int cnt) { return live_values<TG>(cnt, gwarp); };
+    if constexpr (G > 1) __syncthreads();   // u and w_n were stored by other threads
+    for (int i0 = grp * kB; i0 <= n; i0 += G * kB) {
         const int nbk = min(kB, n + 1 - i0);
         int nvl[kB];
-        const int nvmax = block_live(i0, nbk, nvl);
-        const VT *kb = K + base + (int64_t)i0 * MP + tid;
-        const VT *skb = SK + base + (int64_t)i0 * MP + tid;
+        int nvmax = 0;
+#pragma unroll
+        for (int l = 0; l < kB; ++l) {
+            nvl[l] = l < nbk ? glive(cnt_s[i0 + l + 1]) : 0;
+            nvmax = max(nvmax, nvl[l]);
+        }
+        const VT *kb = K + base + (int64_t)i0 * MP + gtid;
+        const VT *skb = SK + base + (int64_t)i0 * MP + gtid;
         DotAcc<VT> acc[3 * kB];   // [l] a, [kB + l] b, [2 kB + l] g
         VT hl[kB], bp[kB];
 #pragma unroll
         for (int l = 0; l < kB; ++l) hl[l] = bp[l] = VT(0);
-        for_live<VPT, Cfg::kChunkDot>(nvmax, [&](int v, bool a) {
-            const int p = tid + v * T;
+        for_live<VG, Cfg::kChunkDot>(nvmax, [&](int v, bool a) {
+            const int p = gtid + v * TG;
             VT uu;
-            if constexpr (kUs) uu = us[p]; else uu = a ? u[v * T] : VT(0);
-            const VT wn = wget(v);
+            if constexpr (kUs) uu = us[p]; else uu = a ? ug[v * TG] : VT(0);
+            VT wn;
+            if constexpr (G > 1) wn = ws[p]; else wn = wget(v);
 #pragma unroll
             for (int l = 0; l < kB; ++l) {
                 const bool al = a && v < nvl[l];
-                const VT kr = al ? kb[l * MP + v * T] : VT(0);
-                const VT sr = al ? skb[l * MP + v * T] : VT(0);
+                const VT kr = al ? kb[l * MP + v * TG] : VT(0);
+                const VT sr = al ? skb[l * MP + v * TG] : VT(0);
                 acc[l].add(kr, uu);
                 if constexpr (kLo) hl[l] = fma(kr, uls[p], hl[l]);
                 if (need_w) bp[l] = fma(sr, uu, bp[l]);
@@ -556,12 +586,13 @@ __global__ void __launch_bounds__(T, T == 256 ? 4 : T == 512 ? 2 : 1) gs_kernel(
             if constexpr (kLo) acc[l].add_lo(hl[l]);
             acc[kB + l].set(bp[l]);
         }
-        block_sum(acc, red, buf, [&](int q, double t) {
+        block_sum(acc, gpart, buf, [&](int q, double t) {
             const int l = q % kB, i = i0 + l;
             if (l >= nbk) return;
             if (q < kB) ta[i] = t; else if (q < 2 * kB) tb[i] = t; else tg[i] = t;
-        });
+        }, gwarp, TG / 32, 32 / G, G > 1 ? 1 + grp : 0);
     }
+    if constexpr (G > 1) __syncthreads();   // both halves' totals
 
     // ---- scalars, G's column, the new row of L^-1, the coefficients (FP64).
     // Lc holds L^-1 (lower triangular), so every product below is a matrix-
