@@ -199,7 +199,7 @@ int marnoldi_forces(marnoldi_ctx *ctx, const double *dH_dd, const double *dS_dd,
  * The k-th eigen level and eigenvector from the subspace levels and vectors
  * (arXiv:1307.3218, Section 2, the paragraph on the k-th eigen level, Eq. 3,
  * and the sign rule of the Appendix), after a global-mode marnoldi_solve of
- * every real orbital of one structure (no members) with nu <= 128.
+ * every real orbital of one structure (no members).
  *   n(eta) = sum_j sum_a w_a f((eps_a - eta) / sigma) (the integrated density
  *   of states, each level's step smoothed by the Fermi function of width
  *   sigma), eta(n) its inverse by bisection (eta(0) = -inf, eta(M_real) =
@@ -213,10 +213,11 @@ int marnoldi_forces(marnoldi_ctx *ctx, const double *dH_dd, const double *dS_dd,
  *   first among equals.  Columns whose largest |t_a W_a| is below 1e-12 of the
  *   reference's are left 0.  eta_bounds (may be NULL): eta(k-1), eta(k).
  * The signs come from a second pass: the reference column's subspace vector by
- * inverse iteration, then a solve of the columns in the window with the
+ * inverse iteration (its nu x nu matrix in shared memory up to nu = 128, else
+ * in a device scratch), then a solve of the columns in the window with the
  * projection of their stored vectors on it.  The context's last solve stays.
- * Errors: MARNOLDI_EINVAL (k outside [1, M_real], sigma <= 0, nu > 128, a
- * regional, partial or member solve), MARNOLDI_ESTATE (no solve).
+ * Errors: MARNOLDI_EINVAL (k outside [1, M_real], sigma <= 0, a regional,
+ * partial or member solve), MARNOLDI_ESTATE (no solve).
  */
 int marnoldi_eigenstate(marnoldi_ctx *ctx, int64_t k, double sigma, double *eps_k, double *phi,
                         double *eta_bounds);

@@ -1711,13 +1711,16 @@ int marnoldi_eigenstate(marnoldi_ctx *c, int64_t k, double sigma, double *eps_k,
         return (double *)q;
     };
     double *vref = vbuf((size_t)M * sizeof(double));
+    const size_t agb = eigvec_scratch_bytes(nu);
+    double *ag = agb ? vbuf(agb) : nullptr;
+    if (agb && !ag) return done(fail(c, MARNOLDI_ENOMEM, "eigenstate buffers"));
     double *proj = vbuf(sel.size() * (size_t)nu * sizeof(double));
     double *phid = vbuf((size_t)M * sizeof(double));
     if (!vref || !proj || !phid) return done(fail(c, MARNOLDI_ENOMEM, "eigenstate buffers"));
     e = cudaMemsetAsync(vref, 0, (size_t)M * sizeof(double), v->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(phid, 0, (size_t)M * sizeof(double), v->stream);
     if (e != cudaSuccess) return done(fail_cuda(c, e, "eigenstate buffers"));
-    if ((rc = launch(v, KK_EIGSTATE, [&] { return launch_eigvec(v->last_kb, 0, eref, M, vref, v->stream); })))
+    if ((rc = launch(v, KK_EIGSTATE, [&] { return launch_eigvec(v->last_kb, 0, eref, M, vref, ag, v->stream); })))
         return done(rc);
     v->proj_vec = vref;
     v->proj_out = proj;

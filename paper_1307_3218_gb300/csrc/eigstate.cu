@@ -143,26 +143,28 @@ __global__ void __launch_bounds__(256) project_kernel(const VT *__restrict__ K, 
     }
 }
 
-// The vector K v_a of batch column c for the level eps (n <= kMaxEigvec):
-// A = L^-1 H~ L^-T as in the eigensolve, two steps of inverse iteration on
-// A - (eps + delta) I with partial-pivoting LU, y = L^-T v, then
+// The vector K v_a of batch column c for the level eps: A = L^-1 H~ L^-T as
+// in the eigensolve, two steps of inverse iteration on A - (eps + delta) I
+// with partial-pivoting LU, y = L^-T v, then
 // out[r] = sum_i s_i y_i w_i[pos(r)] over the rows in the column's tiles.
-constexpr int kMaxEigvec = 128;
+// A sits in shared memory up to n = kSmemEigvec, else in the global scratch Ag
+// (n <= kMaxNu; one CTA, so it stays in L2).
+constexpr int kSmemEigvec = 128;
 
 template <typename VT>
 __global__ void __launch_bounds__(256) eigvec_kernel(
     int c, double eps, const double *__restrict__ Hsub, const double *__restrict__ Lsub,
     const double *__restrict__ scale, const int *__restrict__ nu_eff, const VT *__restrict__ K,
     const uint16_t *__restrict__ tinv, int nb, int ntile, int nu, int64_t m_pad, int64_t M,
-    double *__restrict__ out)
+    double *__restrict__ out, double *__restrict__ Ag)
 {
     extern __shared__ __align__(16) double es[];
     __shared__ int inv[kMaxTiles];
-    __shared__ int piv[kMaxEigvec];
-    __shared__ double x[kMaxEigvec], y[kMaxEigvec];
+    __shared__ int piv[kMaxNu];
+    __shared__ double x[kMaxNu], y[kMaxNu];
     const int n = nu_eff[c];
     const int lda = n | 1;
-    double *A = es;
+    double *A = Ag ? Ag : es;
     const int tid = threadIdx.x, T = blockDim.x;
     const double *Lc = Lsub + (int64_t)c * nu * nu;
     for (int idx = tid; idx < n * n; idx += T) {
@@ -171,7 +173,7 @@ __global__ void __launch_bounds__(256) eigvec_kernel(
     }
     __syncthreads();
     for (int i = n - 1; i >= 0; --i) {   // A <- L^-1 A, row i from rows <= i
-        double v[kMaxEigvec / 256 + 1];
+        double v[kMaxNu / 256 + 1];
         for (int q = 0; q * T + tid < n; ++q) {
             const int col = q * T + tid;
             double s = 0.0;
@@ -183,7 +185,7 @@ __global__ void __launch_bounds__(256) eigvec_kernel(
         __syncthreads();
     }
     for (int i = n - 1; i >= 0; --i) {   // A <- A L^-T, column i from columns <= i
-        double v[kMaxEigvec / 256 + 1];
+        double v[kMaxNu / 256 + 1];
         for (int q = 0; q * T + tid < n; ++q) {
             const int row = q * T + tid;
             double s = 0.0;
@@ -312,21 +314,27 @@ cudaError_t launch_project(const KrylovBatch &b, const double *v, int64_t M, dou
     return cudaGetLastError();
 }
 
-int eigvec_max_nu() { return kMaxEigvec; }
+int eigvec_max_nu() { return kMaxNu; }
 
-cudaError_t launch_eigvec(const KrylovBatch &b, int c, double eps, int64_t M, double *out, cudaStream_t s)
+size_t eigvec_scratch_bytes(int nu) { return nu > kSmemEigvec ? (size_t)nu * (nu | 1) * sizeof(double) : 0; }
+
+cudaError_t launch_eigvec(const KrylovBatch &b, int c, double eps, int64_t M, double *out, double *Ag,
+                          cudaStream_t s)
 {
-    if (b.nu > kMaxEigvec || c < 0 || c >= b.nb || b.ntile > kMaxTiles) return cudaErrorInvalidValue;
-    const size_t smem = (size_t)kMaxEigvec * (kMaxEigvec | 1) * sizeof(double);
+    if (b.nu > kMaxNu || c < 0 || c >= b.nb || b.ntile > kMaxTiles) return cudaErrorInvalidValue;
+    if (b.nu > kSmemEigvec && !Ag) return cudaErrorInvalidValue;
+    const bool in_smem = b.nu <= kSmemEigvec;
+    const size_t smem = in_smem ? (size_t)kSmemEigvec * (kSmemEigvec | 1) * sizeof(double) : 0;
+    double *ag = in_smem ? nullptr : Ag;
     cudaError_t e;
     if (b.prec == 0) {
         if ((e = allow_dynamic_smem((const void *)eigvec_kernel<double>, smem)) != cudaSuccess) return e;
         eigvec_kernel<double><<<1, 256, smem, s>>>(c, eps, b.Hsub, b.Lsub, b.scale, b.nu_eff, (const double *)b.K,
-                                                   b.tinv, b.nb, b.ntile, b.nu, b.shape.m_pad, M, out);
+                                                   b.tinv, b.nb, b.ntile, b.nu, b.shape.m_pad, M, out, ag);
     } else {
         if ((e = allow_dynamic_smem((const void *)eigvec_kernel<float>, smem)) != cudaSuccess) return e;
         eigvec_kernel<float><<<1, 256, smem, s>>>(c, eps, b.Hsub, b.Lsub, b.scale, b.nu_eff, (const float *)b.K,
-                                                  b.tinv, b.nb, b.ntile, b.nu, b.shape.m_pad, M, out);
+                                                  b.tinv, b.nb, b.ntile, b.nu, b.shape.m_pad, M, out, ag);
     }
     return cudaGetLastError();
 }

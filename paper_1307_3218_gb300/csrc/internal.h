@@ -260,13 +260,16 @@ cudaError_t launch_bisection(const ColumnState &st, double kT, double electron_c
 //                   of the largest (W_a = f((eps_a - hi) / sigma) - f((eps_a - lo) / sigma))
 //   launch_project  proj[c * nu + i] = v^T w_i for the batch's stored vectors (v over M rows)
 //   launch_eigvec   out[r] (M rows, untouched outside the column's tiles) = row r of K v_a for
-//                   the level eps of batch column c (nu <= eigvec_max_nu())
+//                   the level eps of batch column c (nu <= eigvec_max_nu(); Ag: a scratch of
+//                   eigvec_scratch_bytes(nu) bytes, needed above 128)
 //   launch_combine  phi[cols[c]] = sum_a sign(proj[c nu + a]) t_a W_a over the solved columns
 cudaError_t launch_window(const ColumnState &st, double lo, double hi, double sigma, double *colmax, int *colarg,
                           int64_t *argmax, cudaStream_t s);
 cudaError_t launch_project(const KrylovBatch &b, const double *v, int64_t M, double *proj, cudaStream_t s);
 int eigvec_max_nu();
-cudaError_t launch_eigvec(const KrylovBatch &b, int c, double eps, int64_t M, double *out, cudaStream_t s);
+size_t eigvec_scratch_bytes(int nu);
+cudaError_t launch_eigvec(const KrylovBatch &b, int c, double eps, int64_t M, double *out, double *Ag,
+                          cudaStream_t s);
 cudaError_t launch_combine(const ColumnState &st, const double *proj, double lo, double hi, double sigma,
                            double *phi, cudaStream_t s);
 
