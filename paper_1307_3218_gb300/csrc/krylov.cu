@@ -135,26 +135,6 @@ template <> struct DotAcc<float> {
     }
 };
 
-__device__ __forceinline__ void load4(const double *p, double (&v)[4])
-{
-    const double2 a = __ldg(reinterpret_cast<const double2 *>(p));
-    const double2 b = __ldg(reinterpret_cast<const double2 *>(p) + 1);
-    v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
-}
-__device__ __forceinline__ void load4(const float *p, float (&v)[4])
-{
-    const float4 a = __ldg(reinterpret_cast<const float4 *>(p));
-    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
-}
-__device__ __forceinline__ void store4(double *p, const double (&v)[4])
-{
-    reinterpret_cast<double2 *>(p)[0] = make_double2(v[0], v[1]);
-    reinterpret_cast<double2 *>(p)[1] = make_double2(v[2], v[3]);
-}
-__device__ __forceinline__ void store4(float *p, const float (&v)[4])
-{
-    reinterpret_cast<float4 *>(p)[0] = make_float4(v[0], v[1], v[2], v[3]);
-}
 
 // ------------------------------------------------------------------ init
 // k_1 = e_j / sqrt(S_jj); S k_1 = (column j of S) / sqrt(S_jj), read from block

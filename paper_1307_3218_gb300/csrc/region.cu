@@ -256,47 +256,45 @@ __global__ void __launch_bounds__(256) spmm_regional_hs_kernel(
     for (int s = 0; s < cnt; ++s) {
         const int q = lci[base + (int64_t)s * n_reg + p];
         const int64_t k = lgk[base + (int64_t)s * n_reg + p];
+        // whole 4-vectors per load: the lanes read different blocks, so every
+        // load instruction costs the L1 one sector per lane
         VT xv[4];
-        const VT *xq = x + 32 * (int64_t)tinv[(int64_t)(q >> 3) * ncols + c] + 4 * (q & 7);
-#pragma unroll
-        for (int e = 0; e < 4; ++e) xv[e] = xq[e];
+        load4(x + 32 * (int64_t)tinv[(int64_t)(q >> 3) * ncols + c] + 4 * (q & 7), xv);
         const VT *Hb = Hv + stride * k;
         const VT *Sb = Sv + stride * k;
 #pragma unroll
         for (int a = 0; a < 4; ++a) {
+            VT hr[4], lr[4], sr[4];
+            load4(Hb + 4 * a, hr);
+            if constexpr (kF) load4(Hb + 16 + 4 * a, lr);
+            if constexpr (kS) load4(Sb + 4 * a, sr);
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
                 if constexpr (kF) {
-                    const float h = Hb[4 * a + e], l = Hb[16 + 4 * a + e];
-                    const float pr = __fmul_rn(h, xv[e]);
-                    const float er = __fmaf_rn(h, xv[e], -pr);
-                    df_add(acc[a], acl[a], pr, __fmaf_rn(l, xv[e], er));
+                    const float pr = __fmul_rn(hr[e], xv[e]);
+                    const float er = __fmaf_rn(hr[e], xv[e], -pr);
+                    df_add(acc[a], acl[a], pr, __fmaf_rn(lr[e], xv[e], er));
                 } else {
-                    acc[a] = fma(Hb[4 * a + e], xv[e], acc[a]);
+                    acc[a] = fma(hr[e], xv[e], acc[a]);
                 }
-                if constexpr (kS) sacc[a] = fma(Sb[4 * a + e], xv[e], sacc[a]);
+                if constexpr (kS) sacc[a] = fma(sr[e], xv[e], sacc[a]);
             }
         }
     }
     const int64_t yp = 32 * (int64_t)tinv[(int64_t)(p >> 3) * ncols + c] + 4 * (p & 7);
-    VT *y = U + (int64_t)c * ldu + yp;
     if constexpr (kF) {
-        VT *yl = Ulo + (int64_t)c * ldu + yp;
+        VT yh[4], yl[4];
 #pragma unroll
         for (int a = 0; a < 4; ++a) {
-            const float h = __fadd_rn(acc[a], acl[a]);
-            y[a] = h;
-            yl[a] = __fsub_rn(acl[a], __fsub_rn(h, acc[a]));
+            yh[a] = __fadd_rn(acc[a], acl[a]);
+            yl[a] = __fsub_rn(acl[a], __fsub_rn(yh[a], acc[a]));
         }
+        store4(U + (int64_t)c * ldu + yp, yh);
+        store4(Ulo + (int64_t)c * ldu + yp, yl);
     } else {
-#pragma unroll
-        for (int a = 0; a < 4; ++a) y[a] = acc[a];
+        store4(U + (int64_t)c * ldu + yp, acc);
     }
-    if constexpr (kS) {
-        VT *sy = SY + (int64_t)c * ldsy + yp;
-#pragma unroll
-        for (int a = 0; a < 4; ++a) sy[a] = sacc[a];
-    }
+    if constexpr (kS) store4(SY + (int64_t)c * ldsy + yp, sacc);
 }
 
 }  // namespace
