@@ -609,7 +609,12 @@ size_t per_column_bytes(const ColumnShape &shape, size_t vs, int nu, int region_
 int64_t clamp_batch(int64_t B, int64_t nc, bool regional)
 {
     B = std::min<int64_t>(std::max<int64_t>(B, 1), nc);
-    return std::min<int64_t>(B, regional ? 65535 : 65535 * 32);
+    B = std::min<int64_t>(B, regional ? 65535 : 65535 * 32);
+    // regional batches hold whole groups of 4 columns, so that the orbitals of
+    // one atom, listed together, stay in one batch and share the regional
+    // product's block reads
+    if (regional && B < nc && B >= 4) B -= B % 4;
+    return B;
 }
 
 // Offsets and sizes of a solve of nc columns (prow = rows of the columns'

@@ -227,16 +227,22 @@ __device__ __forceinline__ void df_add(float &hi, float &lo, float h2, float l2)
 
 // y = H_local x and, with kS, S_local x in one pass (both feed the same
 // Gram-Schmidt step and share the local block list, so the x gathers and the
-// index reads serve both).  Lanes run over local block rows of one column, so
-// the local-structure reads coalesce and the x gathers stay inside the
-// column's short local vector.  FP32: H by exact products and two-sums over
-// its hi + lo values, output as a (hi, lo) pair (the subspace matrix entries
-// use it), S by FMAs over its hi values; FP64: FMAs.  Rows whose support tile
-// lies more than `lim` hops from the column's atom are exact zeros and are
-// written without being computed.
-template <typename VT, bool kS>
-__global__ void __launch_bounds__(256) spmm_regional_hs_kernel(
-    int n_reg, int maxrow, const int *__restrict__ lcnt, const int *__restrict__ lci,
+// index reads serve both).  Lanes run over local block rows, so the
+// local-structure reads coalesce and the x gathers stay inside the columns'
+// short local vectors.  FP32: H by exact products and two-sums over its hi + lo
+// values, output as a (hi, lo) pair (the subspace matrix entries use it), S by
+// FMAs over its hi values; FP64: FMAs.  Rows whose support tile lies more than
+// `lim` hops from the column's atom are exact zeros and are written without
+// being computed.
+//
+// The NC batch columns c0 .. c0 + NC - 1 belong to one atom here: a column's
+// region, local block lists and tile order depend only on its atom, so one
+// pass over the blocks, each block read once, serves all NC columns (the
+// lanes read different blocks, so the block reads are what the L1 spends its
+// time on).  Every column's sums run in the same order as alone.
+template <typename VT, bool kS, int NC>
+__device__ __forceinline__ void regional_rows(
+    int p, int c0, int n_reg, int maxrow, const int *__restrict__ lcnt, const int *__restrict__ lci,
     const int *__restrict__ lgk, const VT *__restrict__ Hv, const VT *__restrict__ Sv,
     const VT *__restrict__ X, int64_t ldx, VT *__restrict__ U, VT *__restrict__ Ulo, int64_t ldu,
     VT *__restrict__ SY, int64_t ldsy, int ncols, const uint8_t *__restrict__ thop,
@@ -244,22 +250,21 @@ __global__ void __launch_bounds__(256) spmm_regional_hs_kernel(
 {
     constexpr bool kF = sizeof(VT) == 4;
     constexpr int stride = kF ? 32 : 16;
-    const int p = blockIdx.x * 32 + threadIdx.x;
-    const int c = blockIdx.y * 8 + threadIdx.y;
-    if (p >= n_reg || c >= ncols) return;
-    const VT *x = X + (int64_t)c * ldx;
-    const int64_t base = (int64_t)c * maxrow * n_reg;
-    const bool act = (int)thop[(int64_t)(p >> 3) * ncols + c] <= lim;
-    const int cnt = act ? lcnt[(int64_t)c * n_reg + p] : 0;
-    VT acc[4] = {VT(0), VT(0), VT(0), VT(0)}, acl[4] = {VT(0), VT(0), VT(0), VT(0)};
-    VT sacc[4] = {VT(0), VT(0), VT(0), VT(0)};
+    const int64_t base = (int64_t)c0 * maxrow * n_reg;
+    const bool act = (int)thop[(int64_t)(p >> 3) * ncols + c0] <= lim;
+    const int cnt = act ? lcnt[(int64_t)c0 * n_reg + p] : 0;
+    VT acc[NC][4], acl[NC][4], sacc[NC][4];
+#pragma unroll
+    for (int m = 0; m < NC; ++m)
+#pragma unroll
+        for (int a = 0; a < 4; ++a) acc[m][a] = acl[m][a] = sacc[m][a] = VT(0);
     for (int s = 0; s < cnt; ++s) {
         const int q = lci[base + (int64_t)s * n_reg + p];
         const int64_t k = lgk[base + (int64_t)s * n_reg + p];
-        // whole 4-vectors per load: the lanes read different blocks, so every
-        // load instruction costs the L1 one sector per lane
-        VT xv[4];
-        load4(x + 32 * (int64_t)tinv[(int64_t)(q >> 3) * ncols + c] + 4 * (q & 7), xv);
+        const int64_t xp = 32 * (int64_t)tinv[(int64_t)(q >> 3) * ncols + c0] + 4 * (q & 7);
+        VT xv[NC][4];
+#pragma unroll
+        for (int m = 0; m < NC; ++m) load4(X + (int64_t)(c0 + m) * ldx + xp, xv[m]);
         const VT *Hb = Hv + stride * k;
         const VT *Sb = Sv + stride * k;
 #pragma unroll
@@ -269,32 +274,76 @@ __global__ void __launch_bounds__(256) spmm_regional_hs_kernel(
             if constexpr (kF) load4(Hb + 16 + 4 * a, lr);
             if constexpr (kS) load4(Sb + 4 * a, sr);
 #pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                if constexpr (kF) {
-                    const float pr = __fmul_rn(hr[e], xv[e]);
-                    const float er = __fmaf_rn(hr[e], xv[e], -pr);
-                    df_add(acc[a], acl[a], pr, __fmaf_rn(lr[e], xv[e], er));
-                } else {
-                    acc[a] = fma(hr[e], xv[e], acc[a]);
+            for (int m = 0; m < NC; ++m) {
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    if constexpr (kF) {
+                        const float pr = __fmul_rn(hr[e], xv[m][e]);
+                        const float er = __fmaf_rn(hr[e], xv[m][e], -pr);
+                        df_add(acc[m][a], acl[m][a], pr, __fmaf_rn(lr[e], xv[m][e], er));
+                    } else {
+                        acc[m][a] = fma(hr[e], xv[m][e], acc[m][a]);
+                    }
+                    if constexpr (kS) sacc[m][a] = fma(sr[e], xv[m][e], sacc[m][a]);
                 }
-                if constexpr (kS) sacc[a] = fma(sr[e], xv[e], sacc[a]);
             }
         }
     }
-    const int64_t yp = 32 * (int64_t)tinv[(int64_t)(p >> 3) * ncols + c] + 4 * (p & 7);
-    if constexpr (kF) {
-        VT yh[4], yl[4];
+    const int64_t yp = 32 * (int64_t)tinv[(int64_t)(p >> 3) * ncols + c0] + 4 * (p & 7);
 #pragma unroll
-        for (int a = 0; a < 4; ++a) {
-            yh[a] = __fadd_rn(acc[a], acl[a]);
-            yl[a] = __fsub_rn(acl[a], __fsub_rn(yh[a], acc[a]));
+    for (int m = 0; m < NC; ++m) {
+        const int64_t c = c0 + m;
+        if constexpr (kF) {
+            VT yh[4], yl[4];
+#pragma unroll
+            for (int a = 0; a < 4; ++a) {
+                yh[a] = __fadd_rn(acc[m][a], acl[m][a]);
+                yl[a] = __fsub_rn(acl[m][a], __fsub_rn(yh[a], acc[m][a]));
+            }
+            store4(U + c * ldu + yp, yh);
+            store4(Ulo + c * ldu + yp, yl);
+        } else {
+            store4(U + c * ldu + yp, acc[m]);
         }
-        store4(U + (int64_t)c * ldu + yp, yh);
-        store4(Ulo + (int64_t)c * ldu + yp, yl);
-    } else {
-        store4(U + (int64_t)c * ldu + yp, acc);
+        if constexpr (kS) store4(SY + c * ldsy + yp, sacc[m]);
     }
-    if constexpr (kS) store4(SY + (int64_t)c * ldsy + yp, sacc);
+}
+
+// Thread (x, y) of a 32x8 CTA: local row p = 32 blockIdx.x + x of the group
+// of G = reg_group<VT>() batch columns starting at c0 = G (8 blockIdx.y + y).
+// A full group whose columns share their atom (the orbitals of one atom, in
+// the order the columns are usually listed) takes one shared pass; any other
+// group runs its columns one by one.  G is what the registers allow: FP64
+// accumulators for four columns would leave one CTA per SM.
+template <typename VT>
+constexpr int reg_group()
+{
+    return sizeof(VT) == 4 ? 4 : 2;
+}
+
+template <typename VT, bool kS>
+__global__ void __launch_bounds__(256) spmm_regional_hs_kernel(
+    int n_reg, int maxrow, const int *__restrict__ lcnt, const int *__restrict__ lci,
+    const int *__restrict__ lgk, const VT *__restrict__ Hv, const VT *__restrict__ Sv,
+    const VT *__restrict__ X, int64_t ldx, VT *__restrict__ U, VT *__restrict__ Ulo, int64_t ldu,
+    VT *__restrict__ SY, int64_t ldsy, int ncols, const int64_t *__restrict__ cols,
+    const uint8_t *__restrict__ thop, const uint16_t *__restrict__ tinv, int lim)
+{
+    const int p = blockIdx.x * 32 + threadIdx.x;
+    constexpr int G = reg_group<VT>();
+    const int c0 = (blockIdx.y * 8 + threadIdx.y) * G;
+    if (p >= n_reg || c0 >= ncols) return;
+    const int members = min(G, ncols - c0);
+    bool shared = members == G;
+    for (int m = 1; m < members; ++m) shared = shared && (cols[c0 + m] >> 2) == (cols[c0] >> 2);
+    if (shared) {
+        regional_rows<VT, kS, G>(p, c0, n_reg, maxrow, lcnt, lci, lgk, Hv, Sv, X, ldx, U, Ulo, ldu,
+                                         SY, ldsy, ncols, thop, tinv, lim);
+    } else {
+        for (int m = 0; m < members; ++m)
+            regional_rows<VT, kS, 1>(p, c0 + m, n_reg, maxrow, lcnt, lci, lgk, Hv, Sv, X, ldx, U, Ulo, ldu,
+                                     SY, ldsy, ncols, thop, tinv, lim);
+    }
 }
 
 }  // namespace
@@ -305,26 +354,27 @@ cudaError_t launch_spmm_regional_hs(const DeviceMatrix &A, const RegionMaps &rm,
 {
     if (!b.thop || !b.tinv || b.ntile * 8 < rm.n_reg) return cudaErrorInvalidValue;
     const dim3 block(32, 8);
-    const dim3 grid((unsigned)((rm.n_reg + 31) / 32), (unsigned)((b.nb + 7) / 8));
+    const int G = b.prec == 0 ? reg_group<double>() : reg_group<float>();
+    const dim3 grid((unsigned)((rm.n_reg + 31) / 32), (unsigned)(((b.nb + G - 1) / G + 7) / 8));
     const int64_t ldu = b.shape.m_pad;
     if (b.prec == 0) {
         if (SY)
             spmm_regional_hs_kernel<double, true><<<grid, block, 0, s>>>(
                 rm.n_reg, rm.maxrow, rm.lcnt, rm.lci, rm.lgk, A.Hd, A.Sd, (const double *)X, ldx, (double *)b.U,
-                nullptr, ldu, (double *)SY, ldsy, b.nb, b.thop, b.tinv, lim);
+                nullptr, ldu, (double *)SY, ldsy, b.nb, b.cols, b.thop, b.tinv, lim);
         else
             spmm_regional_hs_kernel<double, false><<<grid, block, 0, s>>>(
                 rm.n_reg, rm.maxrow, rm.lcnt, rm.lci, rm.lgk, A.Hd, A.Sd, (const double *)X, ldx, (double *)b.U,
-                nullptr, ldu, nullptr, 0, b.nb, b.thop, b.tinv, lim);
+                nullptr, ldu, nullptr, 0, b.nb, b.cols, b.thop, b.tinv, lim);
     } else {
         if (SY)
             spmm_regional_hs_kernel<float, true><<<grid, block, 0, s>>>(
                 rm.n_reg, rm.maxrow, rm.lcnt, rm.lci, rm.lgk, A.Hf, A.Sf, (const float *)X, ldx, (float *)b.U,
-                (float *)b.Ulo, ldu, (float *)SY, ldsy, b.nb, b.thop, b.tinv, lim);
+                (float *)b.Ulo, ldu, (float *)SY, ldsy, b.nb, b.cols, b.thop, b.tinv, lim);
         else
             spmm_regional_hs_kernel<float, false><<<grid, block, 0, s>>>(
                 rm.n_reg, rm.maxrow, rm.lcnt, rm.lci, rm.lgk, A.Hf, A.Sf, (const float *)X, ldx, (float *)b.U,
-                (float *)b.Ulo, ldu, nullptr, 0, b.nb, b.thop, b.tinv, lim);
+                (float *)b.Ulo, ldu, nullptr, 0, b.nb, b.cols, b.thop, b.tinv, lim);
     }
     return cudaGetLastError();
 }
