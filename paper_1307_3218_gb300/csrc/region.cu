@@ -7,12 +7,13 @@
 // minimum-image distance (ties to the lower atom index), kept in ascending
 // atom index.  Local orbital 4 p + a is orbital a of atom R_J[p].
 //
-// Per batch column c (the region is per column; the four columns of an atom
-// build the same one):
+// Per batch column c (a region depends only on the column's atom, so of a
+// run of batch columns of one atom only the first, its leader, searches):
 //   region_kernel:     candidates from the cell list within radius r_s,
 //                      bitonic sort by (d^2, index), the first n_reg sorted
 //                      again by index -> reg[c][p]
-//   local_bsr_kernel:  for every local block row p, the blocks of global row
+//   local_bsr_kernel:  copies the leader's region to the other columns of
+//                      its run; for every local block row p, the blocks of global row
 //                      R_J[p] whose column atom lies in R_J (binary search):
 //                      local column lci and global block index lgk, stored
 //                      slot-major ([c][slot][p]) so that lanes over p coalesce
@@ -44,6 +45,16 @@ __device__ __forceinline__ double min_image_d2(const double *pi, const double *p
         d2 = q == 0 ? __dmul_rn(d, d) : __dadd_rn(d2, __dmul_rn(d, d));
     }
     return d2;
+}
+
+// First batch column of the run of consecutive batch columns that share
+// column c's atom.
+__device__ __forceinline__ int run_leader(const int64_t *__restrict__ cols, int c)
+{
+    const int64_t J = cols[c] >> 2;
+    int l = c;
+    while (l > 0 && (cols[l - 1] >> 2) == J) --l;
+    return l;
 }
 
 __device__ __forceinline__ bool key_less(double da, int ia, double db, int ib)
@@ -86,6 +97,10 @@ __global__ void __launch_bounds__(1024) region_kernel(
     __shared__ double bx[3], pj[3];
     const int c = blockIdx.x;
     const int J = (int)(cols[c] >> 2);
+    if (c > 0 && (cols[c - 1] >> 2) == J) {   // not a leader: local_bsr_kernel copies the region
+        if (threadIdx.x == 0) rstat[c] = 0;
+        return;
+    }
     if (threadIdx.x < 3) {
         bx[threadIdx.x] = box[threadIdx.x];
         pj[threadIdx.x] = pos[3 * (int64_t)J + threadIdx.x];
@@ -147,14 +162,17 @@ __global__ void __launch_bounds__(1024) region_kernel(
 }
 
 __global__ void __launch_bounds__(256) local_bsr_kernel(
-    const int64_t *__restrict__ rp, const int32_t *__restrict__ ci, const int *__restrict__ reg,
-    int n_reg, int maxrow, int *__restrict__ lcnt, int *__restrict__ lci, int *__restrict__ lgk)
+    const int64_t *__restrict__ rp, const int32_t *__restrict__ ci, const int64_t *__restrict__ cols,
+    int *__restrict__ reg, int n_reg, int maxrow, int *__restrict__ lcnt, int *__restrict__ lci,
+    int *__restrict__ lgk)
 {
     const int c = blockIdx.y;
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n_reg) return;
-    const int *R = reg + (int64_t)c * n_reg;
+    const int lead = run_leader(cols, c);
+    const int *R = reg + (int64_t)lead * n_reg;
     const int I = R[p];
+    if (lead != c) reg[(int64_t)c * n_reg + p] = I;
     int cnt = 0;
     const int64_t base = (int64_t)c * maxrow * n_reg;
     for (int64_t k = rp[I]; k < rp[I + 1]; ++k) {
@@ -399,8 +417,8 @@ cudaError_t launch_local_bsr(const DeviceMatrix &A, const RegionMaps &rm, const 
                              cudaStream_t s)
 {
     const dim3 grid((unsigned)((rm.n_reg + 255) / 256), (unsigned)b.nb);
-    local_bsr_kernel<<<grid, 256, 0, s>>>(A.rp, A.ci, rm.reg, rm.n_reg, rm.maxrow, rm.lcnt, rm.lci,
-                                          rm.lgk);
+    local_bsr_kernel<<<grid, 256, 0, s>>>(A.rp, A.ci, b.cols, rm.reg, rm.n_reg, rm.maxrow, rm.lcnt,
+                                          rm.lci, rm.lgk);
     return cudaGetLastError();
 }
 
