@@ -236,6 +236,9 @@ int marnoldi_solved_shape(marnoldi_ctx *ctx, int64_t *ncols, int *nu);
 /*
  * Tuning and instrumentation.
  *   marnoldi_set_batch: columns per device batch (0 = choose from free memory).
+ *     In regional mode a batch smaller than the column list is rounded down to
+ *     a multiple of 4, so that the orbitals of one atom, listed together, stay
+ *     in one batch (they share the regional product's block reads).
  *   marnoldi_set_profiling: 1 = time every kernel launch with CUDA events on the
  *     context's stream (adds event records; off by default).
  *   marnoldi_kernel_stats: for kind = 0 .. marnoldi_kernel_kinds()-1, the kernel
@@ -328,7 +331,9 @@ int marnoldi_count_noalloc(const double *eps_device, const double *w_device,
  *     real orbital (columns == NULL) and one marnoldi_density, computed on the
  *     host from the block pattern alone: structure copies, column state, batch
  *     workspace of batch_columns columns (>= 1; clamped to the column count and
- *     the launch limits; the value used goes to *batch_used, which may be NULL)
+ *     the launch limits, and in regional mode rounded down to a multiple of 4
+ *     when below the column count; the value used goes to *batch_used, which
+ *     may be NULL)
  *     and the density staging.  box is needed in regional mode (cell list).  It
  *     equals the peak of marnoldi_device_bytes of such a run.  Errors
  *     (MARNOLDI_EINVAL, through marnoldi_last_error(NULL)): arguments that
