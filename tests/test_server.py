@@ -44,6 +44,20 @@ def test_footprint_grows_with_batch_and_clamps(lib):
     assert b_mixed < b_all
 
 
+def test_regional_batches_hold_whole_groups_of_four(lib):
+    """In regional mode a batch below the column count is rounded down to a
+    multiple of 4 (the orbitals of one atom stay together); global mode and
+    batches of 1 to 3 columns are not rounded."""
+    t = config_c1()
+    box = t.structure.box
+    ncols = t.real_columns().size
+    for B, want in ((1, 1), (3, 3), (7, 4), (65, 64), (ncols - 1, ncols - 4), (ncols, ncols), (1 << 40, ncols)):
+        _, used = m.marnoldi_footprint(t.n_block_rows, t.row_ptr, t.orbital_mask, box, 1, 30, 32, B)
+        assert used == want, (B, used)
+    _, used = m.marnoldi_footprint(t.n_block_rows, t.row_ptr, t.orbital_mask, None, 1, 30, 0, 7)
+    assert used == 7
+
+
 def test_footprint_counts_only_real_orbitals(lib):
     t = tiny_hydrocarbon(24, 8, seed=3)
     nreal = t.real_columns().size
