@@ -143,7 +143,7 @@ void load_tune_cache_locked()
         k.m_pad = mp;
         ColumnShape cand[3];
         const int n = column_shape_candidates(k.m_pad, cand);
-        for (int q = 0; q < n; ++q)   // only shapes this build has
+        for (int q = 0; q < n; ++q)   // only shapes the library is compiled for
             if (cand[q].vpt == v && cand[q].threads == t) g_tuned[k] = cand[q];
     }
     fclose(f);
