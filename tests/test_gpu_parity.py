@@ -263,6 +263,31 @@ def test_nu300_sampled(m):
     assert g["N"] == pytest.approx(t.n_electrons, rel=1e-12)
 
 
+@pytest.mark.parametrize("prec", [0, 1])
+def test_nu_at_the_limit(m, prec):
+    """nu = 320, the largest the library accepts (321 is refused), on 100-atom
+    amorphous carbon (M = 400), FP64 and mixed, against the oracle on a sample."""
+    from tbsynth import amorphous_system
+    t = amorphous_system(100, seed=3)
+    ctx = m.setup_system(t, prec)
+    with pytest.raises(m.MarnoldiError) as ei:
+        m.marnoldi_solve(ctx, None, 321, 0, t.n_electrons, KT)
+    assert ei.value.code == m.marnoldi.MARNOLDI_EINVAL
+    m.marnoldi_destroy(ctx)
+    g = gpu_solve(m, t, 320, prec=prec)
+    assert g["N"] == pytest.approx(t.n_electrons, rel=1e-12 if prec == 0 else 1e-8)
+    sample = np.sort(np.random.default_rng(7).choice(t.M, size=24, replace=False))
+    ref = oracle.solve(t, nu=320, kT=KT, mu_fixed=g["mu"], cols=sample)
+    mask = ~np.isnan(ref.rho)
+    drho = np.abs(g["rho"][mask] - ref.rho[mask]).max()
+    drhoE = np.abs(g["rhoE"][mask] - ref.rhoE[mask]).max()
+    if prec == 0:
+        assert drho <= FP64_REL * np.abs(ref.rho[mask]).max()
+        assert drhoE <= FP64_REL * np.abs(ref.rhoE[mask]).max()
+    else:
+        assert drho <= 1e-5 and drhoE <= 1e-4
+
+
 # ----------------------------------------------------------------- mixed precision
 
 def mixed_errors(g, ref, t):
