@@ -585,7 +585,7 @@ size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
 // state, kept until the next solve, and the batch workspace, kept and only
 // grown across solves.
 struct SolvePlan {
-    size_t o_cols, o_poff, o_nue, o_est, o_eps, o_w, o_t, o_P, state_bytes;
+    size_t o_cols, o_poff, o_nue, o_est, o_eps, o_w, o_t, o_P, o_grp, state_bytes;
     int64_t B, ntile;
     ColumnShape shape;
     size_t vs;
@@ -633,7 +633,9 @@ bool plan_solve(int64_t m_vec, int prec, int nu, int region_atoms, int maxrow, i
     p.o_w = p.o_eps + al256((size_t)nc * nu * 8);
     p.o_t = p.o_w + al256((size_t)nc * nu * 8);
     p.o_P = p.o_t + al256((size_t)nc * nu * 8);
-    p.state_bytes = p.o_P + al256((size_t)prow * nu * 8);
+    p.o_grp = p.o_P + al256((size_t)prow * nu * 8);
+    // regional product groups: at most one per column plus one end mark per batch
+    p.state_bytes = p.o_grp + (regional ? al256((size_t)(nc + (nc + B - 1) / B) * 4) : 0);
 
     p.B = B;
     p.shape = column_shape(m_vec, prec);
@@ -1203,6 +1205,28 @@ int marnoldi_solve(marnoldi_ctx *c, const int64_t *columns, int64_t ncols, int n
     c->st.P = (double *)(sb + plan.o_P);
     cudaError_t e = cudaMemcpyAsync(c->d_cols, cols.data(), nc * 8, cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync((void *)c->st.p_off, p_off.data(), nc * 8, cudaMemcpyHostToDevice, c->stream);
+    // regional product groups per batch: runs of one atom's columns, at most
+    // regional_group() long, then the batch's column count as an end mark
+    std::vector<int> grp;
+    std::vector<int64_t> gofs;
+    if (regional) {
+        const int G = regional_group(c->prec);
+        for (int64_t start = 0; start < nc; start += B) {
+            const int64_t nbat = std::min<int64_t>(B, nc - start);
+            gofs.push_back((int64_t)grp.size());
+            for (int64_t q = 0; q < nbat;) {
+                grp.push_back((int)q);
+                const int64_t J = cols[start + q] >> 2;
+                int64_t len = 1;
+                while (q + len < nbat && len < G && (cols[start + q + len] >> 2) == J) ++len;
+                q += len;
+            }
+            grp.push_back((int)nbat);
+        }
+        gofs.push_back((int64_t)grp.size());
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(sb + plan.o_grp, grp.data(), grp.size() * 4, cudaMemcpyHostToDevice, c->stream);
+    }
     if (e == cudaSuccess) e = cudaMemsetAsync(c->st.eig_status, 0, nc * 4, c->stream);
     if (e != cudaSuccess) return fail_cuda(c, e, "column state upload");
 
@@ -1310,6 +1334,9 @@ int marnoldi_solve(marnoldi_ctx *c, const int64_t *columns, int64_t ncols, int n
         kb.nb = (int)std::min<int64_t>(B, nc - start);
         kb.cols = c->d_cols + start;
         if (regional) {
+            const int64_t bi = start / B;
+            c->rm.gstart = (const int *)(sb + plan.o_grp) + gofs[bi];
+            c->rm.ngroups = (int)(gofs[bi + 1] - gofs[bi] - 1);
             if ((rc = find_regions(c, kb))) return rc;
             if ((rc = launch(c, KK_REGION, [&] { return launch_local_bsr(c->A, c->rm, kb, c->stream); })))
                 return rc;

@@ -176,7 +176,15 @@ struct RegionMaps {
     int ncell[3] = {1, 1, 1};
     double cell_edge[3] = {1.0, 1.0, 1.0};
     int *reg = nullptr, *lcnt = nullptr, *lci = nullptr, *lgk = nullptr, *rstat = nullptr;
+    // the batch's groups of the regional product: group g is batch columns
+    // gstart[g] .. gstart[g + 1] - 1, one atom's, at most regional_group(prec)
+    const int *gstart = nullptr;
+    int ngroups = 0;
 };
+
+// Columns per group of the regional product (the columns of one atom that
+// share a pass over the local blocks): 4 in mixed precision, 2 in FP64.
+int regional_group(int prec);
 
 cudaError_t launch_region(const RegionMaps &rm, const KrylovBatch &b, double rs, int cap,
                           cudaStream_t s);

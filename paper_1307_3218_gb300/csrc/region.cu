@@ -327,12 +327,13 @@ __device__ __forceinline__ void regional_rows(
     }
 }
 
-// Thread (x, y) of a 32x8 CTA: local row p = 32 blockIdx.x + x of the group
-// of G = reg_group<VT>() batch columns starting at c0 = G (8 blockIdx.y + y).
-// A full group whose columns share their atom (the orbitals of one atom, in
-// the order the columns are usually listed) takes one shared pass; any other
-// group runs its columns one by one.  G is what the registers allow: FP64
-// accumulators for four columns would leave one CTA per SM.
+// Thread (x, y) of a 32x8 CTA: local row p = 32 blockIdx.x + x of group
+// g = 8 blockIdx.y + y, the batch columns gstart[g] .. gstart[g + 1] - 1 of one
+// atom (the host splits the batch into runs of one atom's columns of at most
+// G = reg_group<VT>()).  A full group takes one shared pass; a shorter one (an
+// atom with fewer real orbitals, or a run cut by the batch) runs its columns
+// one by one.  G is what the registers allow: FP64 accumulators for four
+// columns would leave one CTA per SM.
 template <typename VT>
 constexpr int reg_group()
 {
@@ -344,27 +345,30 @@ __global__ void __launch_bounds__(256) spmm_regional_hs_kernel(
     int n_reg, int maxrow, const int *__restrict__ lcnt, const int *__restrict__ lci,
     const int *__restrict__ lgk, const VT *__restrict__ Hv, const VT *__restrict__ Sv,
     const VT *__restrict__ X, int64_t ldx, VT *__restrict__ U, VT *__restrict__ Ulo, int64_t ldu,
-    VT *__restrict__ SY, int64_t ldsy, int ncols, const int64_t *__restrict__ cols,
+    VT *__restrict__ SY, int64_t ldsy, int ncols, const int *__restrict__ gstart, int ngroups,
     const uint8_t *__restrict__ thop, const uint16_t *__restrict__ tinv, int lim)
 {
-    const int p = blockIdx.x * 32 + threadIdx.x;
     constexpr int G = reg_group<VT>();
-    const int c0 = (blockIdx.y * 8 + threadIdx.y) * G;
-    if (p >= n_reg || c0 >= ncols) return;
-    const int members = min(G, ncols - c0);
-    bool shared = members == G;
-    for (int m = 1; m < members; ++m) shared = shared && (cols[c0 + m] >> 2) == (cols[c0] >> 2);
-    if (shared) {
-        regional_rows<VT, kS, G>(p, c0, n_reg, maxrow, lcnt, lci, lgk, Hv, Sv, X, ldx, U, Ulo, ldu,
-                                         SY, ldsy, ncols, thop, tinv, lim);
+    const int p = blockIdx.x * 32 + threadIdx.x;
+    const int g = blockIdx.y * 8 + threadIdx.y;
+    if (p >= n_reg || g >= ngroups) return;
+    // clipped to ncols: a run of the autotuner covers the batch's first columns only
+    const int c0 = gstart[g], c1 = min(gstart[g + 1], ncols);
+    if (c0 >= c1) return;
+    if (c1 - c0 == G) {
+        regional_rows<VT, kS, G>(p, c0, n_reg, maxrow, lcnt, lci, lgk, Hv, Sv, X, ldx, U, Ulo, ldu, SY, ldsy,
+                                 ncols, thop, tinv, lim);
     } else {
-        for (int m = 0; m < members; ++m)
-            regional_rows<VT, kS, 1>(p, c0 + m, n_reg, maxrow, lcnt, lci, lgk, Hv, Sv, X, ldx, U, Ulo, ldu,
-                                     SY, ldsy, ncols, thop, tinv, lim);
+#pragma unroll 1
+        for (int c = c0; c < c1; ++c)
+            regional_rows<VT, kS, 1>(p, c, n_reg, maxrow, lcnt, lci, lgk, Hv, Sv, X, ldx, U, Ulo, ldu, SY, ldsy,
+                                     ncols, thop, tinv, lim);
     }
 }
 
 }  // namespace
+
+int regional_group(int prec) { return prec == 0 ? reg_group<double>() : reg_group<float>(); }
 
 cudaError_t launch_spmm_regional_hs(const DeviceMatrix &A, const RegionMaps &rm, const KrylovBatch &b,
                                     const void *X, int64_t ldx, void *SY, int64_t ldsy, int lim,
@@ -372,27 +376,27 @@ cudaError_t launch_spmm_regional_hs(const DeviceMatrix &A, const RegionMaps &rm,
 {
     if (!b.thop || !b.tinv || b.ntile * 8 < rm.n_reg) return cudaErrorInvalidValue;
     const dim3 block(32, 8);
-    const int G = b.prec == 0 ? reg_group<double>() : reg_group<float>();
-    const dim3 grid((unsigned)((rm.n_reg + 31) / 32), (unsigned)(((b.nb + G - 1) / G + 7) / 8));
+    if (!rm.gstart || rm.ngroups < 1) return cudaErrorInvalidValue;
+    const dim3 grid((unsigned)((rm.n_reg + 31) / 32), (unsigned)((rm.ngroups + 7) / 8));
     const int64_t ldu = b.shape.m_pad;
     if (b.prec == 0) {
         if (SY)
             spmm_regional_hs_kernel<double, true><<<grid, block, 0, s>>>(
                 rm.n_reg, rm.maxrow, rm.lcnt, rm.lci, rm.lgk, A.Hd, A.Sd, (const double *)X, ldx, (double *)b.U,
-                nullptr, ldu, (double *)SY, ldsy, b.nb, b.cols, b.thop, b.tinv, lim);
+                nullptr, ldu, (double *)SY, ldsy, b.nb, rm.gstart, rm.ngroups, b.thop, b.tinv, lim);
         else
             spmm_regional_hs_kernel<double, false><<<grid, block, 0, s>>>(
                 rm.n_reg, rm.maxrow, rm.lcnt, rm.lci, rm.lgk, A.Hd, A.Sd, (const double *)X, ldx, (double *)b.U,
-                nullptr, ldu, nullptr, 0, b.nb, b.cols, b.thop, b.tinv, lim);
+                nullptr, ldu, nullptr, 0, b.nb, rm.gstart, rm.ngroups, b.thop, b.tinv, lim);
     } else {
         if (SY)
             spmm_regional_hs_kernel<float, true><<<grid, block, 0, s>>>(
                 rm.n_reg, rm.maxrow, rm.lcnt, rm.lci, rm.lgk, A.Hf, A.Sf, (const float *)X, ldx, (float *)b.U,
-                (float *)b.Ulo, ldu, (float *)SY, ldsy, b.nb, b.cols, b.thop, b.tinv, lim);
+                (float *)b.Ulo, ldu, (float *)SY, ldsy, b.nb, rm.gstart, rm.ngroups, b.thop, b.tinv, lim);
         else
             spmm_regional_hs_kernel<float, false><<<grid, block, 0, s>>>(
                 rm.n_reg, rm.maxrow, rm.lcnt, rm.lci, rm.lgk, A.Hf, A.Sf, (const float *)X, ldx, (float *)b.U,
-                (float *)b.Ulo, ldu, nullptr, 0, b.nb, b.cols, b.thop, b.tinv, lim);
+                (float *)b.Ulo, ldu, nullptr, 0, b.nb, rm.gstart, rm.ngroups, b.thop, b.tinv, lim);
     }
     return cudaGetLastError();
 }
