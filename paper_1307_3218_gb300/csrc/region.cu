@@ -18,7 +18,8 @@
 //                      local column lci and global block index lgk, stored
 //                      slot-major ([c][slot][p]) so that lanes over p coalesce
 //   init_regional:     k_1 = e_{jl} / sqrt(S_jj), S k_1 from row j's local blocks
-//   spmm_regional_hs:  H_local x and S_local x for every column in one pass,
+//   spmm_regional_hs:  H_local x and S_local x in one pass per group of one
+//                      atom's columns (each block read once for the group),
 //                      x and y of length m_pad >= 4 n_reg, matrix values
 //                      gathered from the global BSR through lgk
 #include "internal.h"
