@@ -1,0 +1,75 @@
+"""The bench's roofline accounting, recomputed independently on a small case.
+
+bench.support_counts (tiles of 8 atoms within L pattern hops of each column's
+atom, by scipy's shortest paths) and bench.gs_algorithmic_support (the bytes
+the Gram-Schmidt steps must move over the vectors' supports, summed with
+aggregated counts) feed the `achieved` figure of the bench's roofline.  Here
+a breadth-first search written out in Python and per-column, per-step loops
+give the same numbers exactly.
+"""
+
+from collections import deque
+
+import numpy as np
+import pytest
+
+import bench
+from tbsynth import amorphous_system, tiny_hydrocarbon
+
+
+def _hops(t, start):
+    dist = np.full(t.n_block_rows, -1, dtype=np.int64)
+    dist[start] = 0
+    q = deque([start])
+    while q:
+        a = q.popleft()
+        for k in range(t.row_ptr[a], t.row_ptr[a + 1]):
+            b = int(t.col_idx[k])
+            if dist[b] < 0:
+                dist[b] = dist[a] + 1
+                q.append(b)
+    return dist
+
+
+def _tile_counts(t, atom, nu, m_pad):
+    d = _hops(t, atom)
+    ntile = m_pad // 32
+    out = np.zeros(nu + 2, dtype=np.int64)
+    for tile in range(ntile):
+        members = [d[a] for a in range(8 * tile, min(8 * tile + 8, t.n_block_rows)) if d[a] >= 0]
+        if not members:
+            continue
+        h = min(members)
+        for L in range(nu + 2):
+            out[L] += h <= L
+    return out
+
+
+def _gs_bytes(tc, nu, vbytes):
+    total = 0
+    for c in range(tc.shape[0]):
+        E = 32 * tc[c]
+        for n in range(nu):
+            total += (2 if vbytes == 4 else 1) * E[n + 1]   # u (and its lo word)
+            total += E[n]                                    # w_n
+            for i in range(n + 1):
+                total += 2 * E[i + 1]                        # w_i and S w_i
+            if n + 1 < nu:
+                for i in range(n + 1):
+                    total += E[i + 1]                        # w_i again, for the subtraction
+                total += E[n + 1]                            # the new w
+    return total * vbytes
+
+
+@pytest.mark.parametrize("maker,nu", [(lambda: amorphous_system(64, seed=2), 6),
+                                      (lambda: tiny_hydrocarbon(20, 8, seed=1), 9)])
+def test_support_counts_and_gs_bytes(maker, nu):
+    t = maker()
+    cols = t.real_columns()
+    m_pad = bench.column_m_pad(t.M)
+    tc = bench.support_counts(t, cols, nu, m_pad)
+    want = np.array([_tile_counts(t, int(j) // 4, nu, m_pad) for j in cols])
+    np.testing.assert_array_equal(tc, want)
+    for vbytes in (4, 8):
+        got, _ = bench.gs_algorithmic_support(nu, tc, vbytes)
+        assert got == _gs_bytes(want, nu, vbytes)
