@@ -87,56 +87,84 @@ def amorphous_carbon(n_atoms: int, density_gcc: float = 3.0, d_min: float = 1.3,
                      seed: int = 0, sort: bool = True) -> Structure:
     """Random sequential addition of ``n_atoms`` carbon atoms in a periodic cube.
 
-    Candidates are drawn uniformly in the box and accepted when no accepted atom
-    lies closer than ``d_min`` (minimum-image distance).  A cell grid of edge
-    >= d_min keeps each test local.
+    Candidates are drawn uniformly in the box (batches of 4096 from the seeded
+    generator) and taken in order; a candidate is accepted when no accepted atom
+    lies closer than ``d_min`` (minimum-image distance).  Each batch is tested
+    at once against the atoms accepted before it (a cell grid of edge >= d_min
+    keeps the test local), and then in order against the batch's own earlier
+    acceptances, which gives the same atoms as testing one candidate at a time.
     """
+    from scipy.spatial import cKDTree
+
     L = (n_atoms / number_density(density_gcc)) ** (1.0 / 3.0)
     nc = max(1, int(L // d_min))
     cs = L / nc
     rng = np.random.default_rng(seed)
-    cells: dict[tuple[int, int, int], list[int]] = {}
-    xs: list[float] = []
-    ys: list[float] = []
-    zs: list[float] = []
     d2min = d_min * d_min
-    offs = [(a, b, c) for a in (-1, 0, 1) for b in (-1, 0, 1) for c in (-1, 0, 1)]
-    batch = rng.random((4096, 3)) * L
-    bi = 0
+    offs = np.array([(a, b, c) for a in (-1, 0, 1) for b in (-1, 0, 1) for c in (-1, 0, 1)], dtype=np.int64)
+    K = 2                                             # atom slots per cell, grown when one fills
+    slots = np.full((nc * nc * nc, K), -1, dtype=np.int64)
+    counts = np.zeros(nc * nc * nc, dtype=np.int64)
+    pos = np.empty((n_atoms, 3))
+    n = 0
     tries = 0
-    while len(xs) < n_atoms:
-        if bi == batch.shape[0]:
-            batch = rng.random((4096, 3)) * L
-            bi = 0
-        x, y, z = batch[bi]
-        bi += 1
-        tries += 1
-        if tries > 200 * n_atoms + 10000:
-            raise RuntimeError("random packing did not converge; density too high for d_min")
-        cx, cy, cz = int(x / cs) % nc, int(y / cs) % nc, int(z / cs) % nc
-        ok = True
-        for a, b, c in offs:
-            lst = cells.get(((cx + a) % nc, (cy + b) % nc, (cz + c) % nc))
-            if not lst:
-                continue
-            for k in lst:
-                dx = xs[k] - x
-                dy = ys[k] - y
-                dz = zs[k] - z
-                dx -= L * round(dx / L)
-                dy -= L * round(dy / L)
-                dz -= L * round(dz / L)
-                if dx * dx + dy * dy + dz * dz < d2min:
-                    ok = False
-                    break
-            if not ok:
-                break
-        if ok:
-            cells.setdefault((cx, cy, cz), []).append(len(xs))
-            xs.append(x)
-            ys.append(y)
-            zs.append(z)
-    pos = np.stack([np.array(xs), np.array(ys), np.array(zs)], axis=1)
+    limit = 200 * n_atoms + 10000
+
+    def d2_to(P, x):
+        # minimum-image squared distance from the points P to x, rounded as in
+        # a one-candidate-at-a-time test: d -= L round(d / L), (dx^2 + dy^2) + dz^2
+        d = P - x
+        d = d - L * np.round(d / L)
+        return (d[..., 0] * d[..., 0] + d[..., 1] * d[..., 1]) + d[..., 2] * d[..., 2]
+
+    while n < n_atoms:
+        batch = rng.random((4096, 3)) * L
+        cidx = (batch / cs).astype(np.int64) % nc                    # (B, 3)
+        cell = (cidx[:, 0] * nc + cidx[:, 1]) * nc + cidx[:, 2]
+        # against the atoms accepted before this batch
+        nb = (cidx[:, None, :] + offs[None, :, :]) % nc               # (B, 27, 3)
+        ncell = (nb[..., 0] * nc + nb[..., 1]) * nc + nb[..., 2]
+        ids = slots[ncell]                                            # (B, 27, K)
+        valid = ids >= 0
+        d2 = d2_to(pos[np.where(valid, ids, 0)], batch[:, None, None, :])
+        free = ~np.any(valid & (d2 < d2min), axis=(1, 2))
+        # pairs of this batch's candidates that may conflict (exact test below):
+        # only a candidate with an earlier partner needs the in-order test
+        tree = cKDTree(np.minimum(batch, np.nextafter(L, 0.0)), boxsize=L)
+        earlier: dict[int, list[int]] = {}
+        for i, j in tree.query_pairs(d_min * (1.0 + 1e-9) + 1e-12):
+            a, b = (i, j) if i < j else (j, i)
+            earlier.setdefault(b, []).append(a)
+        accepted = free.copy()
+        for i in sorted(earlier):
+            if accepted[i]:
+                for k in earlier[i]:
+                    if accepted[k] and d2_to(batch[k], batch[i]) < d2min:
+                        accepted[i] = False
+                        break
+        # candidates are consumed in order until n_atoms are accepted
+        order = np.flatnonzero(accepted)
+        take = order[:n_atoms - n]
+        used = int(take[-1]) + 1 if take.size == n_atoms - n else batch.shape[0]
+        if tries + used > limit:
+            # the one-at-a-time test stops at candidate number limit + 1
+            if np.count_nonzero(accepted[:max(0, limit - tries)]) < n_atoms - n:
+                raise RuntimeError("random packing did not converge; density too high for d_min")
+        tries += used
+        # the new atoms into the cell grid (slots within a cell in any order)
+        c_new = cell[take]
+        o = np.argsort(c_new, kind="stable")
+        srt = c_new[o]
+        starts = np.r_[0, np.flatnonzero(srt[1:] != srt[:-1]) + 1] if srt.size else np.zeros(0, np.int64)
+        rank = np.empty(c_new.size, dtype=np.int64)   # earlier new atoms in the same cell
+        rank[o] = np.arange(srt.size) - np.repeat(starts, np.diff(np.r_[starts, srt.size]))
+        need = int((counts[c_new] + rank).max(initial=-1)) + 1
+        if need > slots.shape[1]:
+            slots = np.concatenate([slots, np.full((slots.shape[0], need - slots.shape[1]), -1, np.int64)], axis=1)
+        slots[c_new, counts[c_new] + rank] = np.arange(n, n + take.size)
+        np.add.at(counts, c_new, 1)
+        pos[n:n + take.size] = batch[take]
+        n += take.size
     s = Structure(pos, np.zeros(n_atoms, np.uint8), np.full(3, L))
     return spatial_sort(s) if sort else s
 
