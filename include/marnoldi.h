@@ -273,20 +273,31 @@ int marnoldi_kernel_stats(marnoldi_ctx *ctx, int kind, const char **name, int64_
  *   E_band and N over the members (mu of member 0); marnoldi_level_range and
  *   marnoldi_fermi_at return MARNOLDI_EINVAL.
  *   marnoldi_member_energy(ctx, q, ...): E_band, mu and N(mu) of member q.
+ *   marnoldi_set_member_temperatures(ctx, n, kT[n]): member q's Fermi level,
+ *     density and energy use kT[q] (> 0, finite) instead of the solve's kT;
+ *     n must equal the member count (MARNOLDI_EINVAL otherwise).  kT enters
+ *     only the Fermi step, so members of different temperatures share every
+ *     Krylov launch.  marnoldi_set_members clears the temperatures; this call
+ *     clears the last solve.
  */
 int marnoldi_set_members(marnoldi_ctx *ctx, int n_members, const int64_t *atom_offsets,
                          const double *electron_counts);
 int marnoldi_member_energy(marnoldi_ctx *ctx, int member, double *band_energy, double *mu,
                            double *electron_count_out);
+int marnoldi_set_member_temperatures(marnoldi_ctx *ctx, int n_members, const double *kT);
 
 /*
  * Launch-shape autotuner of the Gram-Schmidt kernel (process-wide).
  *   marnoldi_set_autotune: mode 0 (default, also when MARNOLDI_AUTOTUNE is
  *     unset or not "1") uses a fixed rule: 256 threads per CTA up to m = 4096,
- *     512 for FP32 vectors up to 8192, else 1024, values per thread covering m.
+ *     512 for FP32 vectors up to 8192, the streamed kernel for longer FP32
+ *     vectors (reported as 32 values per thread and 544 threads: 512
+ *     threads and a producer warp that copies the vectors into shared memory
+ *     with the bulk-copy engine), else 1024, values per thread covering m.
  *     Mode 1: the first solve of each (precision, nu, global/regional, padded
  *     vector length) times every shape with the same padded length (threads
- *     256, 512 or 1024) on its first 1,216 columns, keeps the fastest for the
+ *     256, 512 or 1024; for FP32 vectors of 16,384 entries also the
+ *     streamed kernel) on its first 1,216 columns, keeps the fastest for the
  *     rest of the process and, when MARNOLDI_TUNE_CACHE names a file, appends
  *     it there and reads earlier choices from it.  Shapes change the order of
  *     the kernel's partial sums, so results may differ by rounding between
@@ -297,6 +308,19 @@ int marnoldi_member_energy(marnoldi_ctx *ctx, int member, double *band_energy, d
  */
 int marnoldi_set_autotune(int mode);
 int marnoldi_gs_shape(const marnoldi_ctx *ctx, int *values_per_thread, int *threads);
+
+/*
+ * Index checks (debugging).  A library built with -DMARNOLDI_CHECK (the build
+ * script's "check" variant) tests, in its kernels, the indices that come from
+ * data (block lists, tile orders, support counts, output offsets) before
+ * using them; a failed test skips the access and records the first failure of
+ * its source file, and no kernel ever traps.  marnoldi_check_status reports
+ * *compiled = 1 in such a build (0 otherwise, with *site = 0), the first
+ * recorded failure as *site (a CheckSite number, 0 = none) and *index (the
+ * offending index), and clears the records.  It synchronises with the device.
+ * Errors (MARNOLDI_EINVAL, MARNOLDI_ECUDA) through marnoldi_last_error(NULL).
+ */
+int marnoldi_check_status(int *compiled, int *site, int64_t *index);
 
 /*
  * Electron count and band energy at a given mu over subspace levels already in
@@ -312,13 +336,16 @@ int marnoldi_gs_shape(const marnoldi_ctx *ctx, int *values_per_thread, int *thre
  *   cuda_stream           stream to run on (NULL = legacy default stream).
  *
  * Scratch: a fixed 64 KiB device array inside the library (every GPU that
- * loads the library holds it until exit), so ncols*nu is limited to 16,777,216
- * levels; larger inputs return MARNOLDI_EINVAL.  The first call on a device
- * looks up that array's device address; make it before any stream capture.
+ * loads the library holds it until exit), so ncols*nu is limited to
+ * MARNOLDI_COUNT_NOALLOC_MAX_LEVELS = 16,777,216 levels; larger inputs return
+ * MARNOLDI_EINVAL.  Every call looks up that array's device address on the
+ * current device (no allocation); the first call on a device also loads the
+ * library's device code there, so make it before any stream capture.
  * Every call shares the one array: calls that overlap on the GPU (other
  * streams, other threads) race and must be serialised by the caller.
  * Errors are reported through marnoldi_last_error(NULL).
  */
+#define MARNOLDI_COUNT_NOALLOC_MAX_LEVELS 16777216
 int marnoldi_count_noalloc(const double *eps_device, const double *w_device,
                            const int32_t *nu_eff_device, int64_t ncols, int nu, double mu,
                            double kT, double *out_device, void *cuda_stream);

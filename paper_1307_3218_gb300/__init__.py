@@ -10,11 +10,11 @@ columns over ranks with one shared Fermi level (``shard.py``).
 """
 
 from .marnoldi import (MARNOLDI_FP64, MARNOLDI_MIXED, Context, MarnoldiError, Server, load,
-                       marnoldi_column_stats, marnoldi_device_bytes, marnoldi_footprint, marnoldi_gs_shape,
+                       marnoldi_check_status, marnoldi_column_stats, marnoldi_device_bytes, marnoldi_footprint, marnoldi_gs_shape,
                        marnoldi_set_autotune, marnoldi_count_noalloc, marnoldi_density, marnoldi_density_device,
                        marnoldi_destroy, marnoldi_eigenstate, marnoldi_energy, marnoldi_fermi_at, marnoldi_forces,
                        marnoldi_green,
-                       marnoldi_kernel_kinds, marnoldi_level_range, marnoldi_member_energy, marnoldi_set_members,
+                       marnoldi_kernel_kinds, marnoldi_level_range, marnoldi_member_energy, marnoldi_set_member_temperatures, marnoldi_set_members,
                        union_of,
                        marnoldi_kernel_stats, marnoldi_last_error, marnoldi_set_allocator,
                        marnoldi_set_batch, marnoldi_set_profiling, marnoldi_setup,
@@ -22,10 +22,11 @@ from .marnoldi import (MARNOLDI_FP64, MARNOLDI_MIXED, Context, MarnoldiError, Se
 
 __all__ = [
     "MARNOLDI_FP64", "MARNOLDI_MIXED", "Context", "MarnoldiError", "Server", "load",
-    "marnoldi_column_stats", "marnoldi_device_bytes", "marnoldi_footprint", "marnoldi_gs_shape",
+    "marnoldi_check_status", "marnoldi_column_stats", "marnoldi_device_bytes", "marnoldi_footprint", "marnoldi_gs_shape",
     "marnoldi_set_autotune", "marnoldi_count_noalloc", "marnoldi_density", "marnoldi_density_device", "marnoldi_destroy",
     "marnoldi_eigenstate", "marnoldi_energy", "marnoldi_fermi_at", "marnoldi_forces", "marnoldi_green", "marnoldi_kernel_kinds",
-    "marnoldi_kernel_stats", "marnoldi_level_range", "marnoldi_member_energy", "marnoldi_set_members",
+    "marnoldi_kernel_stats", "marnoldi_level_range", "marnoldi_member_energy", "marnoldi_set_member_temperatures",
+    "marnoldi_set_members",
     "union_of",
     "marnoldi_last_error", "marnoldi_set_allocator", "marnoldi_set_batch",
     "marnoldi_set_profiling", "marnoldi_setup", "marnoldi_solve", "marnoldi_solved_shape",

@@ -19,8 +19,8 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 SOURCES = ["api.cu", "krylov.cu", "eigsub.cu", "outputs.cu", "region.cu", "support.cu", "noalloc.cu",
-           "server.cu", "eigstate.cu"]
-HEADERS = [os.path.join(CSRC, "internal.h"), os.path.join(INCLUDE, "marnoldi.h")]
+           "server.cu", "eigstate.cu", "gs_stream.cu"]
+HEADERS = [os.path.join(CSRC, "internal.h"), os.path.join(CSRC, "gs_common.cuh"), os.path.join(INCLUDE, "marnoldi.h")]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
@@ -34,8 +34,14 @@ def nvcc() -> str:
     raise RuntimeError("nvcc not found: the CUDA toolkit is required to build libmarnoldi")
 
 
-def lib_path() -> str:
-    return os.path.join(BUILD, f"libmarnoldi_{platform.machine()}.so")
+def lib_path(variant: str = "") -> str:
+    """The library of the default build, or of a variant ("check": built with
+    -DMARNOLDI_CHECK, index checks in the kernels)."""
+    tag = f"_{variant}" if variant else ""
+    return os.path.join(BUILD, f"libmarnoldi{tag}_{platform.machine()}.so")
+
+
+VARIANTS = {"": [], "check": ["-DMARNOLDI_CHECK"]}
 
 
 def _stale(out: str, deps: list[str]) -> bool:
@@ -45,12 +51,14 @@ def _stale(out: str, deps: list[str]) -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False, extra_flags: list[str] | None = None) -> str:
-    """Compile (if stale) and link libmarnoldi; returns the library path."""
+def build(force: bool = False, verbose: bool = False, extra_flags: list[str] | None = None,
+          variant: str = "") -> str:
+    """Compile (if stale) and link libmarnoldi (or a variant of it, see VARIANTS); returns the
+    library path."""
     os.makedirs(BUILD, exist_ok=True)
     cc = nvcc()
-    flags = FLAGS + list(extra_flags or [])
-    mach = platform.machine()
+    flags = FLAGS + VARIANTS[variant] + list(extra_flags or [])
+    mach = platform.machine() + (f"_{variant}" if variant else "")
     objs = []
     jobs = []
     for src in SOURCES:
@@ -68,7 +76,7 @@ def build(force: bool = False, verbose: bool = False, extra_flags: list[str] | N
                     print(r.stdout + r.stderr)
                 if r.returncode != 0:
                     raise RuntimeError(f"nvcc failed: {' '.join(j)}\n{r.stdout}{r.stderr}")
-    out = lib_path()
+    out = lib_path(variant)
     if force or jobs or _stale(out, objs):
         tmp = out + f".tmp{os.getpid()}"
         r = subprocess.run([cc, *ARCH, "-shared", "-o", tmp, *objs], capture_output=True, text=True)

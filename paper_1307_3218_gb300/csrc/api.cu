@@ -4,6 +4,8 @@
 #include "marnoldi.h"
 #include "internal.h"
 
+#include <nvtx3/nvToolsExt.h>
+
 #include <algorithm>
 #include <iterator>
 #include <cmath>
@@ -141,8 +143,8 @@ void load_tune_cache_locked()
     int v, t;
     while (fscanf(f, "%d %d %d %lld %d %d", &k.prec, &k.nu, &k.regional, &mp, &v, &t) == 6) {
         k.m_pad = mp;
-        ColumnShape cand[3];
-        const int n = column_shape_candidates(k.m_pad, cand);
+        ColumnShape cand[kMaxShapes];
+        const int n = column_shape_candidates(k.m_pad, k.prec, cand);
         for (int q = 0; q < n; ++q)   // only shapes the library is compiled for
             if (cand[q].vpt == v && cand[q].threads == t) g_tuned[k] = cand[q];
     }
@@ -218,6 +220,7 @@ struct marnoldi_ctx {
     // Fermi level, solved in the same launches
     std::vector<int64_t> mem_atom;   // n + 1 atom offsets (empty: one structure)
     std::vector<double> mem_ne;
+    std::vector<double> mem_kT;   // per-member kT (empty: the solve's kT for every member)
     std::vector<int64_t> mem_col;    // n + 1 offsets into the solved columns
     std::vector<double> mem_mu, mem_N, mem_E;
 
@@ -319,6 +322,16 @@ cudaEvent_t get_event(marnoldi_ctx *c)
     cudaEventCreate(&e);
     return e;
 }
+
+// NVTX range over one phase of a call (host timeline: when its launches are
+// issued and, for the phases that end in a synchronisation, until they end).
+// A profiler shows them; without one the calls cost next to nothing.
+struct Phase {
+    explicit Phase(const char *name) { nvtxRangePushA(name); }
+    ~Phase() { nvtxRangePop(); }
+    Phase(const Phase &) = delete;
+    Phase &operator=(const Phase &) = delete;
+};
 
 void collect_profile(marnoldi_ctx *c)
 {
@@ -1012,6 +1025,7 @@ int marnoldi_set_members(marnoldi_ctx *c, int n_members, const int64_t *atom_off
     c->solved = false;
     c->mem_atom.clear();
     c->mem_ne.clear();
+    c->mem_kT.clear();
     c->mem_col.clear();
     if (n_members == 0) return MARNOLDI_OK;
     if (n_members < 0 || !atom_offsets || !electron_counts)
@@ -1037,6 +1051,21 @@ int marnoldi_set_members(marnoldi_ctx *c, int n_members, const int64_t *atom_off
     return MARNOLDI_OK;
 }
 
+int marnoldi_set_member_temperatures(marnoldi_ctx *c, int n_members, const double *kT)
+{
+    if (!c) return MARNOLDI_EINVAL;
+    c->err.clear();
+    c->solved = false;
+    if (c->mem_atom.empty() || n_members != (int)c->mem_atom.size() - 1 || !kT)
+        return fail(c, MARNOLDI_EINVAL, "temperatures need the context's %d members",
+                    c->mem_atom.empty() ? 0 : (int)c->mem_atom.size() - 1);
+    for (int q = 0; q < n_members; ++q)
+        if (!(kT[q] > 0.0) || !std::isfinite(kT[q]))
+            return fail(c, MARNOLDI_EINVAL, "member %d: kT must be positive and finite", q);
+    c->mem_kT.assign(kT, kT + n_members);
+    return MARNOLDI_OK;
+}
+
 int marnoldi_member_energy(marnoldi_ctx *c, int member, double *band_energy, double *mu,
                            double *electron_count_out)
 {
@@ -1055,6 +1084,30 @@ int marnoldi_set_autotune(int mode)
     if (mode != 0 && mode != 1) return MARNOLDI_EINVAL;
     std::lock_guard<std::mutex> lock(g_tune_mu);
     g_autotune = mode;
+    return MARNOLDI_OK;
+}
+
+int marnoldi_check_status(int *compiled, int *site, int64_t *index)
+{
+    if (!compiled || !site || !index) return set_global_error(MARNOLDI_EINVAL, "check_status: NULL output");
+    *compiled = kCheckBuild ? 1 : 0;
+    *site = 0;
+    *index = 0;
+    cudaError_t (*take[])(unsigned long long *) = {check_take_krylov, check_take_region, check_take_outputs,
+                                                   check_take_gs_stream};
+    for (auto f : take) {
+        unsigned long long w = 0;
+        const cudaError_t e = f(&w);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return set_global_error(MARNOLDI_ECUDA, "check_status: reading the check words failed");
+        }
+        if (w && *site == 0) {
+            *site = (int)((w >> 40) & 0x7fff);
+            const unsigned long long lo = w & 0xffffffffffull;
+            *index = (lo & (1ull << 39)) ? (int64_t)(lo | ~0xffffffffffull) : (int64_t)lo;
+        }
+    }
     return MARNOLDI_OK;
 }
 
@@ -1093,6 +1146,7 @@ int marnoldi_solve(marnoldi_ctx *c, const int64_t *columns, int64_t ncols, int n
                    int region_atoms, double electron_count, double kT, const double *mu_fixed)
 {
     if (!c) return MARNOLDI_EINVAL;
+    const Phase phase("marnoldi_solve");
     c->err.clear();
     c->solved = false;   // a failed solve leaves no stale results
     const bool regional = region_atoms > 0;
@@ -1337,6 +1391,7 @@ int marnoldi_solve(marnoldi_ctx *c, const int64_t *columns, int64_t ncols, int n
             const int64_t bi = start / B;
             c->rm.gstart = (const int *)(sb + plan.o_grp) + gofs[bi];
             c->rm.ngroups = (int)(gofs[bi + 1] - gofs[bi] - 1);
+            const Phase ph("region");
             if ((rc = find_regions(c, kb))) return rc;
             if ((rc = launch(c, KK_REGION, [&] { return launch_local_bsr(c->A, c->rm, kb, c->stream); })))
                 return rc;
@@ -1350,8 +1405,8 @@ int marnoldi_solve(marnoldi_ctx *c, const int64_t *columns, int64_t ncols, int n
             if (it != g_tuned.end()) {
                 kb.shape = it->second;
             } else {
-                ColumnShape cand[3];
-                const int ncand = column_shape_candidates(mp, cand);
+                ColumnShape cand[kMaxShapes];
+                const int ncand = column_shape_candidates(mp, c->prec, cand);
                 KrylovBatch ks = kb;
                 ks.nb = (int)std::min<int64_t>(kb.nb, kTuneColumns);
                 float best = 0.f;
@@ -1384,7 +1439,10 @@ int marnoldi_solve(marnoldi_ctx *c, const int64_t *columns, int64_t ncols, int n
             }
             tune = false;
         }
-        if ((rc = build(kb))) return rc;
+        {
+            const Phase ph("krylov");   // support search, initial vectors, nu steps of SpMM + Gram-Schmidt
+            if ((rc = build(kb))) return rc;
+        }
         if (c->proj_vec) {
             if ((rc = launch(c, KK_EIGSTATE, [&] {
                      return launch_project(kb, c->proj_vec, c->m, proj_buf.get(), c->stream);
@@ -1393,6 +1451,7 @@ int marnoldi_solve(marnoldi_ctx *c, const int64_t *columns, int64_t ncols, int n
             es.proj = proj_buf.get();
             es.proj_out = c->proj_out;
         }
+        const Phase ph("eigensolve");
         if ((rc = launch(c, KK_EIG, [&] { return launch_eig(c->A, kb, c->st, start, rmp, es, c->stream); })))
             return rc;
     }
@@ -1401,6 +1460,7 @@ int marnoldi_solve(marnoldi_ctx *c, const int64_t *columns, int64_t ncols, int n
     c->last_regional = regional;
     c->last_all_real = columns == nullptr;
     // ---- Fermi level
+    const Phase ph_fermi("fermi");
     double mu = 0.0, N = 0.0, E = 0.0;
     if (mu_fixed) {
         mu = *mu_fixed;
@@ -1421,11 +1481,12 @@ int marnoldi_solve(marnoldi_ctx *c, const int64_t *columns, int64_t ncols, int n
         std::vector<double> mmu(nmem), mN(nmem), mE(nmem);
         for (size_t m = 0; m < nmem; ++m) {
             const double ne = members ? c->mem_ne[m] : electron_count;
+            const double mkT = members && !c->mem_kT.empty() ? c->mem_kT[m] : kT;
             const ColumnState sub = column_view(c->st, col0[m], col0[m + 1]);
             if (sub.ncols == 0)
                 return fail(c, MARNOLDI_EINVAL, "member %zu has no real orbitals", m);
             if ((rc = launch(c, KK_COUNT, [&] {
-                     return launch_bisection(sub, kT, ne, c->d_partial, c->d_ticket, c->d_range, c->d_out,
+                     return launch_bisection(sub, mkT, ne, c->d_partial, c->d_ticket, c->d_range, c->d_out,
                                              c->d_bisect, c->stream);
                  })))
                 return rc;
@@ -1470,6 +1531,9 @@ int marnoldi_solve(marnoldi_ctx *c, const int64_t *columns, int64_t ncols, int n
     c->kT = kT;
     c->solved = true;
     for (int64_t q = 0; q < nc; ++q) {
+        if (est[q] & 4)
+            return fail(c, MARNOLDI_ETIMEOUT, "column %lld: a bounded wait of the Gram-Schmidt kernel gave up",
+                        (long long)c->cols[q]);
         if (est[q] & 2)
             return fail(c, MARNOLDI_ENOTSPD, "column %lld: a Krylov vector has non-positive S norm", (long long)c->cols[q]);
         if (est[q] & 1)
@@ -1480,6 +1544,7 @@ int marnoldi_solve(marnoldi_ctx *c, const int64_t *columns, int64_t ncols, int n
 
 int marnoldi_density_device(marnoldi_ctx *c, double *rho, double *rhoE)
 {
+    const Phase phase("density");
     if (!c || !rho || !rhoE) return MARNOLDI_EINVAL;
     if (!c->solved) return fail(c, MARNOLDI_ESTATE, "density requested before a successful solve");
     const size_t bytes = (size_t)c->nnzb * 16 * sizeof(double);
@@ -1493,7 +1558,8 @@ int marnoldi_density_device(marnoldi_ctx *c, double *rho, double *rhoE)
     for (size_t m = 0; m + 1 < c->mem_col.size(); ++m) {   // each member at its own Fermi level
         const ColumnState sub = column_view(c->st, c->mem_col[m], c->mem_col[m + 1]);
         const int rc = launch(c, KK_DENSITY, [&] {
-            return launch_density(c->A, sub, c->mem_mu[m], c->kT, rho, rhoE, c->stream);
+            return launch_density(c->A, sub, c->mem_mu[m], c->mem_kT.empty() ? c->kT : c->mem_kT[m], rho, rhoE,
+                                  c->stream);
         });
         if (rc) return rc;
     }
@@ -1565,6 +1631,7 @@ int marnoldi_fermi_at(marnoldi_ctx *c, double mu, double kT, double *N, double *
 
 int marnoldi_green(marnoldi_ctx *c, const double *z, int nz, double *G)
 {
+    const Phase phase("green");
     if (!c || (nz > 0 && (!z || !G)) || nz < 0) return MARNOLDI_EINVAL;
     if (!c->solved) return fail(c, MARNOLDI_ESTATE, "green requested before a successful solve");
     const size_t per = (size_t)c->nnzb * 16 * 2;
@@ -1592,6 +1659,7 @@ int marnoldi_green(marnoldi_ctx *c, const double *z, int nz, double *G)
 
 int marnoldi_forces(marnoldi_ctx *c, const double *dH, const double *dS, double *F)
 {
+    const Phase phase("forces");
     if (!c || !dH || !dS || !F) return MARNOLDI_EINVAL;
     if (!c->solved) return fail(c, MARNOLDI_ESTATE, "forces requested before a successful solve");
     const size_t vals = (size_t)c->nnzb * 16, bytes = (size_t)(2 + 6) * vals * sizeof(double) +
@@ -1622,6 +1690,7 @@ int marnoldi_eigenstate(marnoldi_ctx *c, int64_t k, double sigma, double *eps_k,
                         double *eta_bounds)
 {
     if (!c || !eps_k || !phi) return MARNOLDI_EINVAL;
+    const Phase phase("eigenstate");
     if (!c->solved) return fail(c, MARNOLDI_ESTATE, "eigenstate requested before a successful solve");
     if (!c->mem_atom.empty() || c->last_regional || !c->last_all_real)
         return fail(c, MARNOLDI_EINVAL, "the eigenstate needs a global-mode solve of every real orbital "

@@ -417,7 +417,7 @@ __global__ void __launch_bounds__(kApplyThreads) eig_apply_kernel(
     }
     if (tid == 0) {
         nu_eff_out[g] = n;
-        eig_status[g] = (nsw < 0 ? 1 : 0) | (bstatus[c] == 2 ? 2 : 0);
+        eig_status[g] = (nsw < 0 ? 1 : 0) | (bstatus[c] == 2 ? 2 : 0) | (bstatus[c] == 3 ? 4 : 0);
     }
 }
 

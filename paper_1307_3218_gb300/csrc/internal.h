@@ -75,9 +75,15 @@ struct ColumnShape {
     int64_t m_pad;
 };
 ColumnShape column_shape(int64_t m, int prec);
-// Every shape the Gram-Schmidt kernel is built for with the same m_pad
-// (threads 256, 512 or 1024; at most 3); returns how many were written.
-int column_shape_candidates(int64_t m_pad, ColumnShape *out);
+// Every shape the Gram-Schmidt kernels are built for with the same m_pad and
+// precision (threads 256, 512 or 1024; at most kMaxShapes); returns how many
+// were written.
+constexpr int kMaxShapes = 4;
+int column_shape_candidates(int64_t m_pad, int prec, ColumnShape *out);
+// The shape of the streamed Gram-Schmidt kernel (gs_stream.cu): FP32
+// vectors of m_pad = 16,384, 512 consumer threads of 32 values and a
+// producer warp: {vpt 32, threads 544}.
+bool gs_stream_shape(const ColumnShape &s, int prec);
 
 // ---------------------------------------------------------------- Krylov build
 // All pointers are device pointers.  Batch layout (c = batch column):
@@ -86,7 +92,8 @@ int column_shape_candidates(int64_t m_pad, ColumnShape *out);
 //     k_i = scale[c][i] * w_i (scale = 1 / ||w_i||_S, set by the MGS of step i)
 //   U[c][r] at c * m_pad + r: H w_n of the current step
 //   Hsub[c][i][l] at (c * nu + i) * nu + l (double)
-// status[c]: 0 active, 1 stopped (breakdown), 2 non-positive S norm.
+// status[c]: 0 active, 1 stopped (breakdown), 2 non-positive S norm, 3 a bounded
+// wait of the streamed Gram-Schmidt kernel gave up.
 struct KrylovBatch {
     int prec;             // 0 FP64, 1 mixed (vectors float)
     int nb;               // columns in this batch
@@ -119,6 +126,59 @@ struct KrylovBatch {
     uint16_t *tinv = nullptr;
     int *tcnt = nullptr;
 };
+
+// ---------------------------------------------------------------- index checks
+// Built with -DMARNOLDI_CHECK, kernels test the indices they take from data
+// (block lists, tile orders, support counts, output offsets) before using
+// them.  A failed test records the first failure of its translation unit
+// (the check site and the index) in a device word and the access is skipped:
+// nothing traps.  marnoldi_check_status reads and clears the words.  Without
+// the flag every test is the constant true and compiles away.
+enum CheckSite : int {
+    kChkSpmmGather = 1,   // krylov.cu: position of a gathered 4-vector in a column's vector
+    kChkInitPos,          // krylov.cu: position of an entry of S e_j
+    kChkRegionCol,        // region.cu: local column of a local block
+    kChkRegionGather,     // region.cu: position of a gathered 4-vector
+    kChkDensityOut,       // outputs.cu: density entry of a pattern row
+    kChkSupportCount,     // krylov.cu, gs_stream.cu: tiles of a support (at most m_pad / 32)
+};
+#ifdef MARNOLDI_CHECK
+constexpr bool kCheckBuild = true;
+namespace {
+__device__ unsigned long long g_check_word;   // one per translation unit
+__device__ __forceinline__ bool in_range(int64_t i, int64_t n, int site)
+{
+    if (i >= 0 && i < n) return true;
+    atomicCAS(&g_check_word, 0ull,
+              (1ull << 63) | ((unsigned long long)(site & 0x7fff) << 40) | ((unsigned long long)i & 0xffffffffffull));
+    return false;
+}
+}  // namespace
+// Defines check_take_<name>: read this translation unit's word and clear it.
+#define MARNOLDI_CHECK_TAKE(name)                                                       \
+    cudaError_t check_take_##name(unsigned long long *w)                                \
+    {                                                                                   \
+        cudaError_t e = cudaMemcpyFromSymbol(w, g_check_word, sizeof(*w));             \
+        if (e == cudaSuccess && *w) {                                                   \
+            const unsigned long long z = 0;                                             \
+            e = cudaMemcpyToSymbol(g_check_word, &z, sizeof(z));                        \
+        }                                                                               \
+        return e;                                                                       \
+    }
+#else
+constexpr bool kCheckBuild = false;
+__device__ __forceinline__ constexpr bool in_range(int64_t, int64_t, int) { return true; }
+#define MARNOLDI_CHECK_TAKE(name)                            \
+    cudaError_t check_take_##name(unsigned long long *w)     \
+    {                                                        \
+        *w = 0;                                              \
+        return cudaSuccess;                                  \
+    }
+#endif
+cudaError_t check_take_krylov(unsigned long long *w);
+cudaError_t check_take_region(unsigned long long *w);
+cudaError_t check_take_outputs(unsigned long long *w);
+cudaError_t check_take_gs_stream(unsigned long long *w);
 
 // Four consecutive values (16-byte aligned for float, 32 for double) in one or
 // two vector loads (read-only path) or stores.
@@ -224,6 +284,7 @@ cudaError_t launch_support(const DeviceMatrix &A, const RegionMaps *rm, const Kr
 cudaError_t launch_spmm_hs(const DeviceMatrix &A, const KrylovBatch &b, const void *X, int64_t ldx,
                            void *SY, int64_t ldsy, int lim, cudaStream_t s);
 cudaError_t launch_gs(const KrylovBatch &b, int n, int need_w, double tau, cudaStream_t s);
+cudaError_t launch_gs_stream(const KrylovBatch &b, int n, int need_w, double tau, cudaStream_t s);
 
 // ---------------------------------------------------------------- subspace eigensolve
 // Per solved column c (global index col0 + batch column):
@@ -235,7 +296,7 @@ struct ColumnState {
     int *nu_eff;
     double *eps, *w, *t, *P;
     const int64_t *p_off;
-    int *eig_status;     // 0 ok, 1 QL did not converge
+    int *eig_status;     // bits: 1 QL did not converge, 2 non-positive S norm, 4 a wait gave up
 };
 
 // Scratch of the three-kernel eigensolve, per chunk of subspaces:

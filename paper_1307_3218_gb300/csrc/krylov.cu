@@ -21,7 +21,7 @@
 // in mixed precision the vectors, the SpMM and the Gram-Schmidt updates are
 // FP32.  Reductions use a fixed order (warp butterflies, then one warp over
 // the warps), so results do not depend on scheduling.
-#include "internal.h"
+#include "gs_common.cuh"
 
 #include <cstdio>
 
@@ -37,104 +37,32 @@ const char *kernel_name(int kind)
 
 // Vectors up to 4096 entries run 256-thread CTAs (several columns share an SM
 // and overlap each other's reductions).  Longer FP32 vectors up to 8192
-// entries run 512-thread CTAs of 16 values per thread (two per SM); the rest
-// run 1024-thread CTAs.  VPT is the power of two that covers m.
+// entries run 512-thread CTAs of 16 values per thread (two per SM); longer
+// FP32 vectors run the streamed kernel (gs_stream.cu: 512 consumer threads of
+// 32 values and a producer warp, shape {32, 544}); the rest run 1024-thread
+// CTAs.  VPT is the power of two that covers m.
 ColumnShape column_shape(int64_t m, int prec)
 {
     if (prec == 1 && m > 4096 && m <= 8192) return ColumnShape{16, 512, 8192};
+    if (prec == 1 && m > 8192 && m <= 16384) return ColumnShape{32, 544, 16384};   // gs_stream.cu
     const int T = m <= 4096 ? 256 : 1024;
     int v = 1;
     while (v < 16 && (int64_t)v * T < m) v *= 2;
     return ColumnShape{v, T, (int64_t)v * T};
 }
 
-int column_shape_candidates(int64_t m_pad, ColumnShape *out)
+int column_shape_candidates(int64_t m_pad, int prec, ColumnShape *out)
 {
     int n = 0;
     for (int T : {256, 512, 1024})
         for (int v = 1; v <= 16; v *= 2)
             if ((int64_t)v * T == m_pad) out[n++] = ColumnShape{v, T, m_pad};
+    const ColumnShape st{32, 544, 16384};
+    if (m_pad == st.m_pad && gs_stream_shape(st, prec)) out[n++] = st;
     return n;
 }
 
 namespace {
-
-constexpr unsigned kFull = 0xffffffffu;
-
-// ------------------------------------------------------------------ dot accumulators
-// Per-thread partial inner products.  FP64 vectors: fused multiply-adds in
-// FP64.  FP32 vectors (mixed precision): the product a*b of two floats is
-// split exactly into p + e (p = fl(a*b), e = fma(a, b, -p)) and p is added to
-// the running sum with an exact two-sum, so the pair (hi, lo) carries the sum
-// to about 2^-48 relative.  The reduction across the CTA stays in such pairs
-// and only the CTA total is converted to FP64, so the inner products are
-// FP64-accurate on FP32 data with no per-element FP64 work (GB300 issues
-// FP32 at about 64 times its FP64 rate).  The _rn intrinsics keep the
-// compiler from contracting the error-free steps into FMAs.
-__device__ __forceinline__ void df_add(float &hi, float &lo, float h2, float l2)
-{
-    const float s = __fadd_rn(hi, h2);
-    const float bb = __fsub_rn(s, hi);
-    const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(h2, bb));
-    hi = s;
-    lo = __fadd_rn(lo, __fadd_rn(l2, err));
-}
-
-template <typename VT> struct DotAcc;
-template <> struct DotAcc<double> {
-    double s = 0.0;
-    __device__ __forceinline__ void add(double a, double b) { s = fma(a, b, s); }
-    __device__ __forceinline__ double value() const { return s; }
-    __device__ __forceinline__ void merge(const DotAcc &o) { s += o.s; }
-    __device__ __forceinline__ DotAcc shfl_xor(int o) const
-    {
-        DotAcc r;
-        r.s = __shfl_xor_sync(kFull, s, o);
-        return r;
-    }
-    __device__ __forceinline__ double pack() const { return s; }
-    __device__ __forceinline__ void unpack(double p) { s = p; }
-    __device__ __forceinline__ void set(double x) { s = x; }
-};
-template <> struct DotAcc<float> {
-    float hi = 0.f, lo = 0.f;
-    __device__ __forceinline__ void add(float a, float b)
-    {
-        const float p = __fmul_rn(a, b);
-        const float e = __fmaf_rn(a, b, -p);
-        df_add(hi, lo, p, e);
-    }
-    __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
-    // fold in a correction of about 2^-24 relative to the sum
-    __device__ __forceinline__ void add_lo(float x) { lo = __fadd_rn(lo, x); }
-    __device__ __forceinline__ void merge(const DotAcc &o) { df_add(hi, lo, o.hi, o.lo); }
-    __device__ __forceinline__ DotAcc shfl_xor(int o) const
-    {
-        DotAcc r;
-        r.hi = __shfl_xor_sync(kFull, hi, o);
-        r.lo = __shfl_xor_sync(kFull, lo, o);
-        return r;
-    }
-    __device__ __forceinline__ double pack() const
-    {
-        union { float2 f; double d; } u;
-        u.f = make_float2(hi, lo);
-        return u.d;
-    }
-    __device__ __forceinline__ void unpack(double p)
-    {
-        union { float2 f; double d; } u;
-        u.d = p;
-        hi = u.f.x;
-        lo = u.f.y;
-    }
-    __device__ __forceinline__ void set(float x)
-    {
-        hi = x;
-        lo = 0.f;
-    }
-};
-
 
 // ------------------------------------------------------------------ init
 // k_1 = e_j / sqrt(S_jj); S k_1 = (column j of S) / sqrt(S_jj), read from block
@@ -169,7 +97,10 @@ __global__ void init_kernel(const int64_t *__restrict__ rp, const int32_t *__res
     for (int64_t k = rp[J] + threadIdx.x; k < rp[J + 1]; k += blockDim.x) {
         const int64_t I = ci[k];
 #pragma unroll
-        for (int a = 0; a < 4; ++a) sk0[vpos(tinv, nb, c, 4 * I + a)] = (VT)(Sv[16 * k + 4 * b + a] * inv);
+        for (int a = 0; a < 4; ++a) {
+            const int64_t q = vpos(tinv, nb, c, 4 * I + a);
+            if (in_range(q, m_pad, kChkInitPos)) sk0[q] = (VT)(Sv[16 * k + 4 * b + a] * inv);
+        }
     }
 }
 
@@ -252,8 +183,14 @@ __global__ void __launch_bounds__(256) spmm_hs_kernel(
         for (int64_t k = rp[I]; k < k1; ++k) {
             const int64_t J = ci[k];
             VT xv[2][4] = {{VT(0), VT(0), VT(0), VT(0)}, {VT(0), VT(0), VT(0), VT(0)}};
-            if (L[0].act) load4(x0 + 4 * apos(tinv, ncols, cc[0], J), xv[0]);
-            if (L[1].act) load4(x1 + 4 * apos(tinv, ncols, cc[1], J), xv[1]);
+            if (L[0].act) {
+                const int64_t xp = 4 * apos(tinv, ncols, cc[0], J);
+                if (in_range(xp, ldu - 3, kChkSpmmGather)) load4(x0 + xp, xv[0]);
+            }
+            if (L[1].act) {
+                const int64_t xp = 4 * apos(tinv, ncols, cc[1], J);
+                if (in_range(xp, ldu - 3, kChkSpmmGather)) load4(x1 + xp, xv[1]);
+            }
             const VT *Hb = Hv + BS * k;
             const VT *Sb = Sv + BS * k;
 #pragma unroll
@@ -342,8 +279,6 @@ __global__ void __launch_bounds__(256) spmm_hs_kernel(
 // anyway, which G records.  The coefficients and G are FP64.
 // u (and its lo word) and w sit in shared memory (or registers for small
 // VPT); w holds w_n during the coefficient sweep and w_{n+1} afterwards.
-constexpr int kGsBlock = 4;
-
 template <typename VT, int VPT, int T>
 struct GsCfg {
     static constexpr bool kLo = sizeof(VT) == 4;                    // u as (hi, lo) pair
@@ -353,98 +288,6 @@ struct GsCfg {
     static constexpr int kChunkUpd = sizeof(VT) == 8 ? 1 : 4;
     static constexpr int kSmemVectors = (kUs ? 1 : 0) + (kLo ? 1 : 0) + (kWs ? 1 : 0);
 };
-
-// Live values of warp `warp` when the first cnt tile positions are live.
-template <int T>
-__device__ __forceinline__ int live_values(int cnt, int warp)
-{
-    constexpr int NW = T / 32;
-    return cnt > warp ? (cnt - warp + NW - 1) / NW : 0;
-}
-
-// f(v, live) over the thread's first nv values, chunk by chunk; a compiler
-// barrier between chunks keeps one chunk's loads live at a time, and only the
-// last live chunk tests its values.
-template <int VPT, int kChunk, typename F>
-__device__ __forceinline__ void for_live(int nv, F &&f)
-{
-#pragma unroll
-    for (int v0 = 0; v0 < VPT; v0 += kChunk) {
-        if (v0 >= nv) break;
-        if (v0 + kChunk <= nv) {
-#pragma unroll
-            for (int q = 0; q < kChunk && v0 + q < VPT; ++q) f(v0 + q, true);
-        } else {
-#pragma unroll
-            for (int q = 0; q < kChunk && v0 + q < VPT; ++q) f(v0 + q, v0 + q < nv);
-        }
-        if (v0 + kChunk < VPT) asm volatile("" ::: "memory");
-    }
-}
-
-// Barrier of a group of the CTA's threads: 0 = the whole CTA, else the named
-// barrier `bar` over `nthreads` threads (whole warps).
-__device__ __forceinline__ void group_sync(int bar, int nthreads)
-{
-    if (bar == 0) __syncthreads();
-    else asm volatile("bar.sync %0, %1;" ::"r"(bar), "r"(nthreads) : "memory");
-}
-
-// Sum of N <= 16 per-thread accumulators over a group of warps (the CTA, or
-// one of its halves) in a fixed order.  In each warp a reduce-scatter
-// butterfly over NP = 2^ceil(log2 N) slots leaves slot q on lanes
-// q (32 / NP) .. (q + 1) (32 / NP) - 1 (each lane sends half of its slots per
-// round, so N values cost about as many shuffles as two); then warp w of the
-// group sums values w, w + gnw, ... over its warps and its lane 0 runs
-// epi(q, total).  `buf` alternates the partial slots (part holds
-// 2 x 16 x stride doubles, stride >= gnw) so that two barriers per reduction
-// suffice; `bar` selects the group's barrier (0: the CTA's).
-template <typename VT, int N, typename Epi>
-__device__ __forceinline__ void block_sum(const DotAcc<VT> (&in)[N], double *part, int &buf, Epi epi,
-                                          int gwarp, int gnw, int stride, int bar)
-{
-    static_assert(N >= 1 && N <= 16, "1 <= N <= 16");
-    constexpr int LOGN = N > 8 ? 4 : N > 4 ? 3 : N > 2 ? 2 : N > 1 ? 1 : 0;
-    constexpr int NP = 1 << LOGN;
-    const int lane = threadIdx.x & 31;
-    DotAcc<VT> a[NP];
-#pragma unroll
-    for (int q = 0; q < N; ++q) a[q] = in[q];
-#pragma unroll
-    for (int r = 0; r < LOGN; ++r) {
-        const int o = 16 >> r, half = NP >> (r + 1);
-        const bool up = (lane & o) != 0;
-#pragma unroll
-        for (int j = 0; j < half; ++j) {
-            DotAcc<VT> keep = up ? a[j + half] : a[j];
-            const DotAcc<VT> send = up ? a[j] : a[j + half];
-            keep.merge(send.shfl_xor(o));
-            a[j] = keep;
-        }
-    }
-#pragma unroll
-    for (int o = 16 >> LOGN; o > 0; o >>= 1) a[0].merge(a[0].shfl_xor(o));
-    const int qm = lane >> (5 - LOGN);
-    if ((lane & ((32 >> LOGN) - 1)) == 0 && qm < N) part[(buf * 16 + qm) * stride + gwarp] = a[0].pack();
-    group_sync(bar, gnw * 32);
-    for (int q = gwarp; q < N; q += gnw) {
-        DotAcc<VT> x;
-        if (lane < gnw) x.unpack(part[(buf * 16 + q) * stride + lane]);
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) x.merge(x.shfl_xor(o));
-        if (lane == 0) epi(q, x.value());
-    }
-    group_sync(bar, gnw * 32);
-    buf ^= 1;
-}
-
-// sum over the warp of x (every lane holds the total)
-__device__ __forceinline__ double warp_total(double x)
-{
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(kFull, x, o);
-    return x;
-}
 
 template <typename VT, int VPT, int T>
 __global__ void __launch_bounds__(T, T == 256 ? 4 : T == 512 ? 2 : 1) gs_kernel(
@@ -475,12 +318,14 @@ __global__ void __launch_bounds__(T, T == 256 ? 4 : T == 512 ? 2 : 1) gs_kernel(
     __shared__ int bc_stop;
     __shared__ double bc_dinv;
     const int64_t base = (int64_t)c * nu * MP;
-    double *Lc = Lsub + (int64_t)c * nu * nu;   // L^-1, row-major, lower triangle
     int buf = 0;
     auto live = [&](int cnt) { return live_values<T>(cnt, warp); };
 
     for (int i = tid; i < n; i += T) ssc[i] = scale[(int64_t)c * nu + i];
-    for (int L = tid; L <= n + 1; L += T) cnt_s[L] = tcnt[(int64_t)c * (nu + 2) + L];
+    for (int L = tid; L <= n + 1; L += T) {
+        const int t = tcnt[(int64_t)c * (nu + 2) + L];
+        cnt_s[L] = in_range(t, MP / 32 + 1, kChkSupportCount) ? t : (int)(MP / 32);
+    }
     __syncthreads();
 
     // u (hi, lo) and w_n on chip; zeros past their supports
@@ -577,104 +422,12 @@ __global__ void __launch_bounds__(T, T == 256 ? 4 : T == 512 ? 2 : 1) gs_kernel(
     // ---- scalars, G's column, the new row of L^-1, the coefficients (FP64).
     // Lc holds L^-1 (lower triangular), so every product below is a matrix-
     // vector product, one warp per row or column, with no serial chain.
-    if (tid == 0) {
-        double sn = 1.0;   // slot 0 is stored normalised (G_00 = 1)
-        int stop = 0;
-        if (n > 0) {
-            const double beta2 = tg[n];
-            if (!(beta2 > 0.0) || beta2 <= tau2 * (beta2 + cn2[c])) {
-                stop = 1;
-                // a square norm below zero by no more than the threshold times the
-                // projected part is rounding at breakdown (FP32 vectors near linear
-                // dependence); further below, or NaN, it is not a norm (2)
-                status[c] = (beta2 >= -sqrt(tau2) * cn2[c]) ? 1 : 2;
-                nu_eff[c] = n;
-            } else {
-                sn = 1.0 / sqrt(beta2);
-                scale[(int64_t)c * nu + n] = sn;
-            }
-        }
-        ssc[n] = sn;
-        bc_stop = stop;
+    {
+        const GsScalarSmem<VT> sm{ssc, ta, tb, tg, lrow, nrow, zc, coef, bc_stop, bc_dinv};
+        if (!gs_scalars<VT, T>(c, n, nu, need_w, tau2, tid, Hsub, Lsub, scale, cn2, status, nu_eff, sm,
+                               [] { __syncthreads(); }))
+            return;
     }
-    __syncthreads();
-    if (bc_stop) return;
-    const double sn = ssc[n];
-    for (int m = tid; m <= n; m += T) {   // G_{mn}, p_m (of s_n u) and h_m of unit-norm vectors
-        const double f = ssc[m] * sn;
-        tg[m] *= f;
-        tb[m] *= f;
-        const double h = ta[m] * f;
-        Hsub[((int64_t)c * nu + m) * nu + n] = h;
-        Hsub[((int64_t)c * nu + n) * nu + m] = h;
-    }
-    __syncthreads();
-    constexpr int NW = T / 32;
-    // l = L^-1 G_{<n, n}
-    for (int r = warp; r < n; r += NW) {
-        double x = 0.0;
-        for (int m = lane; m <= r; m += 32) x = fma(Lc[(int64_t)r * nu + m], tg[m], x);
-        x = warp_total(x);
-        if (lane == 0) lrow[r] = x;
-    }
-    __syncthreads();
-    // d = sqrt(G_nn - |l|^2), G_nn = 1; the new row of L^-1 is (-l^T L^-1, 1) / d
-    if (warp == 0) {
-        double x = 0.0;
-        for (int r = lane; r < n; r += 32) x = fma(lrow[r], lrow[r], x);
-        x = warp_total(x);
-        if (lane == 0) {
-            const double dd = 1.0 - x;
-            if (!(dd > 0.0)) {   // the stored basis has lost its rank
-                bc_stop = 1;
-                status[c] = 1;
-                nu_eff[c] = n;
-            } else {
-                bc_dinv = 1.0 / sqrt(dd);
-            }
-        }
-    }
-    __syncthreads();
-    if (bc_stop) return;
-    const double dinv = bc_dinv;
-    double *Ln = Lc + (int64_t)n * nu;
-    for (int m = warp; m < n; m += NW) {
-        double x = 0.0;
-        for (int r = m + lane; r < n; r += 32) x = fma(lrow[r], Lc[(int64_t)r * nu + m], x);
-        x = warp_total(x);
-        if (lane == 0) {
-            nrow[m] = -dinv * x;
-            Ln[m] = -dinv * x;
-        }
-    }
-    if (tid == 0) {
-        nrow[n] = dinv;
-        Ln[n] = dinv;
-    }
-    __syncthreads();
-    if (!need_w) return;
-    // z = L^-1 p, |z|^2 = |projection of s_n u|_S^2, c = L^-T z
-    for (int r = warp; r <= n; r += NW) {
-        const double *Lr = r == n ? nrow : Lc + (int64_t)r * nu;
-        double x = 0.0;
-        for (int m = lane; m <= r; m += 32) x = fma(Lr[m], tb[m], x);
-        x = warp_total(x);
-        if (lane == 0) zc[r] = x;
-    }
-    __syncthreads();
-    for (int m = warp; m <= n; m += NW) {
-        double x = 0.0;
-        for (int r = m + lane; r <= n; r += 32) x = fma(r == n ? nrow[m] : Lc[(int64_t)r * nu + m], zc[r], x);
-        x = warp_total(x);
-        if (lane == 0) coef[m] = (VT)(x * ssc[m]);
-    }
-    if (warp == 0) {
-        double x = 0.0;
-        for (int r = lane; r <= n; r += 32) x = fma(zc[r], zc[r], x);
-        x = warp_total(x);
-        if (lane == 0) cn2[c] = x;
-    }
-    __syncthreads();
 
     // ---- w_{n+1} = s_n u - sum_i coef_i w_i: streaming subtraction, last block
     // first (its vectors are the ones the sweep read last; its support is u's)
@@ -691,24 +444,53 @@ __global__ void __launch_bounds__(T, T == 256 ? 4 : T == 512 ? 2 : 1) gs_kernel(
 #pragma unroll
         for (int l = 0; l < kB; ++l) co[l] = l < nbk ? coef[i0 + l] : VT(0);
         for_live<VPT, Cfg::kChunkUpd>(nvs, [&](int v, bool a) {
-            VT x;
-            if (first) {
-                VT uu;
-                if constexpr (kUs) uu = us[tid + v * T]; else uu = a ? u[v * T] : VT(0);
-                x = uu * vsn;
-            } else {
-                x = wget(v);
-            }
+            if constexpr (kLo) {
+                // FP32 vectors: the sum runs as a (hi, lo) pair (hi in w's
+                // place, lo in u's lo word, which is no longer needed), with
+                // exact products and two-sums, and is rounded to FP32 once
+                // at the end: s_n u and the projection nearly cancel, so a
+                // plain FP32 chain would leave rounding errors of the size of
+                // s_n u, not of w_{n+1}, outside span(K)
+                const int p = tid + v * T;
+                DotAcc<VT> x;
+                if (first) {
+                    x.add(vsn, us[p]);
+                    x.lo = __fmaf_rn(vsn, uls[p], x.lo);
+                } else {
+                    x.hi = wget(v);
+                    x.lo = uls[p];
+                }
 #pragma unroll
-            for (int l = 0; l < kB; ++l)
-                x = fma(-co[l], (a && v < nvl[l]) ? kb[l * MP + v * T] : VT(0), x);
-            wset(v, x);
+                for (int l = 0; l < kB; ++l)
+                    x.add(-co[l], (a && v < nvl[l]) ? kb[l * MP + v * T] : VT(0));
+                wset(v, x.hi);
+                uls[p] = x.lo;
+            } else {
+                VT x;
+                if (first) {
+                    VT uu;
+                    if constexpr (kUs) uu = us[tid + v * T]; else uu = a ? u[v * T] : VT(0);
+                    x = uu * vsn;
+                } else {
+                    x = wget(v);
+                }
+#pragma unroll
+                for (int l = 0; l < kB; ++l)
+                    x = fma(-co[l], (a && v < nvl[l]) ? kb[l * MP + v * T] : VT(0), x);
+                wset(v, x);
+            }
         });
     }
     VT *wo = K + base + (int64_t)(n + 1) * MP + tid;   // the next slot, unnormalised, zeros included
     const int nvu = live(cnt_s[n + 1]);
 #pragma unroll
-    for (int v = 0; v < VPT; ++v) wo[v * T] = v < nvu ? wget(v) : VT(0);
+    for (int v = 0; v < VPT; ++v) {
+        VT x = VT(0);
+        if (v < nvu) {
+            if constexpr (kLo) x = __fadd_rn(wget(v), uls[tid + v * T]); else x = wget(v);
+        }
+        wo[v * T] = x;
+    }
 }
 
 template <typename VT, int VPT, int T>
@@ -751,6 +533,8 @@ cudaError_t gs_shape(const KrylovBatch &b, int n, int need_w, double tau, cudaSt
 }
 
 }  // namespace
+
+MARNOLDI_CHECK_TAKE(krylov)
 
 cudaError_t launch_init(const DeviceMatrix &A, const KrylovBatch &b, cudaStream_t s)
 {
@@ -796,6 +580,7 @@ cudaError_t launch_spmm_hs(const DeviceMatrix &A, const KrylovBatch &b, const vo
 
 cudaError_t launch_gs(const KrylovBatch &b, int n, int need_w, double tau, cudaStream_t s)
 {
+    if (gs_stream_shape(b.shape, b.prec)) return launch_gs_stream(b, n, need_w, tau, s);
     return b.prec == 0 ? gs_shape<double>(b, n, need_w, tau, s) : gs_shape<float>(b, n, need_w, tau, s);
 }
 

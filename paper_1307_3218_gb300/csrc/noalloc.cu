@@ -17,7 +17,6 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
-#include <mutex>
 
 namespace marnoldi {
 namespace {
@@ -26,16 +25,17 @@ constexpr int kThreads = 256;
 constexpr int kChunk = 4096;                       // levels per block
 constexpr int kMaxBlocks = 4096;                   // partial-sum slots
 constexpr int64_t kMaxLevels = (int64_t)kChunk * kMaxBlocks;
+static_assert(kMaxLevels == MARNOLDI_COUNT_NOALLOC_MAX_LEVELS, "the header states the limit");
 constexpr int kScratchDoubles = 2 * kMaxBlocks + 2; // partials, then the ticket
-constexpr int kMaxDevices = 64;
 
 // Shared by every call on a device; keeps the last call's contents.
 static __device__ __align__(256) double g_count_scratch[kScratchDoubles];
 
-// Device address of g_count_scratch per device ordinal (host code cannot use
-// the symbol itself: on the host it names a stand-in, not device memory).
-double *g_scratch_ptr[kMaxDevices] = {};
-std::mutex g_scratch_mu;
+// The device address of g_count_scratch is looked up on every call (host
+// code cannot use the symbol itself: on the host it names a stand-in, not
+// device memory).  The lookup allocates nothing, and a cached address would
+// go stale if the device's primary context were reset and the module loaded
+// again at another address.
 
 __device__ __forceinline__ double fermi_na(double x)
 {
@@ -98,25 +98,13 @@ __global__ void __launch_bounds__(kThreads) count_noalloc_kernel(
     }
 }
 
-// Set-up, once per device with that device current: the device address of
-// the scratch array.  Returns nullptr on failure.
+// Set-up, on every call with the caller's device current: the device address
+// of the scratch array on that device.  Returns nullptr on failure.
 double *scratch_for_current_device(cudaError_t *err)
 {
-    int dev = 0;
-    *err = cudaGetDevice(&dev);
-    if (*err != cudaSuccess) return nullptr;
-    if (dev < 0 || dev >= kMaxDevices) {
-        *err = cudaErrorInvalidDevice;
-        return nullptr;
-    }
-    std::lock_guard<std::mutex> lock(g_scratch_mu);
-    if (!g_scratch_ptr[dev]) {
-        double *p = nullptr;
-        *err = cudaGetSymbolAddress((void **)&p, g_count_scratch);
-        if (*err != cudaSuccess) return nullptr;
-        g_scratch_ptr[dev] = p;
-    }
-    return g_scratch_ptr[dev];
+    double *p = nullptr;
+    *err = cudaGetSymbolAddress((void **)&p, g_count_scratch);
+    return *err == cudaSuccess ? p : nullptr;
 }
 
 }  // namespace

@@ -200,7 +200,7 @@ __global__ void __launch_bounds__(128) density_kernel(
     const double *__restrict__ eps, const double *__restrict__ t, const double *__restrict__ P,
     const int64_t *__restrict__ p_off, const int64_t *__restrict__ rp,
     const int64_t *__restrict__ tmap, double mu, double kT, double *__restrict__ rho,
-    double *__restrict__ rhoE)
+    double *__restrict__ rhoE, int64_t nval)
 {
     extern __shared__ double ys[];
     double *y = ys, *ye = ys + nu;
@@ -230,6 +230,7 @@ __global__ void __launch_bounds__(128) density_kernel(
             se = fma(row[a], ye[a], se);
         }
         const int64_t o = tmap[kb + (r >> 2)] * 16 + (r & 3) * 4 + b;
+        if (!in_range(o, nval, kChkDensityOut)) continue;
         rho[o] = s;
         rhoE[o] = se;
     }
@@ -395,7 +396,7 @@ cudaError_t launch_density(const DeviceMatrix &A, const ColumnState &st, double 
 {
     if (st.ncols == 0) return cudaSuccess;
     density_kernel<<<(unsigned)st.ncols, 128, 2 * st.nu * sizeof(double), s>>>(
-        st.nu, st.cols, st.nu_eff, st.eps, st.t, st.P, st.p_off, A.rp, A.tmap, mu, kT, rho, rhoE);
+        st.nu, st.cols, st.nu_eff, st.eps, st.t, st.P, st.p_off, A.rp, A.tmap, mu, kT, rho, rhoE, A.nnzb * 16);
     return cudaGetLastError();
 }
 
@@ -407,5 +408,7 @@ cudaError_t launch_green(const DeviceMatrix &A, const ColumnState &st, double zr
         st.nu, st.cols, st.nu_eff, st.eps, st.t, st.P, st.p_off, A.rp, A.tmap, zr, zi, G);
     return cudaGetLastError();
 }
+
+MARNOLDI_CHECK_TAKE(outputs)
 
 }  // namespace marnoldi

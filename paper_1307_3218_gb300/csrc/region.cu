@@ -280,7 +280,9 @@ __device__ __forceinline__ void regional_rows(
     for (int s = 0; s < cnt; ++s) {
         const int q = lci[base + (int64_t)s * n_reg + p];
         const int64_t k = lgk[base + (int64_t)s * n_reg + p];
+        if (!in_range(q, n_reg, kChkRegionCol)) continue;
         const int64_t xp = 32 * (int64_t)tinv[(int64_t)(q >> 3) * ncols + c0] + 4 * (q & 7);
+        if (!in_range(xp, ldu - 3, kChkRegionGather)) continue;
         VT xv[NC][4];
 #pragma unroll
         for (int m = 0; m < NC; ++m) load4(X + (int64_t)(c0 + m) * ldx + xp, xv[m]);
@@ -443,5 +445,7 @@ cudaError_t launch_init_regional(const DeviceMatrix &A, const RegionMaps &rm, co
     return cudaGetLastError();
 }
 
+
+MARNOLDI_CHECK_TAKE(region)
 
 }  // namespace marnoldi

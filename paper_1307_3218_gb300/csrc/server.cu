@@ -169,8 +169,9 @@ marnoldi::PatternStats group_stats(const std::vector<Request *> &g)
 
 bool groupable(const Request *a, const Request *b)
 {
+    // kT enters only each member's own Fermi step (marnoldi_set_member_temperatures)
     return a->region_atoms == 0 && b->region_atoms == 0 && a->prec == b->prec && a->nu == b->nu &&
-           a->kT == b->kT && a->nu <= 253 && a->nu <= a->stats.nc && b->nu <= b->stats.nc &&
+           a->nu <= 253 && a->nu <= a->stats.nc && b->nu <= b->stats.nc &&
            a->m_pad == b->m_pad && (a->rho == nullptr) == (b->rho == nullptr);
 }
 
@@ -202,7 +203,7 @@ void run_group(marnoldi_server *srv, const std::vector<Request *> &g, int64_t ba
     // atoms carry one block (H = 0, S = I) and four padding orbitals
     std::vector<int64_t> off(g.size() + 1, 0), boff(g.size(), 0), rp(1, 0);
     std::vector<int32_t> ci;
-    std::vector<double> H, S, ne;
+    std::vector<double> H, S, ne, kT;
     std::vector<uint8_t> mask;
     int64_t nb = 0;
     for (size_t q = 0; q < g.size(); ++q) {
@@ -227,6 +228,7 @@ void run_group(marnoldi_server *srv, const std::vector<Request *> &g, int64_t ba
         }
         off[q + 1] = off[q] + n;
         ne.push_back(r->electron_count);
+        kT.push_back(r->kT);
     }
     const Request *r0 = g[0];
     auto finish = [&](int rc, const char *msg) {
@@ -244,6 +246,7 @@ void run_group(marnoldi_server *srv, const std::vector<Request *> &g, int64_t ba
         return;
     }
     rc = marnoldi_set_members(ctx, (int)g.size(), off.data(), ne.data());
+    if (!rc) rc = marnoldi_set_member_temperatures(ctx, (int)g.size(), kT.data());
     if (!rc) rc = marnoldi_set_batch(ctx, batch);
     if (!rc) rc = marnoldi_solve(ctx, nullptr, -1, r0->nu, 0, 0.0, r0->kT, nullptr);
     if (!rc && r0->rho) {

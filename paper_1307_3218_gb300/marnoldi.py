@@ -32,6 +32,7 @@ MARNOLDI_ENOCONV = -7
 MARNOLDI_EPENDING = -8
 MARNOLDI_FP64 = 0
 MARNOLDI_MIXED = 1
+MARNOLDI_COUNT_NOALLOC_MAX_LEVELS = 16777216   # include/marnoldi.h
 
 STATUS_NAMES = {0: "OK", -1: "EINVAL", -2: "ENOTSPD", -3: "ENOMEM", -4: "ECUDA", -5: "ETIMEOUT",
                 -6: "ESTATE", -7: "ENOCONV", -8: "EPENDING"}
@@ -52,7 +53,9 @@ class MarnoldiError(RuntimeError):
 
 
 def library_path() -> str:
-    return _build.lib_path()
+    """The library load() opens: $MARNOLDI_LIB if set (another build of the same sources, such as
+    the index-check variant), else the default build."""
+    return os.environ.get("MARNOLDI_LIB") or _build.lib_path()
 
 
 def load(path: str | None = None):
@@ -92,8 +95,10 @@ def load(path: str | None = None):
         "marnoldi_eigenstate": (i32, [P, i64, d, P, P, P]),
         "marnoldi_set_members": (i32, [P, i32, P, P]),
         "marnoldi_member_energy": (i32, [P, i32, P, P, P]),
+        "marnoldi_set_member_temperatures": (i32, [P, i32, P]),
         "marnoldi_set_autotune": (i32, [i32]),
         "marnoldi_gs_shape": (i32, [P, P, P]),
+        "marnoldi_check_status": (i32, [P, P, P]),
         "marnoldi_device_bytes": (i32, [P, P, P]),
         "marnoldi_footprint": (i32, [i64, P, P, P, i32, i32, i32, i64, P, P]),
         "marnoldi_server_create": (i32, [C.POINTER(P), i32, C.c_size_t]),
@@ -325,6 +330,12 @@ def marnoldi_set_members(ctx: Context, atom_offsets, electron_counts) -> None:
                                        _ptr(ne) if n else None), ctx)
 
 
+def marnoldi_set_member_temperatures(ctx: Context, kT) -> None:
+    """Each member's own kT for its Fermi level, density and energy (see the C header)."""
+    t = np.ascontiguousarray(kT, dtype=np.float64)
+    _check(load().marnoldi_set_member_temperatures(ctx.handle, int(t.size), _ptr(t)), ctx)
+
+
 def marnoldi_member_energy(ctx: Context, member: int) -> tuple[float, float, float]:
     E, mu, N = C.c_double(), C.c_double(), C.c_double()
     _check(load().marnoldi_member_energy(ctx.handle, int(member), C.byref(E), C.byref(mu), C.byref(N)), ctx)
@@ -431,12 +442,50 @@ def marnoldi_count_noalloc(eps_device, w_device, nu_eff_device, ncols: int, nu: 
     """N(mu) and E(mu) over device-resident levels into out_device[0:2], allocating nothing.
 
     For callers that cannot allocate device memory; the reduction's scratch is a
-    fixed array inside the library (at most 16,777,216 levels per call).
+    fixed array inside the library (at most 16,777,216 levels per call).  eps_device
+    and w_device: float64 CUDA tensors of at least ncols*nu elements; nu_eff_device:
+    int32, at least ncols, or None; out_device: float64, at least 2; all contiguous
+    and on the current device (else MarnoldiError(EINVAL) before any call).
     """
+    ncols, nu = int(ncols), int(nu)
+    if ncols >= 1 and nu >= 1 and ncols * nu > MARNOLDI_COUNT_NOALLOC_MAX_LEVELS:
+        raise MarnoldiError(MARNOLDI_EINVAL, f"count_noalloc: ncols * nu exceeds the maximum of "
+                            f"{MARNOLDI_COUNT_NOALLOC_MAX_LEVELS} levels of the fixed scratch")
+    need = max(ncols, 0) * max(nu, 0)
+    _device_tensor("eps_device", eps_device, "float64", need)
+    _device_tensor("w_device", w_device, "float64", need)
+    if nu_eff_device is not None:
+        _device_tensor("nu_eff_device", nu_eff_device, "int32", max(ncols, 0))
+    _device_tensor("out_device", out_device, "float64", 2)
     st = _current_stream() if stream is None else int(stream)
     _check(load().marnoldi_count_noalloc(_ptr(eps_device), _ptr(w_device), _ptr(nu_eff_device),
-                                         int(ncols), int(nu), float(mu), float(kT),
+                                         ncols, nu, float(mu), float(kT),
                                          _ptr(out_device), C.c_void_p(st)))
+
+
+def _device_tensor(name: str, a, dtype: str, min_len: int) -> None:
+    """Raise MarnoldiError(EINVAL) unless `a` is a contiguous torch CUDA tensor of `dtype` on the
+    current device with at least min_len elements (the C entry point cannot check any of this)."""
+    import torch
+    if not isinstance(a, torch.Tensor) or not a.is_cuda:
+        raise MarnoldiError(MARNOLDI_EINVAL, f"count_noalloc: {name} must be a torch CUDA tensor")
+    if a.device.index != torch.cuda.current_device():
+        raise MarnoldiError(MARNOLDI_EINVAL, f"count_noalloc: {name} is on cuda:{a.device.index}, "
+                            f"not the current device cuda:{torch.cuda.current_device()}")
+    if a.dtype != getattr(torch, dtype):
+        raise MarnoldiError(MARNOLDI_EINVAL, f"count_noalloc: {name} must be {dtype}, not {a.dtype}")
+    if not a.is_contiguous():
+        raise MarnoldiError(MARNOLDI_EINVAL, f"count_noalloc: {name} must be contiguous")
+    if a.numel() < min_len:
+        raise MarnoldiError(MARNOLDI_EINVAL, f"count_noalloc: {name} holds {a.numel()} elements, "
+                            f"fewer than the {min_len} needed")
+
+
+def marnoldi_check_status() -> tuple[bool, int, int]:
+    """(built with index checks, first failed check site or 0, its index); clears the records."""
+    comp, site, idx = C.c_int(), C.c_int(), C.c_int64()
+    _check(load().marnoldi_check_status(C.byref(comp), C.byref(site), C.byref(idx)))
+    return bool(comp.value), site.value, idx.value
 
 
 def marnoldi_last_error(ctx: Context | None = None) -> str:

@@ -139,3 +139,22 @@ def test_package_fails_loudly_without_library(tmp_path):
             mm.load(str(tmp_path / "missing.so"))
     finally:
         mm._LIB = saved
+
+
+def test_count_noalloc_binding_rejects_host_arrays():
+    """The binding refuses what the C entry point cannot check: host arrays and CPU tensors
+    (and, on a GPU, wrong dtypes, devices, strides or lengths) never reach the kernel."""
+    import torch
+
+    import paper_1307_3218_gb300 as pm
+    x = np.zeros(16)
+    with pytest.raises(pm.MarnoldiError) as ei:
+        pm.marnoldi_count_noalloc(x, x, None, 4, 4, 0.0, 0.1, x)
+    assert ei.value.code == pm.marnoldi.MARNOLDI_EINVAL
+    t = torch.zeros(16, dtype=torch.float64)
+    with pytest.raises(pm.MarnoldiError) as ei:
+        pm.marnoldi_count_noalloc(t, t, None, 4, 4, 0.0, 0.1, t)
+    assert ei.value.code == pm.marnoldi.MARNOLDI_EINVAL
+    with pytest.raises(pm.MarnoldiError) as ei:          # oversize, before any tensor check
+        pm.marnoldi_count_noalloc(t, t, None, 16_777_217, 1, 0.0, 0.1, t)
+    assert "16777216" in str(ei.value)

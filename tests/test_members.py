@@ -128,3 +128,38 @@ def test_member_checks(m):
     m.marnoldi_set_members(ctx, [], [])           # back to one structure
     m.marnoldi_solve(ctx, None, 20, 0, float(sum(ne)), KT)
     m.marnoldi_destroy(ctx)
+
+
+def _alone_kT(m, t, prec, nu, kT):
+    ctx = m.setup_system(t, prec)
+    m.marnoldi_solve(ctx, None, nu, 0, t.n_electrons, kT)
+    out = dict(zip(("E", "mu", "N"), m.marnoldi_energy(ctx)))
+    out["rho"], out["rhoE"] = m.marnoldi_density(ctx)
+    m.marnoldi_destroy(ctx)
+    return out
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_members_with_their_own_temperatures(m, prec):
+    """kT enters only each member's Fermi step: members of the same padded length solved at
+    kT 0.05, 0.1 and 0.2 in one union equal their solves alone, bit for bit."""
+    systems = [amorphous_system(160, seed=11), amorphous_system(256, seed=12), amorphous_system(200, seed=13)]
+    temps = [0.05, 0.2, 0.1]
+    n, rp, ci, H, S, mask, offs, boffs = m.union_of(systems)
+    ctx = m.marnoldi_setup(n, rp, ci, H, S, mask, precision=prec)
+    m.marnoldi_set_members(ctx, offs, [t.n_electrons for t in systems])
+    with pytest.raises(m.MarnoldiError):
+        m.marnoldi_set_member_temperatures(ctx, temps[:2])          # one per member
+    with pytest.raises(m.MarnoldiError):
+        m.marnoldi_set_member_temperatures(ctx, [0.05, -0.1, 0.1])  # positive
+    m.marnoldi_set_member_temperatures(ctx, temps)
+    m.marnoldi_solve(ctx, None, 30, 0, 0.0, 0.1)
+    rho, rhoE = m.marnoldi_density(ctx)
+    for q, (t, kT) in enumerate(zip(systems, temps)):
+        E, mu, N = m.marnoldi_member_energy(ctx, q)
+        a = _alone_kT(m, t, prec, 30, kT)
+        assert (E, mu, N) == (a["E"], a["mu"], a["N"])
+        sl = slice(boffs[q], boffs[q] + t.nnzb)
+        np.testing.assert_array_equal(rho[sl], a["rho"])
+        np.testing.assert_array_equal(rhoE[sl], a["rhoE"])
+    m.marnoldi_destroy(ctx)

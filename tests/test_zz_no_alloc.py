@@ -62,3 +62,40 @@ def test_count_noalloc_rejects_oversize(m):
         m.marnoldi_count_noalloc(x, x, None, 16_777_217, 1, 0.0, KT, x)
     assert ei.value.code == m.marnoldi.MARNOLDI_EINVAL
     assert "16777216" in str(ei.value)
+
+
+def test_count_noalloc_allocates_nothing(m):
+    """After a first call (which loads the library's device code on this device), further calls
+    leave the device's free memory and torch's allocated bytes unchanged."""
+    import torch
+    n, nu = 4096, 30
+    g = torch.Generator(device="cpu").manual_seed(3)
+    eps = torch.randn(n * nu, generator=g, dtype=torch.float64).cuda()
+    w = torch.rand(n * nu, generator=g, dtype=torch.float64).cuda()
+    out = torch.empty(2, dtype=torch.float64, device="cuda")
+    m.marnoldi_count_noalloc(eps, w, None, n, nu, 0.0, KT, out)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    alloc0 = torch.cuda.memory_allocated()
+    for q in range(5):
+        m.marnoldi_count_noalloc(eps, w, None, n, nu, 0.1 * q, KT, out)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 >= free0
+    assert torch.cuda.memory_allocated() == alloc0
+
+
+def test_count_noalloc_binding_checks_tensors(m):
+    import torch
+    good = torch.zeros(64, dtype=torch.float64, device="cuda")
+    out = torch.zeros(2, dtype=torch.float64, device="cuda")
+    for bad in (torch.zeros(64, dtype=torch.float32, device="cuda"),     # dtype
+                torch.zeros(63, dtype=torch.float64, device="cuda"),     # too short for 8 x 8
+                torch.zeros(128, dtype=torch.float64, device="cuda")[::2]):  # strided
+        with pytest.raises(m.MarnoldiError) as ei:
+            m.marnoldi_count_noalloc(bad, good, None, 8, 8, 0.0, KT, out)
+        assert ei.value.code == m.marnoldi.MARNOLDI_EINVAL
+    with pytest.raises(m.MarnoldiError) as ei:
+        m.marnoldi_count_noalloc(good, good, torch.zeros(8, dtype=torch.int64, device="cuda"),
+                                 8, 8, 0.0, KT, out)
+    assert ei.value.code == m.marnoldi.MARNOLDI_EINVAL
