@@ -40,11 +40,15 @@ UNIT = "columns/s"
 L2_FLUSH_BYTES = 256 << 20
 FP64_PEAK_NOTE = "152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz (nominal 1.25 TFLOP/s FP64)"
 # (dram__bytes_read + dram__bytes_write) / algorithmic bytes of one captured
-# Gram-Schmidt launch (ncu --set full, mixed precision, 608 columns, step n = 20):
-# (1.788354e9 + 0.034031e9) / (1.929072e9 read + 0.039846e9 written over the
-# supports); below 1 because the subtraction re-reads the last blocks from L2.
-# Must be re-measured (or removed) whenever the kernel changes.
-GS_DRAM_PER_ALGORITHMIC = {"mixed": 0.9256}
+# Gram-Schmidt launch (ncu --set full, mixed precision, 608 columns, step n = 20,
+# algorithmic 1.929072e9 B read + 0.039846e9 B written over the supports), per
+# precision and launch shape (values per thread, threads) of the kernel that was
+# captured; a shape without an entry reports no traffic.  An entry must be
+# re-measured (or removed) whenever its kernel changes.
+# gs_stream_kernel<512,16384>: (2.024254e9 + 0.038177e9) / 1.968918e9; above 1 by the re-reads
+# of u, its lo word and w_n with every block that miss L2 despite their evict-last hint.
+GS_DRAM_PER_ALGORITHMIC = {("mixed", (32, 544)): 1.0475}
+GS_DRAM_KERNEL = {(32, 544): "gs_stream_kernel<512,16384>"}
 
 
 def parse():
@@ -63,6 +67,14 @@ def parse():
     p.add_argument("--no-extra", action="store_true",
                    help="skip the nu=100 and regional side measurements")
     p.add_argument("--no-serving", action="store_true", help="skip the request-server measurement")
+    p.add_argument("--c4", action="store_true",
+                   help="only the polymer-chain batching workload as configured (256 chains, 4..400 units)")
+    p.add_argument("--c5", action="store_true",
+                   help="only the Poisson serving workload as configured (1,000-200,000 atoms, a sweep of rates)")
+    p.add_argument("--c5-window", type=float, default=60.0)
+    p.add_argument("--large-full", type=int, default=0,
+                   help="only the paper-scale structure of this many atoms at nu = 100, every column, in "
+                        "65,536-column batches, mixed and FP64 (e.g. 1048576)")
     p.add_argument("--large", type=int, default=0,
                    help="atoms of the paper-scale regional run (e.g. 1048576); 0 = skip")
     p.add_argument("--order-n", default="",
@@ -302,7 +314,8 @@ def time_gpu(m, t, cols, args, prec, steps, warmup, dev, measure_clocks=False):
     clocks = clk.stop() if clk else None
     stats = m.marnoldi_kernel_stats(ctx)
     E, mu, N = m.marnoldi_energy(ctx)
-    res = dict(times=times, stats=stats, E=E, mu=mu, N=N, clocks=clocks, ctx=ctx)
+    res = dict(times=times, stats=stats, E=E, mu=mu, N=N, clocks=clocks, ctx=ctx,
+               gs_shape=tuple(m.marnoldi_gs_shape(ctx)))
     return res
 
 
@@ -415,6 +428,21 @@ def main():
         torch.distributed.init_process_group("nccl", device_id=dev)
     m.load()
     m.marnoldi_set_autotune(0 if args.fixed_shapes else 1)
+    if args.large_full:
+        print(json.dumps({"metric": "mArnoldi columns/s", "n_gpus": 1, "data": "synthetic",
+                          "large_full": large_full(m, args.large_full, 256, 65536)}))
+        return
+    if args.c4 or args.c5:
+        # the configured batching / serving workloads alone (one JSON line of their own)
+        prec = 1 if args.precision == "mixed" else 0
+        budget = int(args.serve_budget_gb * 2**30)
+        out = {"metric": "mArnoldi columns/s and serve p50/p99 ms", "n_gpus": 1, "data": "synthetic"}
+        if args.c4:
+            out["c4"] = serve_c4(m, args.serve_workers, budget, prec)
+        if args.c5:
+            out["c5"] = serve_c5(m, args.serve_workers, budget, prec, window_s=args.c5_window)
+        print(json.dumps(out))
+        return
     t, cols = workload(args)
     ncols = len(cols)
     prec = 1 if args.precision == "mixed" else 0
@@ -458,14 +486,17 @@ def main():
         # DRAM bytes per average launch: the ncu capture's DRAM/algorithmic ratio for
         # this kernel (a smaller case of the same kernel; bytes scale with columns and
         # stored vectors) times the algorithmic bytes per launch
-        ratio = GS_DRAM_PER_ALGORITHMIC.get(args.precision) if dom == "gs" and not args.region else None
+        gs_shape = res.get("gs_shape")
+        ratio = (GS_DRAM_PER_ALGORITHMIC.get((args.precision, gs_shape))
+                 if dom == "gs" and not args.region else None)
         launches_per_step = nlaunch / steps
         traffic = round(ratio * by / launches_per_step) if ratio and by else None
         roof = {"kernel": dom, "bound": bound, "achieved": round(ach, 3), "peak": round(peak, 3),
                 "unit": unit, "frac": round(ach / peak, 4), "traffic": traffic,
                 "traffic_note": ("dram bytes per average launch = DRAM/algorithmic "
-                                 f"{ratio} (ncu, gs_kernel<float,16,1024>, step n=20, 608 columns) "
+                                 f"{ratio} (ncu, {GS_DRAM_KERNEL.get(gs_shape)}, step n=20, 608 columns) "
                                  "x algorithmic bytes per launch") if traffic else None,
+                "gs_shape": list(gs_shape) if gs_shape else None,
                 "peak_source": peak_src, "launches": nlaunch, "avg_launch_ms": round(dom_ms / nlaunch, 4),
                 "algorithmic_per_step": {"bytes": by, "flops": fl}}
 
@@ -689,6 +720,74 @@ def large_structure(m, n_atoms: int, n_reg: int, batch: int):
     return out
 
 
+def large_full(m, n_atoms: int, n_reg: int, batch: int, n_sample: int = 32):
+    """The paper-scale configuration in full: every one of the 4 n_atoms columns of amorphous
+    carbon at nu = 100 in regional mode (n_reg-atom regions), streamed through the solve in
+    batches of `batch` columns, mu by bisection over all of them, densities on the device;
+    mixed precision and FP64.  Per-kernel times (CUDA events) give each kernel's share and
+    the Gram-Schmidt HBM fraction (dense-region bytes: every stored vector over the whole
+    region, an upper bound of the supports) and the eigensolver's FP64 rate; a seeded sample
+    of columns is recomputed by the regional oracle at the GPU's mu."""
+    import torch
+    import oracle
+    from tbsynth import amorphous_system
+    t0 = time.perf_counter()
+    t = amorphous_system(n_atoms, seed=0)
+    out = {"atoms": n_atoms, "M": t.M, "nnzb": t.nnzb, "region_atoms": n_reg, "nu": 100,
+           "batch_columns": batch, "generation_s": round(time.perf_counter() - t0, 1)}
+    peaks = read_peaks()
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    nu, m_reg = 100, 4 * n_reg
+    rng = np.random.default_rng(17)
+    sample = np.sort(rng.choice(t.M, size=n_sample, replace=False))
+    for prec in (1, 0):
+        name = "mixed" if prec else "fp64"
+        ctx = m.setup_system(t, prec)
+        m.marnoldi_set_batch(ctx, batch)
+        m.marnoldi_solve(ctx, np.arange(4096, dtype=np.int64), nu, n_reg, 0.0, KT, mu_fixed=4.0)  # warm-up
+        m.marnoldi_set_profiling(ctx, True)
+        m.marnoldi_kernel_stats(ctx, reset=True)
+        rho = torch.empty(t.nnzb * 16, dtype=torch.float64, device="cuda")
+        rhoE = torch.empty_like(rho)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        m.marnoldi_solve(ctx, None, nu, n_reg, float(t.n_electrons), KT)
+        m.marnoldi_density_device(ctx, rho, rhoE)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        E, mu, N = m.marnoldi_energy(ctx)
+        st = m.marnoldi_kernel_stats(ctx)
+        nue, eps, w = m.marnoldi_column_stats(ctx)
+        vb = 4 if prec else 8
+        # Gram-Schmidt bytes over dense regions: per column and step n, u (and lo), w_n,
+        # w_i and S w_i (i <= n), w_i again, the new w
+        per_col = sum(((2 if prec else 1) + 1 + 2 * (n + 1) + (n + 1 if n < nu - 1 else 0) +
+                       (1 if n < nu - 1 else 0)) * m_reg * vb for n in range(nu))
+        gs_ms = st["gs"][1]
+        eig_ms = st["eigsub"][1]
+        eig_flop = (4.0 / 3.0 * nu ** 3 + 6.0 * nu * nu * (4 * 12 + 2)) * t.M
+        rho_h = rho.cpu().numpy().reshape(-1, 4, 4)
+        rhoE_h = rhoE.cpu().numpy().reshape(-1, 4, 4)
+        ref = oracle.solve(t, nu=nu, kT=KT, mu_fixed=mu, cols=sample, region_atoms=n_reg)
+        mask = ~np.isnan(ref.rho)
+        drho = float(np.abs(rho_h[mask] - ref.rho[mask]).max())
+        drhoE = float(np.abs(rhoE_h[mask] - ref.rhoE[mask]).max())
+        out[name] = {"seconds": round(dt, 2), "columns_per_s": round(t.M / dt, 1),
+                     "E_band_per_atom_eV": E / n_atoms, "mu_eV": mu, "N": N,
+                     "kernel_ms": {k: round(v[1], 1) for k, v in st.items() if v[1] > 0},
+                     "gs_hbm_frac_dense_bytes": round(per_col * t.M / (gs_ms / 1e3) / 1e9 / hbm, 3),
+                     "eig_fp64_tflops": round(eig_flop / (eig_ms / 1e3) / 1e12, 3),
+                     "oracle_sample": {"columns": int(sample.size), "max_abs_drho": drho,
+                                       "max_abs_drhoE_eV": drhoE}}
+        m.marnoldi_destroy(ctx)
+        del rho, rhoE
+        torch.cuda.empty_cache()
+    out["note"] = ("gs_hbm_frac_dense_bytes counts every stored vector over the whole region (an upper "
+                   "bound of the bytes over the vectors' supports); eig_fp64_tflops counts the "
+                   "tridiagonalisation (4/3 nu^3) and the rotations applied to 50 rows (6 nu^2 x 50)")
+    return out
+
+
 SERVE_SIZES = (256, 512, 1024, 2048, 4096)
 SERVE_SIZE_P = (0.3, 0.3, 0.2, 0.15, 0.05)
 
@@ -811,6 +910,111 @@ def serving(m, t4096, requests: int, workers: int, budget: int, prec: int):
                     "mean_ms": round(float(lat.mean()), 2), "max_ms": round(float(lat.max()), 2),
                     "columns_per_s": round(ncols_total / pois["wall"], 1)},
     }
+
+
+def _served(results, t_first=None):
+    """Wall time, latencies (ms) and per-request columns of a set of served results."""
+    first = min(r["t_submit"] for r in results) if t_first is None else t_first
+    wall = max(r["t_end"] for r in results) - first
+    lat = np.array([r["latency_s"] for r in results]) * 1e3
+    return wall, lat
+
+
+def serve_c4(m, workers: int, budget: int, prec: int = 1, n_chains: int = 256, seed: int = 4):
+    """Uneven batching on the polymer workload as configured: n_chains fluorene-like chains
+    (69 atoms per unit), unit counts log-uniform in 4..400 from `seed`, nu drawn from
+    {30, 100, 300}, every real orbital, mu by bisection (kT = 0.1 eV), densities back to the
+    host; chains of up to 59 units (4,073 atoms) in global mode, longer ones in regional mode
+    (256-atom regions).  All submitted at once to the request server."""
+    from tbsynth import polymer_system
+    rng = np.random.default_rng(seed)
+    units = np.rint(np.exp(rng.uniform(np.log(4), np.log(400), size=n_chains))).astype(int)
+    nus = rng.choice([30, 100, 300], size=n_chains)
+    t0 = time.perf_counter()
+    chains = [polymer_system(int(u), seed=1000 + q, check_spd=False) for q, u in enumerate(units)]
+    gen_s = time.perf_counter() - t0
+    regions = [0 if u <= 59 else 256 for u in units]
+    cols = [c.real_columns().size for c in chains]
+    with m.Server(workers=workers, hbm_budget_bytes=budget) as srv:
+        srv.set_group_limit(16)
+        srv.wait(srv.submit_system(chains[0], prec, 30, regions[0], chains[0].n_electrons, 0.1))   # warm-up
+        ids = [srv.submit_system(c, prec, int(nu), reg, c.n_electrons, 0.1)
+               for c, nu, reg in zip(chains, nus, regions)]
+        res = [srv.wait(i) for i in ids]
+        st = srv.stats()
+    wall, lat = _served(res)
+    by_nu = {}
+    for nu in (30, 100, 300):
+        sel = [q for q in range(n_chains) if nus[q] == nu]
+        by_nu[f"nu{nu}"] = {"chains": len(sel), "columns": int(sum(cols[q] for q in sel)),
+                            "p50_ms": round(float(np.percentile(lat[sel], 50)), 1) if sel else None}
+    return {"config": f"{n_chains} fluorene-like chains, units log-uniform 4..400 (seed {seed}), nu from "
+                      "{30, 100, 300}, global mode up to 59 units, 256-atom regions above, "
+                      f"{'mixed' if prec else 'fp64'}, kT 0.1 eV, densities to the host",
+            "atoms_total": int(sum(c.n_block_rows for c in chains)), "columns": int(sum(cols)),
+            "regional_chains": int(sum(1 for r in regions if r)), "generation_s": round(gen_s, 1),
+            "wall_s": round(wall, 2), "columns_per_s": round(sum(cols) / wall, 1),
+            "p50_ms": round(float(np.percentile(lat, 50)), 1), "p99_ms": round(float(np.percentile(lat, 99)), 1),
+            "groups": st["groups"], "largest_group": st["largest_group"], "by_nu": by_nu}
+
+
+def serve_c5(m, workers: int, budget: int, prec: int = 1, window_s: float = 60.0,
+             rates=(1.0, 0.5, 0.25, 0.125), seed: int = 5, pool_sizes: int = 6):
+    """Serving as configured: Poisson arrivals of carbon or polymer structures (50/50) of
+    1,000-200,000 atoms (log-uniform; drawn from a pool of `pool_sizes` log-spaced sizes per
+    kind), each with its own nu in {30, 100} and kT in {0.05, 0.1, 0.2} eV; global mode up to
+    4,096 atoms, 256-atom regions above.  For each arrival rate lambda (requests/s), `window_s`
+    seconds of arrivals; reported: offered and served load (requests/s and columns/s) and the
+    submit-to-result latency p50 / p99."""
+    from tbsynth import amorphous_system, polymer_system
+    rng = np.random.default_rng(seed)
+    sizes = np.exp(np.linspace(np.log(1000), np.log(200000), pool_sizes))
+    t0 = time.perf_counter()
+    pool = {("carbon", q): amorphous_system(int(round(n)), seed=500 + q, check_spd=False)
+            for q, n in enumerate(sizes)}
+    pool.update({("polymer", q): polymer_system(max(15, int(round(n / 69))), seed=600 + q, check_spd=False)
+                 for q, n in enumerate(sizes)})
+    gen_s = time.perf_counter() - t0
+    out = {"config": f"Poisson arrivals, carbon or polymer 50/50, 1,000-200,000 atoms log-uniform "
+                     f"(pool of {pool_sizes} sizes per kind), nu from {{30, 100}}, kT from {{0.05, 0.1, 0.2}} eV, "
+                     f"global mode up to 4,096 atoms, 256-atom regions above, {'mixed' if prec else 'fp64'}, "
+                     f"densities to the host, {window_s:g} s of arrivals per rate",
+           "pool_atoms": {f"{k}_{q}": int(v.n_block_rows) for (k, q), v in pool.items()},
+           "generation_s": round(gen_s, 1), "rates": []}
+    with m.Server(workers=workers, hbm_budget_bytes=budget) as srv:
+        srv.set_group_limit(16)
+        for sysm in pool.values():     # one solve of each structure class first (kernels, tuning)
+            reg = 0 if sysm.n_block_rows <= 4096 else 256
+            srv.wait(srv.submit_system(sysm, prec, 30, reg, sysm.n_electrons, 0.1))
+        for lam in rates:
+            n_req = max(1, rng.poisson(lam * window_s))
+            gaps = np.sort(rng.uniform(0.0, window_s, size=n_req))
+            reqs = []
+            for _ in range(n_req):
+                kind = "carbon" if rng.random() < 0.5 else "polymer"
+                n = np.exp(rng.uniform(np.log(1000), np.log(200000)))
+                q = int(np.argmin(np.abs(np.log(sizes) - np.log(n))))
+                reqs.append((pool[(kind, q)], int(rng.choice([30, 100])), float(rng.choice([0.05, 0.1, 0.2]))))
+            ids, t_start = [], time.perf_counter()
+            for g, (sysm, nu, kT) in zip(gaps, reqs):
+                due = t_start + g
+                while time.perf_counter() < due:
+                    time.sleep(min(0.002, max(0.0, due - time.perf_counter())))
+                reg = 0 if sysm.n_block_rows <= 4096 else 256
+                ids.append(srv.submit_system(sysm, prec, nu, reg, sysm.n_electrons, kT))
+            res = [srv.wait(i) for i in ids]
+            wall, lat = _served(res, t_start)
+            cols = sum(int(s.real_columns().size) for s, _, _ in reqs)
+            out["rates"].append({
+                "offered_requests_per_s": lam, "requests": n_req,
+                "offered_columns_per_s": round(cols / window_s, 1),
+                "served_requests_per_s": round(n_req / wall, 3), "served_columns_per_s": round(cols / wall, 1),
+                "drained_s": round(wall, 1), "p50_ms": round(float(np.percentile(lat, 50)), 1),
+                "p99_ms": round(float(np.percentile(lat, 99)), 1)})
+        out["stats"] = {k: srv.stats()[k] for k in ("groups", "largest_group", "peak_running")}
+    sustain = [r for r in out["rates"] if r["drained_s"] <= 1.25 * window_s]
+    out["sustainable_requests_per_s"] = max((r["offered_requests_per_s"] for r in sustain), default=None)
+    return out
 
 
 def main_reference(args, world, rank):

@@ -690,7 +690,10 @@ bool plan_solve(int64_t m_vec, int prec, int nu, int region_atoms, int maxrow, i
     const size_t a_per_sub = p.a_global ? (size_t)nu * (nu | 1) * 8 : 0;
     const size_t per_sub = al256((size_t)(2 + es.nr_max) * nu * 8) + al256((size_t)es.rcap * 16) +
                            al256((size_t)es.scap * 8) + 8 + a_per_sub;
-    es.chunk = (int)std::max<int64_t>(32, std::min<int64_t>(B, (int64_t)(((size_t)3 << 30) / per_sub)));
+    // the QL kernel runs one subspace per lane and its time hardly grows with the chunk (it is
+    // latency-bound), so chunks are as large as 12 GB of scratch allow: at nu = 100 a whole
+    // batch of 8,192 columns is one chunk
+    es.chunk = (int)std::max<int64_t>(32, std::min<int64_t>(B, (int64_t)(((size_t)12 << 30) / per_sub)));
     const size_t ceig = (size_t)es.chunk;
     p.oED = oEg;
     p.oEE = p.oED + al256(ceig * nu * 8);

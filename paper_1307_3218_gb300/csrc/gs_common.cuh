@@ -137,6 +137,67 @@ struct DotAcc2 {
     }
 };
 
+// Two adjacent FP32 values as one 64-bit register (lane x = the lower
+// address), and the packed (f32x2) operations on such pairs; each lane is
+// rounded exactly as the scalar instruction would be.
+__device__ __forceinline__ uint64_t lds2(const float *p)
+{
+    uint64_t r;
+    asm volatile("ld.shared.b64 %0, [%1];" : "=l"(r) : "r"((uint32_t)__cvta_generic_to_shared(p)));
+    return r;
+}
+__device__ __forceinline__ uint64_t pair_of(float x)
+{
+    uint64_t r;
+    asm("mov.b64 %0, {%1, %1};" : "=l"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ uint64_t fma_x2(uint64_t a, uint64_t b, uint64_t c)
+{
+    uint64_t r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+    return r;
+}
+__device__ __forceinline__ float lane_x(uint64_t a) { return __uint_as_float((unsigned)a); }
+__device__ __forceinline__ float lane_y(uint64_t a) { return __uint_as_float((unsigned)(a >> 32)); }
+
+// Two DotAcc<float> (one per lane) in packed registers: per lane the
+// operations of DotAcc<float>::add (p = a b, e = fma(a, b, -p), the two-sum
+// of hi and p, lo += e + err).
+struct PairAcc {
+    uint64_t hi = 0, lo = 0;
+    __device__ __forceinline__ void add(uint64_t a, uint64_t b)
+    {
+        asm("{\n\t.reg .b64 p, np, e, s, bb, t, u, err;\n\t"
+            "mul.rn.f32x2 p, %2, %3;\n\t"
+            "xor.b64 np, p, 0x8000000080000000;\n\t"
+            "fma.rn.f32x2 e, %2, %3, np;\n\t"
+            "add.rn.f32x2 s, %0, p;\n\t"
+            "sub.rn.f32x2 bb, s, %0;\n\t"
+            "sub.rn.f32x2 t, s, bb;\n\t"
+            "sub.rn.f32x2 t, %0, t;\n\t"
+            "sub.rn.f32x2 u, p, bb;\n\t"
+            "add.rn.f32x2 err, t, u;\n\t"
+            "add.rn.f32x2 e, e, err;\n\t"
+            "add.rn.f32x2 %1, %1, e;\n\t"
+            "mov.b64 %0, s;\n\t}"
+            : "+l"(hi), "+l"(lo)
+            : "l"(a), "l"(b));
+    }
+    // the two lanes' sums, joined by a two-sum
+    __device__ __forceinline__ DotAcc<float> joined() const
+    {
+        DotAcc<float> r;
+        r.hi = lane_x(hi);
+        r.lo = lane_x(lo);
+        DotAcc<float> y;
+        y.hi = lane_y(hi);
+        y.lo = lane_y(lo);
+        r.merge(y);
+        return r;
+    }
+};
+
 // Vectors per block of the Gram-Schmidt sweeps (one CTA reduction each).
 constexpr int kGsBlock = 4;
 

@@ -100,6 +100,23 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
         : "memory");
 }
 
+// The same copy with an L2 eviction-priority hint (a policy from createpolicy).
+__device__ __forceinline__ void bulk_g2s_hint(void *dst, const void *src, uint32_t bytes, uint64_t *bar,
+                                              uint64_t policy)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::"r"(
+            smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar)), "l"(policy)
+        : "memory");
+}
+__device__ __forceinline__ uint64_t l2_evict_last_policy()
+{
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+
 // Wait until phase `parity` of `bar` has completed.  Bounded: false once the
 // CTA's abort flag is set, or after kWaitLimitNs (which sets it).
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort)
@@ -142,67 +159,6 @@ __device__ __forceinline__ int chunk_tiles(int cnt, int v)
 {
     return max(0, min(NW, cnt - NW * v));
 }
-
-// Two adjacent FP32 values as one 64-bit register (lane x = the lower
-// address), and the packed (f32x2) operations on such pairs; each lane is
-// rounded exactly as the scalar instruction would be.
-__device__ __forceinline__ uint64_t lds2(const float *p)
-{
-    uint64_t r;
-    asm volatile("ld.shared.b64 %0, [%1];" : "=l"(r) : "r"(smem_addr(p)));
-    return r;
-}
-__device__ __forceinline__ uint64_t pair_of(float x)
-{
-    uint64_t r;
-    asm("mov.b64 %0, {%1, %1};" : "=l"(r) : "f"(x));
-    return r;
-}
-__device__ __forceinline__ uint64_t fma_x2(uint64_t a, uint64_t b, uint64_t c)
-{
-    uint64_t r;
-    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
-    return r;
-}
-__device__ __forceinline__ float lane_x(uint64_t a) { return __uint_as_float((unsigned)a); }
-__device__ __forceinline__ float lane_y(uint64_t a) { return __uint_as_float((unsigned)(a >> 32)); }
-
-// Two DotAcc<float> (one per lane) in packed registers: per lane the
-// operations of DotAcc<float>::add (p = a b, e = fma(a, b, -p), the two-sum
-// of hi and p, lo += e + err).
-struct PairAcc {
-    uint64_t hi = 0, lo = 0;
-    __device__ __forceinline__ void add(uint64_t a, uint64_t b)
-    {
-        asm("{\n\t.reg .b64 p, np, e, s, bb, t, u, err;\n\t"
-            "mul.rn.f32x2 p, %2, %3;\n\t"
-            "xor.b64 np, p, 0x8000000080000000;\n\t"
-            "fma.rn.f32x2 e, %2, %3, np;\n\t"
-            "add.rn.f32x2 s, %0, p;\n\t"
-            "sub.rn.f32x2 bb, s, %0;\n\t"
-            "sub.rn.f32x2 t, s, bb;\n\t"
-            "sub.rn.f32x2 t, %0, t;\n\t"
-            "sub.rn.f32x2 u, p, bb;\n\t"
-            "add.rn.f32x2 err, t, u;\n\t"
-            "add.rn.f32x2 e, e, err;\n\t"
-            "add.rn.f32x2 %1, %1, e;\n\t"
-            "mov.b64 %0, s;\n\t}"
-            : "+l"(hi), "+l"(lo)
-            : "l"(a), "l"(b));
-    }
-    // the two lanes' sums, joined by a two-sum
-    __device__ __forceinline__ DotAcc<float> joined() const
-    {
-        DotAcc<float> r;
-        r.hi = lane_x(hi);
-        r.lo = lane_x(lo);
-        DotAcc<float> y;
-        y.hi = lane_y(hi);
-        y.lo = lane_y(lo);
-        r.merge(y);
-        return r;
-    }
-};
 
 // Ring slot layout (floats, CH = 2 T per piece): w_{i0+l} at 2 l CH,
 // S w_{i0+l} at (2 l + 1) CH (l < 4), u at 8 CH, its lo word at 9 CH and w_n at
@@ -311,6 +267,7 @@ __global__ void __launch_bounds__(T + 32, 1) gs_stream_kernel(
     if (producer) {
         // ---- the producer warp
         uint32_t stage = 0;
+        const uint64_t keep = l2_evict_last_policy();
         // one stage.  Coefficient sweep (sub = false): chunk v of block b's w_i
         // (piece 2 l) and S w_i (2 l + 1), of u (8), u lo (9) and w_n (10).
         // Subtraction (sub = true): chunk v of block b's w_i (piece 2 l) and,
@@ -344,7 +301,11 @@ __global__ void __launch_bounds__(T + 32, 1) gs_stream_kernel(
             const uint32_t bytes = __reduce_add_sync(0xffffffffu, bq);
             if (lane == 0) mbar_arrive_expect_tx(&full[s], bytes);
             __syncwarp();
-            if (bq) bulk_g2s(ring + (int64_t)s * SLOT + (int64_t)lane * CH, src, bq, &full[s]);
+            if (bq) {
+                // u, its lo word and w_n come again with every block: keep them in L2
+                if (lane >= 8) bulk_g2s_hint(ring + (int64_t)s * SLOT + (int64_t)lane * CH, src, bq, &full[s], keep);
+                else bulk_g2s(ring + (int64_t)s * SLOT + (int64_t)lane * CH, src, bq, &full[s]);
+            }
             __syncwarp();
             ++stage;
         };

@@ -286,8 +286,10 @@ def config_c2(seed: int = 0) -> TBSystem:
     return t
 
 
-def amorphous_system(n_atoms: int, seed: int = 0) -> TBSystem:
-    t = build_tb(amorphous_carbon(n_atoms, seed=seed))
+def amorphous_system(n_atoms: int, seed: int = 0, check_spd: bool = True) -> TBSystem:
+    """Amorphous carbon of n_atoms atoms.  check_spd=False skips the host eigensolve that
+    refuses lambda_min(S) <= 0.05 (the library's setup runs its own SPD check)."""
+    t = build_tb(amorphous_carbon(n_atoms, seed=seed), check_spd=check_spd)
     t.meta.update(name=f"amorphous-{n_atoms}", seed=seed)
     return t
 
@@ -320,10 +322,11 @@ def tiny_system(n_atoms: int, seed: int = 0, radius: float | None = None,
     return t
 
 
-def polymer_system(n_units: int, seed: int = 0, **kw) -> TBSystem:
-    """A fluorene-like chain of n_units units (69 atoms each; see tbsynth.polymer)."""
+def polymer_system(n_units: int, seed: int = 0, check_spd: bool = True, **kw) -> TBSystem:
+    """A fluorene-like chain of n_units units (69 atoms each; see tbsynth.polymer).  check_spd=False
+    skips the host eigensolve of S (the library's setup runs its own SPD check)."""
     from .polymer import polyfluorene
-    t = build_tb(polyfluorene(n_units, seed=seed, **kw))
+    t = build_tb(polyfluorene(n_units, seed=seed, **kw), check_spd=check_spd)
     t.meta.update(name=f"polyfluorene-{n_units}", seed=seed)
     return t
 
