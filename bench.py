@@ -71,7 +71,11 @@ def parse():
                    help="only the polymer-chain batching workload as configured (256 chains, 4..400 units)")
     p.add_argument("--c5", action="store_true",
                    help="only the Poisson serving workload as configured (1,000-200,000 atoms, a sweep of rates)")
-    p.add_argument("--c5-window", type=float, default=60.0)
+    p.add_argument("--c5-window", type=float, default=30.0)
+    p.add_argument("--chain", type=int, default=0,
+                   help="only a per-kernel breakdown of one polymer chain of this many units in regional "
+                        "mode (256-atom regions) at each nu of --chain-nu")
+    p.add_argument("--chain-nu", default="100,300")
     p.add_argument("--large-full", type=int, default=0,
                    help="only the paper-scale structure of this many atoms at nu = 100, every column, in "
                         "65,536-column batches, mixed and FP64 (e.g. 1048576)")
@@ -428,6 +432,10 @@ def main():
         torch.distributed.init_process_group("nccl", device_id=dev)
     m.load()
     m.marnoldi_set_autotune(0 if args.fixed_shapes else 1)
+    if args.chain:
+        print(json.dumps({"metric": "mArnoldi columns/s", "n_gpus": 1, "data": "synthetic",
+                          "chain": chain_breakdown(m, args.chain, [int(x) for x in args.chain_nu.split(",")])}))
+        return
     if args.large_full:
         print(json.dumps({"metric": "mArnoldi columns/s", "n_gpus": 1, "data": "synthetic",
                           "large_full": large_full(m, args.large_full, 256, 65536)}))
@@ -584,6 +592,22 @@ def main():
                            "result": {"E_band_eV": rx["E"], "mu_eV": rx["mu"], "N": rx["N"]}}
             if reg_x == 0:
                 checks[label] = gpu_outputs(m, rx["ctx"], cl, nu_x, pr)
+            if label == "nu100" and pr == 1 and rx["stats"].get("gs", (0, 0.0))[1] > 0:
+                # the Gram-Schmidt kernel's HBM fraction at nu = 100 (support bytes)
+                tc100 = support_counts(t, cl, nu_x, column_m_pad(t.M))
+                by100, _ = gs_algorithmic_support(nu_x, tc100, 4)
+                gs_n, gs_ms = rx["stats"]["gs"]
+                ach100 = by100 * 3 / (gs_ms / 1e3) / 1e9
+                pk = peaks.get("hbm_gbs", 6800.0)
+                r100 = GS_DRAM_PER_ALGORITHMIC.get(("mixed", rx.get("gs_shape")))
+                line[label]["roofline"] = {
+                    "kernel": "gs", "bound": "hbm", "achieved": round(ach100, 3), "peak": round(pk, 3),
+                    "unit": "GB/s", "frac": round(ach100 / pk, 4),
+                    "traffic": round(r100 * by100 * 3 / gs_n) if r100 else None,
+                    "traffic_note": (f"DRAM/algorithmic {r100} of the nu = 30 capture of the same kernel x "
+                                     "algorithmic bytes per launch") if r100 else None,
+                    "gs_shape": list(rx.get("gs_shape") or []), "launches": gs_n,
+                    "avg_launch_ms": round(gs_ms / gs_n, 4)}
             m.marnoldi_destroy(rx["ctx"])
 
     if args.large and world == 1:
@@ -720,7 +744,32 @@ def large_structure(m, n_atoms: int, n_reg: int, batch: int):
     return out
 
 
-def large_full(m, n_atoms: int, n_reg: int, batch: int, n_sample: int = 32):
+def chain_breakdown(m, units: int, nus, n_reg: int = 256, prec: int = 1):
+    """One fluorene-like chain of `units` units in regional mode: every real orbital solved (mu by
+    bisection, kT = 0.1 eV) once per nu after a warm-up, with the per-kernel CUDA-event times."""
+    import torch
+    from tbsynth import polymer_system
+    t = polymer_system(units, seed=3, check_spd=False)
+    out = {"units": units, "atoms": int(t.n_block_rows), "columns": int(t.real_columns().size),
+           "region_atoms": n_reg, "precision": "mixed" if prec else "fp64"}
+    for nu in nus:
+        ctx = m.setup_system(t, prec)
+        m.marnoldi_solve(ctx, t.real_columns()[:512], nu, n_reg, 0.0, KT, mu_fixed=-2.0)   # warm-up
+        m.marnoldi_set_profiling(ctx, True)
+        m.marnoldi_kernel_stats(ctx, reset=True)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        m.marnoldi_solve(ctx, None, nu, n_reg, float(t.n_electrons), KT)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        st = m.marnoldi_kernel_stats(ctx)
+        out[f"nu{nu}"] = {"seconds": round(dt, 3), "columns_per_s": round(t.real_columns().size / dt, 1),
+                          "kernel_ms": {k: round(v[1], 1) for k, v in st.items() if v[1] > 0}}
+        m.marnoldi_destroy(ctx)
+    return out
+
+
+def large_full(m, n_atoms: int, n_reg: int, batch: int, n_sample: int = 32, fp64_batch: int = 32768):
     """The paper-scale configuration in full: every one of the 4 n_atoms columns of amorphous
     carbon at nu = 100 in regional mode (n_reg-atom regions), streamed through the solve in
     batches of `batch` columns, mu by bisection over all of them, densities on the device;
@@ -743,7 +792,10 @@ def large_full(m, n_atoms: int, n_reg: int, batch: int, n_sample: int = 32):
     for prec in (1, 0):
         name = "mixed" if prec else "fp64"
         ctx = m.setup_system(t, prec)
-        m.marnoldi_set_batch(ctx, batch)
+        # FP64 vectors double the batch workspace; beside the per-column state of all
+        # 4,194,304 columns (their pattern rows P_j: about 160 GB) half the batch fits
+        b_prec = batch if prec else fp64_batch
+        m.marnoldi_set_batch(ctx, b_prec)
         m.marnoldi_solve(ctx, np.arange(4096, dtype=np.int64), nu, n_reg, 0.0, KT, mu_fixed=4.0)  # warm-up
         m.marnoldi_set_profiling(ctx, True)
         m.marnoldi_kernel_stats(ctx, reset=True)
@@ -772,13 +824,14 @@ def large_full(m, n_atoms: int, n_reg: int, batch: int, n_sample: int = 32):
         mask = ~np.isnan(ref.rho)
         drho = float(np.abs(rho_h[mask] - ref.rho[mask]).max())
         drhoE = float(np.abs(rhoE_h[mask] - ref.rhoE[mask]).max())
-        out[name] = {"seconds": round(dt, 2), "columns_per_s": round(t.M / dt, 1),
+        out[name] = {"seconds": round(dt, 2), "columns_per_s": round(t.M / dt, 1), "batch_columns": b_prec,
                      "E_band_per_atom_eV": E / n_atoms, "mu_eV": mu, "N": N,
                      "kernel_ms": {k: round(v[1], 1) for k, v in st.items() if v[1] > 0},
                      "gs_hbm_frac_dense_bytes": round(per_col * t.M / (gs_ms / 1e3) / 1e9 / hbm, 3),
                      "eig_fp64_tflops": round(eig_flop / (eig_ms / 1e3) / 1e12, 3),
                      "oracle_sample": {"columns": int(sample.size), "max_abs_drho": drho,
                                        "max_abs_drhoE_eV": drhoE}}
+        print(json.dumps({"partial": name, name: out[name]}), flush=True)
         m.marnoldi_destroy(ctx)
         del rho, rhoE
         torch.cuda.empty_cache()
@@ -912,9 +965,10 @@ def serving(m, t4096, requests: int, workers: int, budget: int, prec: int):
     }
 
 
-def _served(results, t_first=None):
-    """Wall time, latencies (ms) and per-request columns of a set of served results."""
-    first = min(r["t_submit"] for r in results) if t_first is None else t_first
+def _served(results):
+    """Wall time from the first submission to the last result (the server's clock) and the
+    latencies (ms) of a set of served results."""
+    first = min(r["t_submit"] for r in results)
     wall = max(r["t_end"] for r in results) - first
     lat = np.array([r["latency_s"] for r in results]) * 1e3
     return wall, lat
@@ -958,8 +1012,8 @@ def serve_c4(m, workers: int, budget: int, prec: int = 1, n_chains: int = 256, s
             "groups": st["groups"], "largest_group": st["largest_group"], "by_nu": by_nu}
 
 
-def serve_c5(m, workers: int, budget: int, prec: int = 1, window_s: float = 60.0,
-             rates=(1.0, 0.5, 0.25, 0.125), seed: int = 5, pool_sizes: int = 6):
+def serve_c5(m, workers: int, budget: int, prec: int = 1, window_s: float = 30.0,
+             rates=(0.2, 0.1, 0.05), seed: int = 5, pool_sizes: int = 6, deadline_s: float = 900.0):
     """Serving as configured: Poisson arrivals of carbon or polymer structures (50/50) of
     1,000-200,000 atoms (log-uniform; drawn from a pool of `pool_sizes` log-spaced sizes per
     kind), each with its own nu in {30, 100} and kT in {0.05, 0.1, 0.2} eV; global mode up to
@@ -975,6 +1029,8 @@ def serve_c5(m, workers: int, budget: int, prec: int = 1, window_s: float = 60.0
     pool.update({("polymer", q): polymer_system(max(15, int(round(n / 69))), seed=600 + q, check_spd=False)
                  for q, n in enumerate(sizes)})
     gen_s = time.perf_counter() - t0
+    t_begin = time.perf_counter()
+    print(json.dumps({"progress": "pool generated", "seconds": round(gen_s, 1)}), flush=True)
     out = {"config": f"Poisson arrivals, carbon or polymer 50/50, 1,000-200,000 atoms log-uniform "
                      f"(pool of {pool_sizes} sizes per kind), nu from {{30, 100}}, kT from {{0.05, 0.1, 0.2}} eV, "
                      f"global mode up to 4,096 atoms, 256-atom regions above, {'mixed' if prec else 'fp64'}, "
@@ -983,10 +1039,18 @@ def serve_c5(m, workers: int, budget: int, prec: int = 1, window_s: float = 60.0
            "generation_s": round(gen_s, 1), "rates": []}
     with m.Server(workers=workers, hbm_budget_bytes=budget) as srv:
         srv.set_group_limit(16)
-        for sysm in pool.values():     # one solve of each structure class first (kernels, tuning)
-            reg = 0 if sysm.n_block_rows <= 4096 else 256
-            srv.wait(srv.submit_system(sysm, prec, 30, reg, sysm.n_electrons, 0.1))
+        # one solve of each class first (kernel loading, shape tuning): global and regional
+        # mode at both nu, on the smallest structures of each mode
+        small_global = min((v for v in pool.values() if v.n_block_rows <= 4096), key=lambda v: v.n_block_rows)
+        small_reg = min((v for v in pool.values() if v.n_block_rows > 4096), key=lambda v: v.n_block_rows)
+        for sysm, reg in ((small_global, 0), (small_reg, 256)):
+            for nu in (30, 100):
+                srv.wait(srv.submit_system(sysm, prec, nu, reg, sysm.n_electrons, 0.1))
+        print(json.dumps({"progress": "warmed up", "seconds": round(time.perf_counter() - t_begin, 1)}),
+              flush=True)
         for lam in rates:
+            if time.perf_counter() - t_begin > deadline_s:
+                break
             n_req = max(1, rng.poisson(lam * window_s))
             gaps = np.sort(rng.uniform(0.0, window_s, size=n_req))
             reqs = []
@@ -1003,15 +1067,19 @@ def serve_c5(m, workers: int, budget: int, prec: int = 1, window_s: float = 60.0
                 reg = 0 if sysm.n_block_rows <= 4096 else 256
                 ids.append(srv.submit_system(sysm, prec, nu, reg, sysm.n_electrons, kT))
             res = [srv.wait(i) for i in ids]
-            wall, lat = _served(res, t_start)
+            wall, lat = _served(res)   # the server's clock: first submission to last result
             cols = sum(int(s.real_columns().size) for s, _, _ in reqs)
             out["rates"].append({
                 "offered_requests_per_s": lam, "requests": n_req,
                 "offered_columns_per_s": round(cols / window_s, 1),
                 "served_requests_per_s": round(n_req / wall, 3), "served_columns_per_s": round(cols / wall, 1),
                 "drained_s": round(wall, 1), "p50_ms": round(float(np.percentile(lat, 50)), 1),
-                "p99_ms": round(float(np.percentile(lat, 99)), 1)})
+                "p99_ms": round(float(np.percentile(lat, 99)), 1),
+                "atoms": [int(sm.n_block_rows) for sm, _, _ in reqs], "nu": [nu for _, nu, _ in reqs],
+                "latency_s": [round(float(x) / 1e3, 2) for x in lat]})
+            print(json.dumps({"progress": "rate", **out["rates"][-1]}), flush=True)
         out["stats"] = {k: srv.stats()[k] for k in ("groups", "largest_group", "peak_running")}
+    # sustainable: every request of the window served within 25 % past the window
     sustain = [r for r in out["rates"] if r["drained_s"] <= 1.25 * window_s]
     out["sustainable_requests_per_s"] = max((r["offered_requests_per_s"] for r in sustain), default=None)
     return out
