@@ -49,6 +49,26 @@ FP64_PEAK_NOTE = "152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz (nominal 1.25 TFL
 # of u, its lo word and w_n with every block that miss L2 despite their evict-last hint.
 GS_DRAM_PER_ALGORITHMIC = {("mixed", (32, 544)): 1.0475}
 GS_DRAM_KERNEL = {(32, 544): "gs_stream_kernel<512,16384>"}
+# SHA-256 of the sources of each captured kernel; when they differ from the files
+# on disk the capture no longer describes the kernel and no traffic is reported
+GS_DRAM_SOURCES = {(32, 544): {
+    "paper_1307_3218_gb300/csrc/gs_stream.cu": "0821e79122b0023002a45dd9c2d130e88e49f222d911d198377e91f1a4e00d90",
+    "paper_1307_3218_gb300/csrc/gs_common.cuh": "c17924ab36aeabf9b8ba5efafff26274875b1c7d799fc4bfb056719952d4d512"}}
+
+
+def capture_current(shape) -> bool:
+    """True when the sources of the kernel whose DRAM ratio is recorded for `shape` are unchanged."""
+    import hashlib
+    want = GS_DRAM_SOURCES.get(shape)
+    if not want:
+        return False
+    for rel, digest in want.items():
+        try:
+            if hashlib.sha256(open(os.path.join(ROOT, rel), "rb").read()).hexdigest() != digest:
+                return False
+        except OSError:
+            return False
+    return True
 
 
 def parse():
@@ -72,6 +92,8 @@ def parse():
     p.add_argument("--c5", action="store_true",
                    help="only the Poisson serving workload as configured (1,000-200,000 atoms, a sweep of rates)")
     p.add_argument("--c5-window", type=float, default=30.0)
+    p.add_argument("--c5-rates", default="1.0,0.5,0.25,0.125",
+                   help="Poisson arrival rates (requests/s) of the --c5 sweep, highest first")
     p.add_argument("--chain", type=int, default=0,
                    help="only a per-kernel breakdown of one polymer chain of this many units in regional "
                         "mode (256-atom regions) at each nu of --chain-nu")
@@ -448,7 +470,8 @@ def main():
         if args.c4:
             out["c4"] = serve_c4(m, args.serve_workers, budget, prec)
         if args.c5:
-            out["c5"] = serve_c5(m, args.serve_workers, budget, prec, window_s=args.c5_window)
+            out["c5"] = serve_c5(m, args.serve_workers, budget, prec, window_s=args.c5_window,
+                                 rates=tuple(float(x) for x in args.c5_rates.split(",")))
         print(json.dumps(out))
         return
     t, cols = workload(args)
@@ -496,7 +519,7 @@ def main():
         # stored vectors) times the algorithmic bytes per launch
         gs_shape = res.get("gs_shape")
         ratio = (GS_DRAM_PER_ALGORITHMIC.get((args.precision, gs_shape))
-                 if dom == "gs" and not args.region else None)
+                 if dom == "gs" and not args.region and capture_current(gs_shape) else None)
         launches_per_step = nlaunch / steps
         traffic = round(ratio * by / launches_per_step) if ratio and by else None
         roof = {"kernel": dom, "bound": bound, "achieved": round(ach, 3), "peak": round(peak, 3),
@@ -599,7 +622,8 @@ def main():
                 gs_n, gs_ms = rx["stats"]["gs"]
                 ach100 = by100 * 3 / (gs_ms / 1e3) / 1e9
                 pk = peaks.get("hbm_gbs", 6800.0)
-                r100 = GS_DRAM_PER_ALGORITHMIC.get(("mixed", rx.get("gs_shape")))
+                r100 = (GS_DRAM_PER_ALGORITHMIC.get(("mixed", rx.get("gs_shape")))
+                        if capture_current(rx.get("gs_shape")) else None)
                 line[label]["roofline"] = {
                     "kernel": "gs", "bound": "hbm", "achieved": round(ach100, 3), "peak": round(pk, 3),
                     "unit": "GB/s", "frac": round(ach100 / pk, 4),
@@ -1013,7 +1037,7 @@ def serve_c4(m, workers: int, budget: int, prec: int = 1, n_chains: int = 256, s
 
 
 def serve_c5(m, workers: int, budget: int, prec: int = 1, window_s: float = 30.0,
-             rates=(0.2, 0.1, 0.05), seed: int = 5, pool_sizes: int = 6, deadline_s: float = 900.0):
+             rates=(1.0, 0.5, 0.25, 0.125), seed: int = 5, pool_sizes: int = 6, deadline_s: float = 600.0):
     """Serving as configured: Poisson arrivals of carbon or polymer structures (50/50) of
     1,000-200,000 atoms (log-uniform; drawn from a pool of `pool_sizes` log-spaced sizes per
     kind), each with its own nu in {30, 100} and kT in {0.05, 0.1, 0.2} eV; global mode up to

@@ -73,3 +73,13 @@ def test_support_counts_and_gs_bytes(maker, nu):
     for vbytes in (4, 8):
         got, _ = bench.gs_algorithmic_support(nu, tc, vbytes)
         assert got == _gs_bytes(want, nu, vbytes)
+
+
+def test_dram_ratio_belongs_to_the_current_kernel():
+    """The DRAM/algorithmic ratio that bench.py turns into `traffic` was measured on one version of
+    the kernel: every recorded ratio names the sources it was captured from, and they must be the
+    files on disk (else recapture the kernel or drop the entry)."""
+    import bench
+    for (prec, shape) in bench.GS_DRAM_PER_ALGORITHMIC:
+        assert shape in bench.GS_DRAM_KERNEL and shape in bench.GS_DRAM_SOURCES
+        assert bench.capture_current(shape), f"sources of {bench.GS_DRAM_KERNEL[shape]} changed since the capture"
