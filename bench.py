@@ -45,14 +45,15 @@ FP64_PEAK_NOTE = "152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz (nominal 1.25 TFL
 # precision and launch shape (values per thread, threads) of the kernel that was
 # captured; a shape without an entry reports no traffic.  An entry must be
 # re-measured (or removed) whenever its kernel changes.
-# gs_stream_kernel<512,16384>: (2.024254e9 + 0.038177e9) / 1.968918e9; above 1 by the re-reads
-# of u, its lo word and w_n with every block that miss L2 despite their evict-last hint.
-GS_DRAM_PER_ALGORITHMIC = {("mixed", (32, 544)): 1.0475}
-GS_DRAM_KERNEL = {(32, 544): "gs_stream_kernel<512,16384>"}
+# gs_stream_kernel<256,16384,3,2> (shape 64 x 288, two CTAs per SM): (2.363514e9 + 0.038593e9)
+# / 1.968918e9; above 1 by the re-reads of u, its lo word and w_n with every block that miss L2
+# despite their evict-last hint (twice as many columns share L2 as with one CTA per SM).
+GS_DRAM_PER_ALGORITHMIC = {("mixed", (64, 288)): 1.2200}
+GS_DRAM_KERNEL = {(64, 288): "gs_stream_kernel<256,16384,3,2>"}
 # SHA-256 of the sources of each captured kernel; when they differ from the files
 # on disk the capture no longer describes the kernel and no traffic is reported
-GS_DRAM_SOURCES = {(32, 544): {
-    "paper_1307_3218_gb300/csrc/gs_stream.cu": "0821e79122b0023002a45dd9c2d130e88e49f222d911d198377e91f1a4e00d90",
+GS_DRAM_SOURCES = {(64, 288): {
+    "paper_1307_3218_gb300/csrc/gs_stream.cu": "340e6c10e95f7d1e86a82211f1ddcad5ee2a72a0f817bc552caa00582069825d",
     "paper_1307_3218_gb300/csrc/gs_common.cuh": "c17924ab36aeabf9b8ba5efafff26274875b1c7d799fc4bfb056719952d4d512"}}
 
 
@@ -98,6 +99,9 @@ def parse():
                    help="only a per-kernel breakdown of one polymer chain of this many units in regional "
                         "mode (256-atom regions) at each nu of --chain-nu")
     p.add_argument("--chain-nu", default="100,300")
+    p.add_argument("--mixed-vs-fp64", default="",
+                   help="comma-separated nu list: mixed against FP64 on every column of the benchmark "
+                        "structure (density statistics at the FP64 Fermi level) and exit")
     p.add_argument("--large-full", type=int, default=0,
                    help="only the paper-scale structure of this many atoms at nu = 100, every column, in "
                         "65,536-column batches, mixed and FP64 (e.g. 1048576)")
@@ -107,7 +111,9 @@ def parse():
                    help="comma-separated atom counts for the order-N study (regional mode), e.g. "
                         "4096,16384,65536,262144; empty = skip")
     p.add_argument("--fixed-shapes", action="store_true",
-                   help="fixed Gram-Schmidt launch-shape rule instead of the autotuner")
+                   help="fixed Gram-Schmidt launch-shape rule instead of the autotuner (use it under a "
+                        "profiler: the tuner's CUDA-event timings are meaningless when every kernel is "
+                        "serialised and replayed)")
     p.add_argument("--serve-requests", type=int, default=60)
     p.add_argument("--serve-workers", type=int, default=4)
     p.add_argument("--serve-budget-gb", type=float, default=64.0)
@@ -458,6 +464,10 @@ def main():
         print(json.dumps({"metric": "mArnoldi columns/s", "n_gpus": 1, "data": "synthetic",
                           "chain": chain_breakdown(m, args.chain, [int(x) for x in args.chain_nu.split(",")])}))
         return
+    if args.mixed_vs_fp64:
+        for nu in [int(x) for x in args.mixed_vs_fp64.split(",")]:
+            print(json.dumps({"mixed_vs_fp64": mixed_vs_fp64(m, nu)}), flush=True)
+        return
     if args.large_full:
         print(json.dumps({"metric": "mArnoldi columns/s", "n_gpus": 1, "data": "synthetic",
                           "large_full": large_full(m, args.large_full, 256, 65536)}))
@@ -768,6 +778,49 @@ def large_structure(m, n_atoms: int, n_reg: int, batch: int):
     return out
 
 
+def mixed_vs_fp64(m, nu: int):
+    """Every column of the benchmark structure (amorphous carbon, 4,096 atoms, global mode) at `nu`
+    in mixed precision against the FP64 path, the mixed density evaluated at the FP64 Fermi level:
+    energy and count differences and the distribution of |d rho| over all entries, with the
+    worst entry's column and its levels nearest mu."""
+    from tbsynth import config_c2
+    t = config_c2(seed=0)
+    ci = np.asarray(t.col_idx)
+    blk_row = np.repeat(np.arange(t.n_block_rows), np.diff(np.asarray(t.row_ptr)))
+    c = m.setup_system(t, 0)
+    m.marnoldi_solve(c, None, nu, 0, t.n_electrons, KT)
+    E64, mu64, N64 = m.marnoldi_energy(c)
+    r64, rE64 = m.marnoldi_density(c)
+    nue, eps64, _ = m.marnoldi_column_stats(c)
+    m.marnoldi_destroy(c)
+    c = m.setup_system(t, 1)
+    m.marnoldi_solve(c, None, nu, 0, t.n_electrons, KT)
+    E32, mu32, N32 = m.marnoldi_energy(c)
+    m.marnoldi_fermi_at(c, mu64, KT)
+    r32, rE32 = m.marnoldi_density(c)
+    nue32, eps32, _ = m.marnoldi_column_stats(c)
+    shape = m.marnoldi_gs_shape(c)
+    m.marnoldi_destroy(c)
+    d, dE = np.abs(r32 - r64).ravel(), np.abs(rE32 - rE64).ravel()
+    k = int(d.argmax())
+    blk, (a, b) = k // 16, divmod(k % 16, 4)
+    col = 4 * int(ci[blk]) + b            # rho e_j fills column j of the block row
+    lv = eps64[col][:nue[col]]
+    near = np.argsort(np.abs(lv - mu64))[:3]
+    shift = (float(np.abs(np.sort(eps32[col][:nue32[col]]) - np.sort(lv)).max())
+             if nue32[col] == nue[col] else None)
+    return {"nu": nu, "atoms": int(t.n_block_rows), "columns": int(t.M), "gs_shape": list(shape),
+            "dE_band_per_atom_eV": abs(E32 - E64) / t.n_block_rows, "dN": abs(N32 - N64),
+            "dmu_eV": abs(mu32 - mu64), "rho_entries": int(d.size), "max_drho": float(d.max()),
+            "max_drhoE_eV": float(dE.max()), "drho_gt_1e-5": int((d > 1e-5).sum()),
+            "drhoE_gt_1e-4": int((dE > 1e-4).sum()),
+            "drho_p99_9": float(np.quantile(d, 0.999)), "drho_p99_99": float(np.quantile(d, 0.9999)),
+            "worst": {"row_atom": int(blk_row[blk]), "column": col, "rho_fp64": float(r64.ravel()[k]),
+                      "rho_mixed": float(r32.ravel()[k]),
+                      "levels_nearest_mu_eV": [float(lv[q] - mu64) for q in near],
+                      "max_level_shift_eV": shift}}
+
+
 def chain_breakdown(m, units: int, nus, n_reg: int = 256, prec: int = 1):
     """One fluorene-like chain of `units` units in regional mode: every real orbital solved (mu by
     bisection, kT = 0.1 eV) once per nu after a warm-up, with the per-kernel CUDA-event times."""
@@ -941,6 +994,14 @@ def serving(m, t4096, requests: int, workers: int, budget: int, prec: int):
     run(workers, group=16, reqs=small[:16])   # warm-up of this class
     solo = run(workers, group=1, reqs=small)
     grouped = run(workers, group=16, reqs=small)
+    # the same two passes with each request's Krylov build as one CUDA graph
+    os.environ["MARNOLDI_KRYLOV_GRAPH"] = "1"
+    try:
+        run(workers, group=16, reqs=small[:16])
+        solo_g = run(workers, group=1, reqs=small)
+        grouped_g = run(workers, group=16, reqs=small)
+    finally:
+        os.environ.pop("MARNOLDI_KRYLOV_GRAPH", None)
     ncols_small = sum(c.real_columns().size for c, _ in small)
     # uneven polymer chains: fluorene-like units (69 atoms each), lengths
     # log-uniform in 4..59 units (the global-mode limit of 4,096 atoms), nu 30
@@ -966,7 +1027,12 @@ def serving(m, t4096, requests: int, workers: int, budget: int, prec: int):
                  "grouped": {"columns_per_s": round(ncols_small / grouped["wall"], 1),
                              "p50_ms": round(float(np.percentile(grouped["lat"], 50)), 2),
                              "groups": grouped["stats"]["groups"],
-                             "largest_group": grouped["stats"]["largest_group"]}}
+                             "largest_group": grouped["stats"]["largest_group"]},
+                 "krylov_graph": {
+                     "one_by_one": {"columns_per_s": round(ncols_small / solo_g["wall"], 1),
+                                    "p50_ms": round(float(np.percentile(solo_g["lat"], 50)), 2)},
+                     "grouped": {"columns_per_s": round(ncols_small / grouped_g["wall"], 1),
+                                 "p50_ms": round(float(np.percentile(grouped_g["lat"], 50)), 2)}}}
     return {
         "small_molecules": out_small,
         "polymer_chains": out_poly,

@@ -244,9 +244,22 @@ int marnoldi_solved_shape(marnoldi_ctx *ctx, int64_t *ncols, int *nu);
  *   marnoldi_kernel_stats: for kind = 0 .. marnoldi_kernel_kinds()-1, the kernel
  *     name, the number of launches and the summed event time (ms, profiling
  *     only) since the last reset; reset != 0 clears them after reading.
+ *   marnoldi_set_krylov_graph: 1 = run the Krylov build of every batch (support
+ *     search, initial vectors, nu steps of product and Gram-Schmidt: 2 nu + 2
+ *     or 2 nu + 3 kernels) as one CUDA graph, captured from the context's
+ *     stream and launched once; the executable graph is kept in the context and
+ *     updated in place for the next batch or solve with the same nu and mode.
+ *     Not while profiling is on (kernels are then launched and timed one by
+ *     one).  The same kernels with the same arguments run in the same order,
+ *     so results equal the direct launches bit for bit.  The default for a new
+ *     context is 1 when the environment variable MARNOLDI_KRYLOV_GRAPH is "1",
+ *     else 0.  MARNOLDI_EINVAL for other values.
+ *   marnoldi_krylov_graph_launches: graphs launched by this context so far.
  */
 int marnoldi_set_batch(marnoldi_ctx *ctx, int64_t batch_columns);
 int marnoldi_set_profiling(marnoldi_ctx *ctx, int enable);
+int marnoldi_set_krylov_graph(marnoldi_ctx *ctx, int enable);
+int marnoldi_krylov_graph_launches(const marnoldi_ctx *ctx, int64_t *graph_launches);
 int marnoldi_kernel_kinds(void);
 int marnoldi_kernel_stats(marnoldi_ctx *ctx, int kind, const char **name, int64_t *launches,
                           double *ms, int reset);
@@ -291,13 +304,14 @@ int marnoldi_set_member_temperatures(marnoldi_ctx *ctx, int n_members, const dou
  *   marnoldi_set_autotune: mode 0 (default, also when MARNOLDI_AUTOTUNE is
  *     unset or not "1") uses a fixed rule: 256 threads per CTA up to m = 4096,
  *     512 for FP32 vectors up to 8192, the streamed kernel for longer FP32
- *     vectors (reported as 32 values per thread and 544 threads: 512
+ *     vectors (reported as 64 values per thread and 288 threads: 256
  *     threads and a producer warp that copies the vectors into shared memory
  *     with the bulk-copy engine), else 1024, values per thread covering m.
  *     Mode 1: the first solve of each (precision, nu, global/regional, padded
  *     vector length) times every shape with the same padded length (threads
- *     256, 512 or 1024; for FP32 vectors of 16,384 entries also the
- *     streamed kernel) on its first 1,216 columns, keeps the fastest for the
+ *     256, 512 or 1024; for FP32 vectors of 16,384 entries also the two
+ *     streamed shapes, 64 x 288 and 32 x 544: 512 consumer threads and the
+ *     producer, one CTA per SM) on its first 1,216 columns, keeps the fastest for the
  *     rest of the process and, when MARNOLDI_TUNE_CACHE names a file, appends
  *     it there and reads earlier choices from it.  Shapes change the order of
  *     the kernel's partial sums, so results may differ by rounding between

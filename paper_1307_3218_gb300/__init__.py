@@ -18,6 +18,7 @@ from .marnoldi import (MARNOLDI_FP64, MARNOLDI_MIXED, Context, MarnoldiError, Se
                        union_of,
                        marnoldi_kernel_stats, marnoldi_last_error, marnoldi_set_allocator,
                        marnoldi_set_batch, marnoldi_set_profiling, marnoldi_setup,
+                       marnoldi_set_krylov_graph, marnoldi_krylov_graph_launches,
                        marnoldi_solve, marnoldi_solved_shape, setup_system, use_torch_allocator)
 
 __all__ = [
@@ -29,6 +30,7 @@ __all__ = [
     "marnoldi_set_members",
     "union_of",
     "marnoldi_last_error", "marnoldi_set_allocator", "marnoldi_set_batch",
-    "marnoldi_set_profiling", "marnoldi_setup", "marnoldi_solve", "marnoldi_solved_shape",
+    "marnoldi_set_profiling", "marnoldi_set_krylov_graph", "marnoldi_krylov_graph_launches",
+    "marnoldi_setup", "marnoldi_solve", "marnoldi_solved_shape",
     "setup_system", "use_torch_allocator",
 ]

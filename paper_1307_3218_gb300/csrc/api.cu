@@ -230,6 +230,14 @@ struct marnoldi_ctx {
     RegionMaps rm{};
     double region_rs = 0.0;
 
+    // the Krylov build of a batch as one CUDA graph (marnoldi_set_krylov_graph):
+    // captured from the stream on every batch, the executable graph kept and
+    // updated in place while the topology (nu, mode) stays the same
+    bool krylov_graph = false;
+    cudaGraphExec_t kexec = nullptr;
+    cudaStream_t cap_stream = nullptr;   // private stream the graph is captured from
+    int64_t graph_launches = 0;
+
     // instrumentation
     int64_t launches[KK_NKINDS] = {};
     double ms[KK_NKINDS] = {};
@@ -362,6 +370,55 @@ int launch(marnoldi_ctx *c, int kind, F &&f)
         c->pending.push_back({kind, {e0, e1}});
     }
     c->launches[kind]++;
+    return MARNOLDI_OK;
+}
+
+// Run `body` (stream work on c->stream only) as one CUDA graph: capture it
+// from a private stream of the context (the context's own stream may be the
+// legacy default stream, which cannot be captured), update the kept
+// executable graph in place (or instantiate one when the topology changed)
+// and launch it on the context's stream, after the work already queued there.
+// A failed launch inside the body ends the capture and returns the body's
+// error.
+template <class F>
+int run_as_graph(marnoldi_ctx *c, F &&body)
+{
+    cudaError_t e;
+    if (!c->cap_stream && (e = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking)) != cudaSuccess) {
+        c->cap_stream = nullptr;
+        return fail_cuda(c, e, "Krylov graph stream");
+    }
+    if ((e = cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeRelaxed)) != cudaSuccess)
+        return fail_cuda(c, e, "Krylov graph capture");
+    const cudaStream_t own = c->stream;
+    c->stream = c->cap_stream;
+    const int r = body();
+    c->stream = own;
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(c->cap_stream, &g);
+    if (r || e != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        return r ? r : fail_cuda(c, e, "Krylov graph capture");
+    }
+    bool updated = false;
+    if (c->kexec) {
+        cudaGraphExecUpdateResultInfo info;
+        updated = cudaGraphExecUpdate(c->kexec, g, &info) == cudaSuccess;
+        if (!updated) {
+            cudaGetLastError();
+            cudaGraphExecDestroy(c->kexec);
+            c->kexec = nullptr;
+        }
+    }
+    if (!updated && (e = cudaGraphInstantiate(&c->kexec, g, 0)) != cudaSuccess) {
+        c->kexec = nullptr;
+        cudaGraphDestroy(g);
+        return fail_cuda(c, e, "Krylov graph instantiation");
+    }
+    cudaGraphDestroy(g);
+    if ((e = cudaGraphLaunch(c->kexec, c->stream)) != cudaSuccess) return fail_cuda(c, e, "Krylov graph launch");
+    c->graph_launches++;
     return MARNOLDI_OK;
 }
 
@@ -782,6 +839,8 @@ void marnoldi_destroy(marnoldi_ctx *c)
         c->events.push_back(p.second.second);
     }
     for (auto e : c->events) cudaEventDestroy(e);
+    if (c->kexec) cudaGraphExecDestroy(c->kexec);
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     cudaStreamSynchronize(c->stream);
     cudaGetLastError();
     delete c;
@@ -888,6 +947,10 @@ int marnoldi::setup_with_allocator(marnoldi_ctx **out, int64_t n_block_rows, con
         return fail(nullptr, MARNOLDI_EINVAL, "row_ptr[n_block_rows] = %lld is not a valid block count", (long long)nnzb);
 
     marnoldi_ctx *c = new marnoldi_ctx();
+    {
+        const char *g = getenv("MARNOLDI_KRYLOV_GRAPH");
+        c->krylov_graph = g && g[0] == '1';
+    }
     c->prec = precision;
     c->nbr = n_block_rows;
     c->nnzb = nnzb;
@@ -996,6 +1059,20 @@ int marnoldi_set_batch(marnoldi_ctx *c, int64_t batch_columns)
 {
     if (!c || batch_columns < 0) return MARNOLDI_EINVAL;
     c->batch_override = batch_columns;
+    return MARNOLDI_OK;
+}
+
+int marnoldi_set_krylov_graph(marnoldi_ctx *c, int enable)
+{
+    if (!c || (enable != 0 && enable != 1)) return MARNOLDI_EINVAL;
+    c->krylov_graph = enable == 1;
+    return MARNOLDI_OK;
+}
+
+int marnoldi_krylov_graph_launches(const marnoldi_ctx *c, int64_t *graph_launches)
+{
+    if (!c || !graph_launches) return MARNOLDI_EINVAL;
+    *graph_launches = c->graph_launches;
     return MARNOLDI_OK;
 }
 
@@ -1444,7 +1521,9 @@ int marnoldi_solve(marnoldi_ctx *c, const int64_t *columns, int64_t ncols, int n
         }
         {
             const Phase ph("krylov");   // support search, initial vectors, nu steps of SpMM + Gram-Schmidt
-            if ((rc = build(kb))) return rc;
+            // as one graph when asked for (not while kernels are timed one by one)
+            if ((rc = c->krylov_graph && !c->profile ? run_as_graph(c, [&] { return build(kb); }) : build(kb)))
+                return rc;
         }
         if (c->proj_vec) {
             if ((rc = launch(c, KK_EIGSTATE, [&] {

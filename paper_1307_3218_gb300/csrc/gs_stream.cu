@@ -16,14 +16,14 @@
 // What differs is how the vectors reach the arithmetic.  gs_kernel loads them
 // with the CTA's own threads, so its loads and its reductions alternate in
 // step and HBM idles during every block reduction.  Here a producer warp
-// feeds a ring of kRing slots; a slot holds one chunk (1,024 entries, 32
-// tiles of 32) of the four vectors w_i and the four S w_i of a block and of
-// u = H w_n, its lo word and w_n, copied by cp.async.bulk straight from each
-// vector's support prefix (the vectors are stored in the column's hop order,
-// so a support is one contiguous prefix) and signalled on the slot's "full"
-// mbarrier with the bytes it carries.  16 consumer warps wait on "full",
-// compute, and release the slot on its "empty" mbarrier (one arrival per
-// warp); the producer refills a slot once it is empty, so copies of later
+// feeds a ring of R slots; a slot holds one chunk (2 T entries, T / 16 tiles
+// of 32, for T consumer threads) of the four vectors w_i and the four S w_i
+// of a block and of u = H w_n, its lo word and w_n, copied by cp.async.bulk
+// straight from each vector's support prefix (the vectors are stored in the
+// column's hop order, so a support is one contiguous prefix) and signalled on
+// the slot's "full" mbarrier with the bytes it carries.  The consumer warps
+// wait on "full", compute, and release the slot on its "empty" mbarrier (one
+// arrival per warp); the producer refills a slot once it is empty, so copies of later
 // chunks stay in flight while the consumers finish a block and while they
 // run the scalar step.  A consumer thread takes two adjacent entries of each
 // vector with one 64-bit shared-memory load and runs both through one packed
@@ -31,12 +31,14 @@
 // error-free arithmetic.  The block sums need no CTA barrier: the last warp
 // to finish a block adds up the warps' partial sums.  u, its lo word and w_n
 // come again with every block (from L2: they are the column's most recently
-// used data), so the whole of shared memory goes to the ring.  The
+// used data), so the ring takes all the dynamic shared memory.  The
 // subtraction runs chunk by chunk: for each chunk the blocks' w_i, last block
 // first, with u, each value's (hi, lo) sum in registers and stored once its
 // chunk is done.
 //
-// Shared memory: the ring, 4 slots of 11 pieces of 1,024 floats (176 KB).
+// Shapes: 512 consumer threads with a ring of 4 slots of 11 pieces of 1,024
+// floats (176 KB, one CTA per SM), or 256 consumer threads with 3 slots of 11
+// pieces of 512 floats (66 KB, two CTAs per SM).
 //
 // Every wait is bounded: an mbarrier wait gives up after kWaitLimitNs of the
 // global timer, sets the CTA's abort flag (later waits then return at once, so
@@ -47,7 +49,6 @@
 namespace marnoldi {
 namespace {
 
-constexpr int kRing = 4;                          // ring slots
 constexpr unsigned long long kWaitLimitNs = 2000000000ull;   // 2 s per wait
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p)
@@ -165,19 +166,19 @@ __device__ __forceinline__ int chunk_tiles(int cnt, int v)
 // 10 CH, each the chunk of positions v CH .. v CH + CH - 1 (only the live
 // tiles are copied).
 constexpr int kSlotPieces = 2 * kGsBlock + 3;
-constexpr int kStreamT = 512;                   // consumer threads (16 warps), 2 values each per chunk
 constexpr int64_t kStreamM = 16384;             // vector length (m_pad)
-constexpr int kStreamVPT = (int)(kStreamM / kStreamT);   // values per consumer thread: 32
-constexpr int kPartBufs = kRing + 2;            // per-block partial-sum buffers (see below)
 
-// Dynamic shared memory of the kernel below: the ring.
-template <int T>
+// Dynamic shared memory of the kernel below: the ring of R slots.
+template <int T, int R>
 constexpr size_t gs_stream_smem()
 {
-    return (size_t)kRing * kSlotPieces * 2 * T * sizeof(float);
+    return (size_t)R * kSlotPieces * 2 * T * sizeof(float);
 }
 
-// T consumer threads (NW = T / 32 warps); warp NW is the producer.  A chunk v
+// T consumer threads (NW = T / 32 warps); warp NW is the producer; R ring
+// slots; MINB CTAs share an SM (two, when the ring and the scalar arrays fit
+// in half of shared memory, so that one CTA's block sums and scalar step
+// overlap the other's copies).  A chunk v
 // is positions v CH .. v CH + CH - 1 (CH = 2 T = 32 NW, tiles 32 v .. 32 v + 31);
 // thread tid takes positions v CH + 2 tid and + 1 (tile 32 v + tid / 16), as a
 // pair in one 64-bit register, and the two lanes of the packed instructions are
@@ -188,7 +189,7 @@ constexpr size_t gs_stream_smem()
 //     that holds live tiles of the block: w_i, S w_i (i in b), u, u lo, w_n
 //   subtraction: for each chunk v of u's support, each pair of blocks b, b - 1
 //     (last first) that hold live tiles in chunk v: w_i (i in b and b - 1),
-//     and u, u lo with the last block.  The first kRing of them are copied
+//     and u, u lo with the last block.  The first R of them are copied
 //     before the scalar step
 //     (when a subtraction follows at all: need_w), and the consumers drain
 //     them if the column stops there.
@@ -197,11 +198,11 @@ constexpr size_t gs_stream_smem()
 // lanes, reduces the 12 sums over its threads (warp_scatter) and stores them in
 // the block's partial buffer; the warp that arrives last (a ticket in shared
 // memory) adds the warps' partials in warp order and stores the totals.  A warp
-// runs at most kRing stages (so kRing blocks) ahead of the slowest one, since
-// a slot is refilled only when every warp has released it; kPartBufs = kRing
-// + 2 buffers, used in turn, are therefore never overwritten while read.
-template <int T, int64_t MP>
-__global__ void __launch_bounds__(T + 32, 1) gs_stream_kernel(
+// runs at most R stages (so R blocks) ahead of the slowest one, since a slot
+// is refilled only when every warp has released it; R + 2 buffers, used in
+// turn, are therefore never overwritten while read.
+template <int T, int64_t MP, int R, int MINB>
+__global__ void __launch_bounds__(T + 32, MINB) gs_stream_kernel(
     float *__restrict__ K, const float *__restrict__ SK, const float *__restrict__ U,
     const float *__restrict__ Ulo, double *__restrict__ Hsub, double *__restrict__ Lsub,
     double *__restrict__ scale, double *__restrict__ cn2, int *__restrict__ status,
@@ -212,6 +213,7 @@ __global__ void __launch_bounds__(T + 32, 1) gs_stream_kernel(
     constexpr int TPC = CH / 32;              // tiles per chunk
     constexpr int kB = kGsBlock;
     constexpr int SLOT = kSlotPieces * CH;    // floats per ring slot
+    constexpr int kPartBufs = R + 2;          // per-block partial-sum buffers
     static_assert(MP % CH == 0, "whole chunks");
     const int c = blockIdx.x;
     if (status[c] != 0) return;
@@ -219,7 +221,7 @@ __global__ void __launch_bounds__(T + 32, 1) gs_stream_kernel(
     const bool producer = warp == NW;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     float *ring = reinterpret_cast<float *>(smem_raw);
-    __shared__ __align__(8) uint64_t full[kRing], empty[kRing];
+    __shared__ __align__(8) uint64_t full[R], empty[R];
     __shared__ double part[kPartBufs][3 * kB][NW];
     __shared__ int ticket[kPartBufs];
     __shared__ double ssc[kMaxNu];
@@ -242,7 +244,7 @@ __global__ void __launch_bounds__(T + 32, 1) gs_stream_kernel(
     }
     if (tid < kPartBufs) ticket[tid] = 0;
     if (tid == T) {
-        for (int s = 0; s < kRing; ++s) {
+        for (int s = 0; s < R; ++s) {
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], NW);
         }
@@ -260,7 +262,7 @@ __global__ void __launch_bounds__(T + 32, 1) gs_stream_kernel(
     int nsub = 0;
     for (int v = 0; v < nch_u; ++v)
         for (int b = nb1 - 1; b >= 0 && block_chunks(b) > v; b -= 2) ++nsub;
-    const int npre = need_w ? min(kRing, nsub) : 0;
+    const int npre = need_w ? min(R, nsub) : 0;
     const float *ug = U + (int64_t)c * MP;
     const float *ulg = Ulo + (int64_t)c * MP;
 
@@ -275,8 +277,8 @@ __global__ void __launch_bounds__(T + 32, 1) gs_stream_kernel(
         // last block.  Lane q sizes piece q, lane 0 arms the slot's barrier
         // with their sum, then each lane copies its piece.
         auto issue = [&](int b, int v, bool sub, bool two) {
-            const int s = (int)(stage % kRing);
-            mbar_wait(&empty[s], ((stage / kRing) & 1) ^ 1, abort);
+            const int s = (int)(stage % R);
+            mbar_wait(&empty[s], ((stage / R) & 1) ^ 1, abort);
             const int64_t off = (int64_t)v * CH;
             const bool with_u = !sub || b == nb1 - 1;
             int vec = -1;      // the stored vector of piece `lane`, if any
@@ -328,11 +330,11 @@ __global__ void __launch_bounds__(T + 32, 1) gs_stream_kernel(
 
     // ---- consumers: coefficient sweep
     uint32_t stage = 0;
-    int slot = 0;              // stage % kRing
-    uint32_t phase = 0;        // (stage / kRing) & 1
+    int slot = 0;              // stage % R
+    uint32_t phase = 0;        // (stage / R) & 1
     auto next = [&] {
         ++stage;
-        if (++slot == kRing) {
+        if (++slot == R) {
             slot = 0;
             phase ^= 1u;
         }
@@ -487,8 +489,8 @@ __global__ void __launch_bounds__(T + 32, 1) gs_stream_kernel(
         // is released (the next phase of each slot's "full" barrier), and flag
         // the column
         if (tid == 0) {
-            for (int s = 0; s < kRing; ++s) {
-                const uint32_t uses = stage > (uint32_t)s ? (stage - (uint32_t)s + kRing - 1) / kRing : 0;
+            for (int s = 0; s < R; ++s) {
+                const uint32_t uses = stage > (uint32_t)s ? (stage - (uint32_t)s + R - 1) / R : 0;
                 mbar_wait_for(&full[s], uses & 1, 1000000ull);
             }
             status[c] = 3;
@@ -498,24 +500,37 @@ __global__ void __launch_bounds__(T + 32, 1) gs_stream_kernel(
 
 }  // namespace
 
+// The two streamed shapes, as (values per consumer thread, threads per CTA):
+// {32, 544}: 512 consumer threads and the producer, a ring of 4 slots of 44 KB,
+// one CTA per SM; {64, 288}: 256 consumer threads and the producer, a ring of
+// 3 slots of 22 KB, two CTAs per SM.
 bool gs_stream_shape(const ColumnShape &s, int prec)
 {
-    return prec == 1 && s.vpt == kStreamVPT && s.threads == kStreamT + 32 && s.m_pad == kStreamM;
+    return prec == 1 && s.m_pad == kStreamM &&
+           ((s.vpt == 32 && s.threads == 544) || (s.vpt == 64 && s.threads == 288));
 }
 
-cudaError_t launch_gs_stream(const KrylovBatch &b, int n, int need_w, double tau, cudaStream_t s)
+namespace {
+template <int T, int R, int MINB>
+cudaError_t launch_stream_shape(const KrylovBatch &b, int n, int need_w, double tau, cudaStream_t s)
 {
-    constexpr int T = kStreamT;
     constexpr int64_t MP = kStreamM;
-    if (!gs_stream_shape(b.shape, b.prec) || (int64_t)b.ntile * 32 < MP || !b.tcnt || !b.Lsub || !b.Ulo)
-        return cudaErrorInvalidValue;
-    const size_t smem = gs_stream_smem<T>();
-    cudaError_t e = allow_dynamic_smem((const void *)gs_stream_kernel<T, MP>, smem);
+    const size_t smem = gs_stream_smem<T, R>();
+    cudaError_t e = allow_dynamic_smem((const void *)gs_stream_kernel<T, MP, R, MINB>, smem);
     if (e != cudaSuccess) return e;
-    gs_stream_kernel<T, MP><<<b.nb, T + 32, smem, s>>>(
+    gs_stream_kernel<T, MP, R, MINB><<<b.nb, T + 32, smem, s>>>(
         (float *)b.K, (const float *)b.SK, (const float *)b.U, (const float *)b.Ulo, b.Hsub, b.Lsub, b.scale,
         b.cn2, b.status, b.nu_eff, b.tcnt, n, b.nu, need_w, tau * tau);
     return cudaGetLastError();
+}
+}  // namespace
+
+cudaError_t launch_gs_stream(const KrylovBatch &b, int n, int need_w, double tau, cudaStream_t s)
+{
+    if (!gs_stream_shape(b.shape, b.prec) || (int64_t)b.ntile * 32 < kStreamM || !b.tcnt || !b.Lsub || !b.Ulo)
+        return cudaErrorInvalidValue;
+    if (b.shape.threads == 288) return launch_stream_shape<256, 3, 2>(b, n, need_w, tau, s);
+    return launch_stream_shape<512, 4, 1>(b, n, need_w, tau, s);
 }
 
 MARNOLDI_CHECK_TAKE(gs_stream)

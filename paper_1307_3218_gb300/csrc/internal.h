@@ -80,9 +80,9 @@ ColumnShape column_shape(int64_t m, int prec);
 // were written.
 constexpr int kMaxShapes = 4;
 int column_shape_candidates(int64_t m_pad, int prec, ColumnShape *out);
-// The shape of the streamed Gram-Schmidt kernel (gs_stream.cu): FP32
-// vectors of m_pad = 16,384, 512 consumer threads of 32 values and a
-// producer warp: {vpt 32, threads 544}.
+// The shapes of the streamed Gram-Schmidt kernel (gs_stream.cu), FP32
+// vectors of m_pad = 16,384 and a producer warp: 512 consumer threads of 32
+// values, {vpt 32, threads 544}, or 256 of 64 values, {vpt 64, threads 288}.
 bool gs_stream_shape(const ColumnShape &s, int prec);
 
 // ---------------------------------------------------------------- Krylov build

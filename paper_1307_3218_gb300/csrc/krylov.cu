@@ -38,13 +38,14 @@ const char *kernel_name(int kind)
 // Vectors up to 4096 entries run 256-thread CTAs (several columns share an SM
 // and overlap each other's reductions).  Longer FP32 vectors up to 8192
 // entries run 512-thread CTAs of 16 values per thread (two per SM); longer
-// FP32 vectors run the streamed kernel (gs_stream.cu: 512 consumer threads of
-// 32 values and a producer warp, shape {32, 544}); the rest run 1024-thread
-// CTAs.  VPT is the power of two that covers m.
+// FP32 vectors run the streamed kernel (gs_stream.cu) with 256 consumer
+// threads of 64 values and a producer warp, two CTAs per SM (shape {64, 288};
+// {32, 544}, one CTA of 512 consumer threads per SM, is the other streamed
+// shape); the rest run 1024-thread CTAs.  VPT is the power of two that covers m.
 ColumnShape column_shape(int64_t m, int prec)
 {
     if (prec == 1 && m > 4096 && m <= 8192) return ColumnShape{16, 512, 8192};
-    if (prec == 1 && m > 8192 && m <= 16384) return ColumnShape{32, 544, 16384};   // gs_stream.cu
+    if (prec == 1 && m > 8192 && m <= 16384) return ColumnShape{64, 288, 16384};   // gs_stream.cu
     const int T = m <= 4096 ? 256 : 1024;
     int v = 1;
     while (v < 16 && (int64_t)v * T < m) v *= 2;
@@ -57,8 +58,8 @@ int column_shape_candidates(int64_t m_pad, int prec, ColumnShape *out)
     for (int T : {256, 512, 1024})
         for (int v = 1; v <= 16; v *= 2)
             if ((int64_t)v * T == m_pad) out[n++] = ColumnShape{v, T, m_pad};
-    const ColumnShape st{32, 544, 16384};
-    if (m_pad == st.m_pad && gs_stream_shape(st, prec)) out[n++] = st;
+    for (const ColumnShape st : {ColumnShape{32, 544, 16384}, ColumnShape{64, 288, 16384}})
+        if (m_pad == st.m_pad && gs_stream_shape(st, prec)) out[n++] = st;
     return n;
 }
 

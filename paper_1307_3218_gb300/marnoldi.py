@@ -87,6 +87,8 @@ def load(path: str | None = None):
         "marnoldi_solved_shape": (i32, [P, P, P]),
         "marnoldi_set_batch": (i32, [P, i64]),
         "marnoldi_set_profiling": (i32, [P, i32]),
+        "marnoldi_set_krylov_graph": (i32, [P, i32]),
+        "marnoldi_krylov_graph_launches": (i32, [P, P]),
         "marnoldi_kernel_kinds": (i32, []),
         "marnoldi_kernel_stats": (i32, [P, i32, C.POINTER(C.c_char_p), C.POINTER(i64),
                                         C.POINTER(d), i32]),
@@ -416,6 +418,16 @@ def marnoldi_column_stats(ctx: Context) -> tuple[np.ndarray, np.ndarray, np.ndar
 
 def marnoldi_set_batch(ctx: Context, batch_columns: int) -> None:
     _check(load().marnoldi_set_batch(ctx.handle, int(batch_columns)), ctx)
+
+
+def marnoldi_set_krylov_graph(ctx: Context, enable: bool) -> None:
+    _check(load().marnoldi_set_krylov_graph(ctx.handle, int(bool(enable))), ctx)
+
+
+def marnoldi_krylov_graph_launches(ctx: Context) -> int:
+    n = C.c_int64()
+    _check(load().marnoldi_krylov_graph_launches(ctx.handle, C.byref(n)), ctx)
+    return n.value
 
 
 def marnoldi_set_profiling(ctx: Context, enable: bool) -> None:

@@ -78,6 +78,47 @@ def test_c2_every_column_nu30(m, c2, ref30, prec):
         assert drhoE <= 1e-4
 
 
+SHAPE_CHILD = """
+import sys, numpy as np, paper_1307_3218_gb300 as m
+from tbsynth import config_c2
+t = config_c2(seed=0)
+ctx = m.setup_system(t, 1)
+m.marnoldi_solve(ctx, None, 30, 0, t.n_electrons, %r)
+rho, rhoE = m.marnoldi_density(ctx)
+E, mu, N = m.marnoldi_energy(ctx)
+np.savez(sys.argv[1], rho=rho, rhoE=rhoE, E=E, mu=mu, N=N, shape=np.array(m.marnoldi_gs_shape(ctx)))
+""" % KT
+
+
+@pytest.mark.parametrize("shape", [(32, 544), (16, 1024)])
+def test_c2_every_column_nu30_other_shapes(m, c2, ref30, shape, tmp_path):
+    """The other Gram-Schmidt launch shapes of 16,384-entry FP32 vectors (the streamed kernel with
+    512 consumer threads and one CTA per SM, and the 1,024-thread kernel without a ring; the
+    default is the streamed kernel with 256 consumer threads and two CTAs per SM), chosen through
+    a tune cache in a child process, against the full oracle at the mixed tolerances."""
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    cache = tmp_path / "shapes.txt"
+    cache.write_text(f"1 30 0 16384 {shape[0]} {shape[1]}\n")
+    out = tmp_path / "g.npz"
+    env = dict(os.environ, MARNOLDI_AUTOTUNE="1", MARNOLDI_TUNE_CACHE=str(cache), PYTHONPATH=root)
+    r = subprocess.run([sys.executable, "-c", SHAPE_CHILD, str(out)], env=env, cwd=root, capture_output=True,
+                       text=True, timeout=900)
+    assert r.returncode == 0, r.stderr[-2000:]
+    g = np.load(out)
+    assert tuple(g["shape"]) == shape
+    dE_atom = abs(float(g["E"]) - ref30.E_band) / c2.n_block_rows
+    drho = float(np.abs(g["rho"] - ref30.rho).max())
+    drhoE = float(np.abs(g["rhoE"] - ref30.rhoE).max())
+    print(f"C2 nu=30 mixed shape={shape}: dE/atom={dE_atom:.3e} eV drho={drho:.3e} drhoE={drhoE:.3e} eV")
+    assert dE_atom <= 1e-6
+    assert abs(float(g["N"]) - ref30.N) <= 1e-8 * c2.n_electrons
+    assert drho <= 1e-5
+    assert drhoE <= 1e-4
+
+
 def column_band_energy(eps, w, nu_eff, mu):
     """Each column's share of E_band: sum_a 2 f((eps_a - mu) / kT) eps_a w_a over its valid levels."""
     valid = np.arange(eps.shape[1])[None, :] < nu_eff[:, None]
