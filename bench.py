@@ -48,13 +48,16 @@ FP64_PEAK_NOTE = "152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz (nominal 1.25 TFL
 # gs_stream_kernel<256,16384,3,2> (shape 64 x 288, two CTAs per SM): (2.363514e9 + 0.038593e9)
 # / 1.968918e9; above 1 by the re-reads of u, its lo word and w_n with every block that miss L2
 # despite their evict-last hint (twice as many columns share L2 as with one CTA per SM).
-GS_DRAM_PER_ALGORITHMIC = {("mixed", (64, 288)): 1.2200}
-GS_DRAM_KERNEL = {(64, 288): "gs_stream_kernel<256,16384,3,2>"}
+# gs_stream_kernel<512,16384,4,1> (shape 32 x 544, one CTA per SM; chosen through a tune cache):
+# (2.024088e9 + 0.038078e9) / 1.968918e9.
+GS_DRAM_PER_ALGORITHMIC = {("mixed", (64, 288)): 1.2200, ("mixed", (32, 544)): 1.0474}
+GS_DRAM_KERNEL = {(64, 288): "gs_stream_kernel<256,16384,3,2>", (32, 544): "gs_stream_kernel<512,16384,4,1>"}
 # SHA-256 of the sources of each captured kernel; when they differ from the files
 # on disk the capture no longer describes the kernel and no traffic is reported
-GS_DRAM_SOURCES = {(64, 288): {
+_GS_STREAM_SOURCES = {
     "paper_1307_3218_gb300/csrc/gs_stream.cu": "340e6c10e95f7d1e86a82211f1ddcad5ee2a72a0f817bc552caa00582069825d",
-    "paper_1307_3218_gb300/csrc/gs_common.cuh": "c17924ab36aeabf9b8ba5efafff26274875b1c7d799fc4bfb056719952d4d512"}}
+    "paper_1307_3218_gb300/csrc/gs_common.cuh": "c17924ab36aeabf9b8ba5efafff26274875b1c7d799fc4bfb056719952d4d512"}
+GS_DRAM_SOURCES = {(64, 288): _GS_STREAM_SOURCES, (32, 544): _GS_STREAM_SOURCES}
 
 
 def capture_current(shape) -> bool:
