@@ -48,6 +48,10 @@ __device__ __forceinline__ double warp_sum(double s)
 
 // ------------------------------------------------------------------ tridiagonalisation
 // A = Q T Q^T with Q = P_0 P_1 ... P_{n-3}; R <- R P_0 P_1 ... (R Q).
+// A is symmetric: after the L^-1 transform only its lower triangle is formed
+// and updated (the product A v reads it by rows left of the diagonal and by
+// columns below), which halves the FP64 work of the rank-2 updates and saves
+// two thirds of the second transform's.
 // Shared memory: A [n][lda], R [nr_max][lda] (lda = nu | 1, odd, so that the
 // per-thread row walks of R spread over the banks), v, e, scalars.  When A
 // does not fit (nu above about 110), it lives in a global scratch of
@@ -135,21 +139,25 @@ __global__ void __launch_bounds__(kTriThreads) eig_tridiag_kernel(
             if (tid + q * T < n) A[i * lda + tid + q * T] = x[q];
         __syncthreads();
     }
-    for (int i = n - 1; i >= 0; --i) {   // A <- A L^-T, column i at a time
+    // A <- A L^-T, column i at a time, rows i.. only: the result is symmetric
+    // and from here on only its lower triangle (diagonal included) is read or
+    // written.  Column i reads columns m <= i, which are not yet replaced, at
+    // rows >= i.
+    for (int i = n - 1; i >= 0; --i) {
         const double *Li = Lc + (int64_t)i * nu;
         double x[kPer];
 #pragma unroll
         for (int q = 0; q < kPer; ++q) {
             const int row = tid + q * T;
             double s = 0.0;
-            if (row < n)
+            if (row >= i && row < n)
                 for (int m = 0; m <= i; ++m) s = fma(A[row * lda + m], Li[m], s);
             x[q] = s;
         }
         __syncthreads();
 #pragma unroll
         for (int q = 0; q < kPer; ++q)
-            if (tid + q * T < n) A[(tid + q * T) * lda + i] = x[q];
+            if (tid + q * T >= i && tid + q * T < n) A[(tid + q * T) * lda + i] = x[q];
         __syncthreads();
     }
     for (int r = 1 + tid; r < nr; r += T) {   // R's rows 1..: R <- R L^-T, one row per thread
@@ -159,15 +167,6 @@ __global__ void __launch_bounds__(kTriThreads) eig_tridiag_kernel(
             double s = 0.0;
             for (int m = 0; m <= i; ++m) s = fma(x[m], Li[m], s);
             x[i] = s;
-        }
-    }
-    __syncthreads();
-    for (int idx = tid; idx < n * n; idx += T) {   // symmetrise what rounding left
-        const int i = idx / n, l = idx - (idx / n) * n;
-        if (i > l) {
-            const double a = 0.5 * (A[i * lda + l] + A[l * lda + i]);
-            A[i * lda + l] = a;
-            A[l * lda + i] = a;
         }
     }
     __syncthreads();
@@ -205,13 +204,17 @@ __global__ void __launch_bounds__(kTriThreads) eig_tridiag_kernel(
         const double tauh = sc4[0];
         for (int l = tid; l < L; l += T) v[l] = (l == 0) ? sc4[1] : A[(k + 1 + l) * lda + k];
         __syncthreads();
-        // p = tau A_sub v, columns over the threads (A_sub symmetric; consecutive
-        // threads read consecutive addresses); p goes to the scratch after e
+        // p = tau A_sub v from A_sub's lower triangle, one entry per thread: row
+        // col left of the diagonal (stride lda, odd, across the threads), then
+        // column col from the diagonal down (consecutive addresses); p goes to
+        // the scratch after e
         double *qv = ev + nu;
         double vp = 0.0;
         for (int col = tid; col < L; col += T) {
+            const double *Ar = A + (k + 1 + col) * lda + (k + 1);
             double pl = 0.0;
-            for (int m = 0; m < L; ++m) pl = fma(A[(k + 1 + m) * lda + (k + 1 + col)], v[m], pl);
+            for (int m = 0; m < col; ++m) pl = fma(Ar[m], v[m], pl);
+            for (int m = col; m < L; ++m) pl = fma(A[(k + 1 + m) * lda + (k + 1 + col)], v[m], pl);
             pl *= tauh;
             qv[col] = pl;
             vp = fma(v[col], pl, vp);
@@ -229,9 +232,9 @@ __global__ void __launch_bounds__(kTriThreads) eig_tridiag_kernel(
         __syncthreads();
         for (int col = tid; col < L; col += T) qv[col] = fma(-sc4[2], v[col], qv[col]);   // q = p - K v
         __syncthreads();
-        for (int idx = tid; idx < L * L; idx += T) {  // A_sub -= v q^T + q v^T
+        for (int idx = tid; idx < L * L; idx += T) {  // A_sub -= v q^T + q v^T, lower triangle
             const int a = idx / L, b = idx - (idx / L) * L;
-            A[(k + 1 + a) * lda + (k + 1 + b)] -= v[a] * qv[b] + qv[a] * v[b];
+            if (a >= b) A[(k + 1 + a) * lda + (k + 1 + b)] -= v[a] * qv[b] + qv[a] * v[b];
         }
         for (int r = tid; r < nr; r += T) {  // R <- R (I - tau v v^T) on columns k+1..
             double *row = R + r * lda + (k + 1);
@@ -303,7 +306,12 @@ __global__ void __launch_bounds__(32) eig_ql_kernel(const int *__restrict__ bnu_
             bool under = false;
             for (; i >= l; --i) {
                 const double f = s * EE(i), b = cth * EE(i);
-                r = hypot(f, g);
+                // r = |(f, g)| as one square root and one reciprocal (the
+                // levels and couplings are bounded by the spectrum's width, so
+                // f^2 + g^2 neither overflows nor underflows to zero unless
+                // both are zero)
+                const double ss = fma(f, f, g * g);
+                r = sqrt(ss);
                 EE(i + 1) = r;
                 if (r == 0.0) {
                     DD(i + 1) -= p;
@@ -311,8 +319,9 @@ __global__ void __launch_bounds__(32) eig_ql_kernel(const int *__restrict__ bnu_
                     under = true;
                     break;
                 }
-                s = f / r;
-                cth = g / r;
+                const double rinv = 1.0 / r;
+                s = f * rinv;
+                cth = g * rinv;
                 g = DD(i + 1) - p;
                 r = (DD(i) - g) * s + 2.0 * cth * b;
                 p = s * r;
