@@ -284,6 +284,32 @@ def spmm_algorithmic(nu: int, m: int, nnzb: int, nbr: int, vbytes: int, ncols: i
 
 
 FP32_INST_PEAK = 152 * 128 * 2.07e9   # FP32 instructions/s: 152 SMs x 128 lanes x 2.07 GHz (nominal)
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+
+
+def eig_flops(nu: int, rows: int) -> float:
+    """FP64 flops of one subspace eigensolve (model), with rows = n_pat + 2 rows of R = [e_1; q; K_pat]:
+    L^-1 H L^-T (4/3 nu^3: the full first product, the lower triangle of the second), Householder
+    tridiagonalisation of a symmetric matrix (4/3 nu^3), R L^-T and R's reflections (3 rows nu^2),
+    implicit QL with about nu^2 Givens rotations (20 nu^2) and their replay on R (6 rows nu^2)."""
+    return 8.0 / 3.0 * nu ** 3 + 9.0 * rows * nu * nu + 20.0 * nu * nu
+
+
+def eig_roofline(t, cols, nu: int, eig_stats, steps: int):
+    """The eigensolver's FP64 rate over a timed region: model flops of every column (eig_flops with
+    each column's pattern rows) / the summed CUDA-event time of its kernels, against the FP64 peak
+    derived from the unit counts (GB300's FP64 pipe: 2 FMA per clock per SM)."""
+    n_launch, ms = eig_stats
+    if ms <= 0:
+        return None
+    blocks = np.diff(np.asarray(t.row_ptr))[np.asarray(cols) // 4]
+    flops = float(sum(eig_flops(nu, 4 * int(b) + 2) for b in blocks)) * steps
+    ach = flops / (ms / 1e3) / 1e12
+    return {"kernel": "eigsub (tridiagonalisation, QL, replay)", "bound": "alu", "achieved": round(ach, 4),
+            "peak": round(FP64_PEAK_TFLOPS, 3), "unit": "TFLOP/s", "frac": round(ach / FP64_PEAK_TFLOPS, 4),
+            "peak_source": "derived: " + FP64_PEAK_NOTE, "launches": n_launch,
+            "model": "per column 8/3 nu^3 + 9 r nu^2 + 20 nu^2 flops, r = pattern rows + 2 (about nu^2 "
+                     "QL rotations)"}
 
 
 def spmm_instructions_support(t, tcnt, nu: int, prec: int):
@@ -568,6 +594,8 @@ def main():
                    "parallelism": f"{world} independent replica(s)" if world > 1 else "1 GPU"},
         "roofline": roof,
         "spmm_roofline": spmm_roof,
+        "eig_roofline": (eig_roofline(t, cols, args.nu, stats["eigsub"], steps)
+                         if "eigsub" in stats and not args.region else None),
         "gpu_launches": int(launches),
         "kernel_ms_per_step": {k: round(v[1] / steps, 3) for k, v in stats.items() if v[0]},
         "clocks": res["clocks"],
@@ -628,6 +656,8 @@ def main():
                            "result": {"E_band_eV": rx["E"], "mu_eV": rx["mu"], "N": rx["N"]}}
             if reg_x == 0:
                 checks[label] = gpu_outputs(m, rx["ctx"], cl, nu_x, pr)
+                if "eigsub" in rx["stats"]:
+                    line[label]["eig_roofline"] = eig_roofline(t, cl, nu_x, rx["stats"]["eigsub"], 3)
             if label == "nu100" and pr == 1 and rx["stats"].get("gs", (0, 0.0))[1] > 0:
                 # the Gram-Schmidt kernel's HBM fraction at nu = 100 (support bytes)
                 tc100 = support_counts(t, cl, nu_x, column_m_pad(t.M))

@@ -83,3 +83,29 @@ def test_dram_ratio_belongs_to_the_current_kernel():
     for (prec, shape) in bench.GS_DRAM_PER_ALGORITHMIC:
         assert shape in bench.GS_DRAM_KERNEL and shape in bench.GS_DRAM_SOURCES
         assert bench.capture_current(shape), f"sources of {bench.GS_DRAM_KERNEL[shape]} changed since the capture"
+
+
+def test_eigensolver_flop_model():
+    """bench.eig_flops against the operation counts written out step by step: the L^-1 products
+    (full first product, lower triangle of the second), the Householder steps on the lower
+    triangle (A v, the rank-2 update) and on R, R L^-T, nu^2 QL rotations of 20 flops and their
+    replay at 6 flops per row; eig_roofline sums it over the columns' own pattern rows."""
+    for nu, rows in ((7, 5), (30, 46), (100, 78)):
+        first = sum(2 * (i + 1) * nu for i in range(nu))
+        second = sum(2 * (i + 1) * (nu - i) for i in range(nu))
+        hh = sum(2 * L * L + 2 * L * (L + 1) for L in range(nu - 1, 1, -1))   # A v, rank-2 (lower)
+        r_lt = sum(2 * (i + 1) for i in range(nu)) * rows
+        r_refl = sum(4 * L for L in range(nu - 1, 1, -1)) * rows
+        ql, replay = 20 * nu * nu, 6 * nu * nu * rows
+        exact = first + second + hh + r_lt + r_refl + ql + replay
+        model = bench.eig_flops(nu, rows)
+        # the model keeps the leading terms: within 1 % at the sizes the bench runs
+        assert abs(model - exact) <= 0.01 * exact, (nu, model, exact)
+    t = tiny_hydrocarbon(12, 4, seed=0)
+    cols = t.real_columns()
+    r = bench.eig_roofline(t, cols, 12, (3, 2.0), 1)
+    blocks = np.diff(t.row_ptr)[cols // 4]
+    want = sum(bench.eig_flops(12, 4 * int(b) + 2) for b in blocks) / 2e-3 / 1e12
+    assert r["achieved"] == pytest.approx(want, rel=1e-3, abs=1e-4)
+    assert r["frac"] == pytest.approx(r["achieved"] / bench.FP64_PEAK_TFLOPS, rel=1e-2, abs=1e-4)
+    assert bench.eig_roofline(t, cols, 12, (0, 0.0), 1) is None
