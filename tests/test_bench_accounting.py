@@ -109,3 +109,45 @@ def test_eigensolver_flop_model():
     assert r["achieved"] == pytest.approx(want, rel=1e-3, abs=1e-4)
     assert r["frac"] == pytest.approx(r["achieved"] / bench.FP64_PEAK_TFLOPS, rel=1e-2, abs=1e-4)
     assert bench.eig_roofline(t, cols, 12, (0, 0.0), 1) is None
+
+
+def test_mixed_vs_fp64_statistics():
+    """bench.mixed_vs_fp64's host logic on a stand-in for the library: two densities that differ in
+    one known entry give that entry's size, its count above the bounds and its column."""
+    from types import SimpleNamespace
+
+    t = tiny_hydrocarbon(12, 4, seed=0)
+    nu = 6
+    rho64 = np.zeros((t.nnzb, 4, 4))
+    rho32 = rho64.copy()
+    blk, a, b = 5, 1, 2
+    rho32[blk, a, b] = 3e-5
+    col = 4 * int(t.col_idx[blk]) + b
+    eps = np.tile(np.linspace(-2.0, 2.0, nu), (t.M, 1))
+
+    class Ctx:
+        def __init__(self, prec):
+            self.prec = prec
+
+    lib = SimpleNamespace(
+        setup_system=lambda sysm, prec: Ctx(prec),
+        marnoldi_solve=lambda ctx, cols, nu_, reg, ne, kT: None,
+        marnoldi_energy=lambda ctx: (-10.0 - 1e-9 * ctx.prec, 0.0, 16.0),
+        marnoldi_density=lambda ctx: ((rho32, 2 * rho32) if ctx.prec else (rho64, 2 * rho64)),
+        marnoldi_column_stats=lambda ctx: (np.full(t.M, nu, np.int32), eps, np.ones((t.M, nu))),
+        marnoldi_fermi_at=lambda ctx, mu, kT: (0.0, 0.0),
+        marnoldi_gs_shape=lambda ctx: (64, 288),
+        marnoldi_destroy=lambda ctx: None)
+    import tbsynth   # mixed_vs_fp64 imports the generator when it runs
+    saved = tbsynth.config_c2
+    tbsynth.config_c2 = lambda seed=0: t
+    try:
+        out = bench.mixed_vs_fp64(lib, nu)
+    finally:
+        tbsynth.config_c2 = saved
+    assert out["max_drho"] == pytest.approx(3e-5)
+    assert out["drho_gt_1e-5"] == 1 and out["drhoE_gt_1e-4"] == 0
+    assert out["max_drhoE_eV"] == pytest.approx(6e-5)
+    assert out["worst"]["column"] == col
+    assert out["dE_band_per_atom_eV"] == pytest.approx(1e-9 / t.n_block_rows)
+    assert out["rho_entries"] == t.nnzb * 16
